@@ -1,0 +1,571 @@
+/*
+ * cg_oracle.c -- plain, slow, serial CPU oracle of the mixed rejection KMC
+ * chain for the lattice Coulomb glass (Ferrero, Kolton & Palassini,
+ * "Parallel kinetic Monte Carlo simulation of Coulomb glasses").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this file:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * load it.  It shares no code with the CUDA library; both follow the same
+ * written definition (the paper plus the readings listed below).
+ *
+ * Every floating-point quantity is IEEE binary64.  Compile with
+ * -ffp-contract=off (no fused multiply-add) and without -ffast-math, so that
+ * each + - * / sqrt is one correctly rounded operation in source order.
+ *
+ * What each function follows:
+ *   orc_philox        Philox-4x32-10 of Salmon, Moraes, Dror & Shaw (SC'11,
+ *                     "Parallel random numbers: as easy as 1, 2, 3"); the
+ *                     paper draws its random numbers from Philox (section
+ *                     "Hopping conduction in the Coulomb glass", GPU
+ *                     implementation paragraph).
+ *   orc_cg_exp        exp(x) by Cody & Waite's additive range reduction
+ *                     (Software Manual for the Elementary Functions, 1980)
+ *                     followed by the Taylor series to degree 13.
+ *   orc_new           Eq. 1 (Hamiltonian, filling, disorder), the tunnelling
+ *                     factor of Eq. 2 and the rate normalisation Gamma, the
+ *                     lattice model with toroidal boundaries and minimum image
+ *                     (section "Results for the lattice model in two
+ *                     dimensions").
+ *   orc_eps_scratch   the single-particle energies below Eq. 2:
+ *                     eps_i = phi_i + sum_j (n_j - nu) / r_ij.
+ *   orc_eval_label    steps 1-2 of the mixed PR algorithm (proposal by the
+ *                     tunnelling factor, acceptance by the activation factor
+ *                     Gamma^A = theta * min[1, exp(-dH/T)]) for one label.
+ *   orc_run           the serial rejection algorithm (section "Parallel
+ *                     rejection algorithm", steps 1-2) driven label by label;
+ *                     on the first accepting label it executes step 3 of the
+ *                     mixed PR algorithm (3a commit, 3b dipole and local-energy
+ *                     update, 3c time through the attempt count).
+ *
+ * Readings of the paper taken here (each also listed in the design doc):
+ *   R1  Philox key = (seed lo 32, seed hi 32); proposal counter for round r,
+ *       label k (0-based) of replica c = (k, r lo 32, r hi 32, c); three of
+ *       the four output words are used (site, displacement, acceptance).
+ *   R2  Displacements: all (dx,dy) with 0 < dx^2+dy^2 <= r_max^2 (r_max
+ *       strictly below L/2), ordered dy outer ascending, dx inner ascending.
+ *       Tower sampling over integer weights W_k = floor(2^32 w_k / Z),
+ *       w_k = exp(-2 r_k / xi), Z = sum_k w_k; the sampled vector is the
+ *       smallest k with x1 < C_k (C_k the running sum); x1 >= C_{V-1} is a
+ *       null proposal (rejected, counted as an attempt).
+ *   R3  The attempt count advances by (p-1) M + q per executed hop (q 1-based):
+ *       the paper's "m = pM + q" (step 3c) disagrees with its Fig. 1 example
+ *       and with <m> = 1/A; every round without an accept adds M.
+ *   R4  Time is the deterministic t = attempts / Gamma with Gamma = N * Z,
+ *       the rule the paper used for its figures (Fig. 3 caption).
+ *   R5  Disorder phi_s = W (u - 1/2), u = (x0 + 1/2) 2^-32 from counter
+ *       (s, 1, 0xFFFFFFFF, c): W is the full width of the interval.
+ *   R6  Initial occupation: sites sorted by (x0 of counter (s, 2, 0xFFFFFFFF,
+ *       c), s) ascending; the first nu*N sites are occupied.
+ *   R7  Accept iff dH <= 0 or u < exp(-dH/T), u = (x2 + 1/2) 2^-32, with the
+ *       exp of orc_cg_exp; exp(x) for x < -23 is taken as 0 (it is below the
+ *       smallest u, so the decision is unchanged).
+ *   R8  The 1/r table holds 0 at zero displacement, which makes the three
+ *       cases of step 3b one formula: eps_l += 1/r_lj - 1/r_li.
+ *   R9  dH = ((eps_j - eps_i) - 1/r_ij) - E * dx evaluated in that order.
+ *   R10 Incremental energy: E_tot += dH of each executed hop; the dipole P
+ *       accumulates the hop's minimum-image dx (unwrapped).
+ *
+ * Geometry is a general Lx x Ly torus (Ly = 1 gives a ring) so that tiny
+ * systems can be enumerated exactly; the library itself only builds L x L.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+#define ORC_ESTUCK -5
+
+/* ------------------------------------------------------------------------ */
+/* Philox-4x32-10                                                            */
+/* ------------------------------------------------------------------------ */
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    int round;
+    for (round = 0; round < 10; ++round) {
+        uint64_t prod0, prod1;
+        uint32_t n0, n1, n2, n3;
+        if (round > 0) {            /* key schedule: Weyl increments */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+        n1 = (uint32_t)prod1;
+        n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+        n3 = (uint32_t)prod0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* exp by Cody-Waite reduction + Taylor series                               */
+/* ------------------------------------------------------------------------ */
+
+/* ln 2 = 0.693147180559945309417232121458176568...; LN2_HI keeps its leading
+ * 29 significant bits, so k * LN2_HI is exact for |k| < 2^24, and LN2_LO is
+ * the rest, rounded to double. */
+static const double ORC_LN2_HI = 0x1.62e42ffp-1;
+static const double ORC_LN2_LO = -0x1.718432a1b0e26p-35;
+static const double ORC_INV_LN2 = 0x1.71547652b82fep+0;
+
+/* exp(x) for -745 < x <= 0 (the only range this model needs). */
+double orc_exp_core(double x)
+{
+    double kd, r, p;
+    int n;
+    kd = nearbyint(x * ORC_INV_LN2);
+    r = (x - kd * ORC_LN2_HI) - kd * ORC_LN2_LO;
+    /* Horner form of sum_{n=0}^{13} r^n / n!, coefficients 1/n! rounded */
+    p = 1.0 / 6227020800.0;              /* 1/13! */
+    {
+        static const double fact[13] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0,
+                                        5040.0, 40320.0, 362880.0, 3628800.0,
+                                        39916800.0, 479001600.0};
+        for (n = 12; n >= 0; --n) {
+            double t = p * r;
+            p = t + 1.0 / fact[n];
+        }
+    }
+    return ldexp(p, (int)kd);
+}
+
+/* The acceptance exponential (reading R7). */
+double orc_cg_exp(double x)
+{
+    if (x < -23.0) return 0.0;
+    return orc_exp_core(x);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Chain state                                                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t rounds;      /* global round counter r of this replica */
+    uint64_t hops;        /* executed hops */
+    uint64_t attempts;    /* serial-equivalent attempts */
+    uint64_t evaluated;   /* labels evaluated (== attempts for the serial chain) */
+    int64_t P;            /* dipole moment, unwrapped (sum of hop dx) */
+    double energy;        /* H_0 + sum of executed dH */
+} orc_counters;
+
+typedef struct {
+    uint32_t i, j;        /* origin and destination site */
+    uint32_t q;           /* 1-based label of the executed hop in its round */
+    uint32_t p;           /* rounds used by this hop, including the accepting one */
+    uint64_t round;       /* global round counter of the accepting round */
+    int32_t dx, dy;       /* hop vector */
+    double dE;            /* dH of the executed hop */
+} orc_hop;
+
+typedef struct orc_chain {
+    int Lx, Ly, N, Hx, Hy;    /* Hx = Lx/2 + 1 folded extents */
+    double nu, W, xi, T, E;
+    int r_max;
+    uint64_t seed;
+    uint32_t replica;
+    /* tables */
+    double *tinv;             /* Hy x Hx, tinv[fy*Hx + fx] = 1/r, 0 at (0,0) */
+    int V;
+    int32_t *vdx, *vdy;
+    double *w;                /* real tunnelling weights */
+    uint64_t *Wint;           /* integer weights */
+    uint64_t *C;              /* running sums */
+    double Z;
+    /* state */
+    uint8_t *n;
+    double *phi;
+    double *eps;
+    orc_counters cnt;
+    int toy;                  /* test-only constant acceptance mode */
+    double toy_A0;
+} orc_chain;
+
+static int fold(int d, int L)
+{
+    /* d in (-L, L): minimum-image |d| */
+    int m = d % L;
+    if (m < 0) m += L;
+    return (m < L - m) ? m : L - m;
+}
+
+double orc_tinv_of(const orc_chain *c, int dx, int dy)
+{
+    int fx = fold(dx, c->Lx), fy = fold(dy, c->Ly);
+    return c->tinv[fy * c->Hx + fx];
+}
+
+static double tinv_sites(const orc_chain *c, int a, int b)
+{
+    int xa = a % c->Lx, ya = a / c->Lx, xb = b % c->Lx, yb = b / c->Lx;
+    return orc_tinv_of(c, xa - xb, ya - yb);
+}
+
+void orc_free(orc_chain *c)
+{
+    if (!c) return;
+    free(c->tinv); free(c->vdx); free(c->vdy); free(c->w); free(c->Wint);
+    free(c->C); free(c->n); free(c->phi); free(c->eps);
+    free(c);
+}
+
+/* eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st, summed over t = 0..N-1 in
+ * increasing order, the product rounded first (reading C7 of the design). */
+void orc_eps_scratch(const orc_chain *c, double *out)
+{
+    int s, t;
+    for (s = 0; s < c->N; ++s) {
+        double acc = 0.0;
+        for (t = 0; t < c->N; ++t) {
+            double term;
+            if (t == s) continue;
+            term = ((double)c->n[t] - c->nu) * tinv_sites(c, s, t);
+            acc = acc + term;
+        }
+        out[s] = c->phi[s] + acc;
+    }
+}
+
+/* H of Eq. 1 from scratch, with the field term written with the site
+ * coordinates x in [0, Lx).  Used for the initial energy only. */
+double orc_energy_scratch(const orc_chain *c)
+{
+    double h1 = 0.0, h2 = 0.0, h3 = 0.0;
+    int s, t;
+    for (s = 0; s < c->N; ++s) {
+        h1 = h1 + c->phi[s] * (double)c->n[s];
+        h3 = h3 + (double)c->n[s] * (double)(s % c->Lx);
+    }
+    for (s = 0; s < c->N; ++s) {
+        double ss = (double)c->n[s] - c->nu;
+        for (t = 0; t < c->N; ++t) {
+            if (t == s) continue;
+            h2 = h2 + ss * ((double)c->n[t] - c->nu) * tinv_sites(c, s, t);
+        }
+    }
+    return h1 + 0.5 * h2 - c->E * h3;
+}
+
+typedef struct { uint32_t key; uint32_t site; } orc_sortkey;
+
+static int cmp_sortkey(const void *a, const void *b)
+{
+    const orc_sortkey *x = (const orc_sortkey *)a, *y = (const orc_sortkey *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->site != y->site) return x->site < y->site ? -1 : 1;
+    return 0;
+}
+
+static void philox_setup_word(const orc_chain *c, uint32_t s, uint32_t domain,
+                              uint32_t out[4])
+{
+    uint32_t ctr[4], key[2];
+    ctr[0] = s; ctr[1] = domain; ctr[2] = 0xFFFFFFFFu; ctr[3] = c->replica;
+    key[0] = (uint32_t)c->seed; key[1] = (uint32_t)(c->seed >> 32);
+    orc_philox(ctr, key, out);
+}
+
+orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
+                   double T, double E, uint64_t seed, uint32_t replica)
+{
+    orc_chain *c;
+    int fx, fy, dx, dy, k, s, nocc, Ry;
+    double nuN;
+    orc_sortkey *sk;
+
+    if (Lx < 2 || Ly < 1 || (Lx % 2) || (Ly > 1 && (Ly % 2))) return NULL;
+    if (!(nu > 0.0 && nu < 1.0) || !(xi > 0.0) || !(T > 0.0) || !(W >= 0.0)) return NULL;
+    if (r_max < 1 || 2 * r_max >= Lx || (Ly > 1 && 2 * r_max >= Ly)) return NULL;
+    nuN = nu * (double)(Lx * Ly);
+    if (fabs(nuN - floor(nuN + 0.5)) > 1e-9) return NULL;
+
+    c = (orc_chain *)calloc(1, sizeof(*c));
+    if (!c) return NULL;
+    c->Lx = Lx; c->Ly = Ly; c->N = Lx * Ly;
+    c->Hx = Lx / 2 + 1; c->Hy = Ly / 2 + 1;
+    c->nu = nu; c->W = W; c->xi = xi; c->T = T; c->E = E; c->r_max = r_max;
+    c->seed = seed; c->replica = replica;
+
+    /* folded minimum-image 1/r table (reading R8: zero at the origin) */
+    c->tinv = (double *)calloc((size_t)c->Hx * c->Hy, sizeof(double));
+    for (fy = 0; fy < c->Hy; ++fy)
+        for (fx = 0; fx < c->Hx; ++fx)
+            c->tinv[fy * c->Hx + fx] =
+                (fx == 0 && fy == 0) ? 0.0
+                                     : 1.0 / sqrt((double)(fx * fx + fy * fy));
+
+    /* displacement list and tower (reading R2) */
+    Ry = (Ly > 1) ? r_max : 0;
+    c->V = 0;
+    for (dy = -Ry; dy <= Ry; ++dy)
+        for (dx = -r_max; dx <= r_max; ++dx) {
+            int r2 = dx * dx + dy * dy;
+            if (r2 > 0 && r2 <= r_max * r_max) c->V++;
+        }
+    c->vdx = (int32_t *)malloc(sizeof(int32_t) * c->V);
+    c->vdy = (int32_t *)malloc(sizeof(int32_t) * c->V);
+    c->w = (double *)malloc(sizeof(double) * c->V);
+    c->Wint = (uint64_t *)malloc(sizeof(uint64_t) * c->V);
+    c->C = (uint64_t *)malloc(sizeof(uint64_t) * c->V);
+    k = 0;
+    for (dy = -Ry; dy <= Ry; ++dy)
+        for (dx = -r_max; dx <= r_max; ++dx) {
+            int r2 = dx * dx + dy * dy;
+            if (r2 > 0 && r2 <= r_max * r_max) {
+                c->vdx[k] = dx; c->vdy[k] = dy;
+                c->w[k] = orc_exp_core(-2.0 * sqrt((double)r2) / xi);
+                ++k;
+            }
+        }
+    c->Z = 0.0;
+    for (k = 0; k < c->V; ++k) c->Z = c->Z + c->w[k];
+    {
+        uint64_t run = 0;
+        for (k = 0; k < c->V; ++k) {
+            double f = (c->w[k] / c->Z) * 4294967296.0;
+            c->Wint[k] = (uint64_t)floor(f);
+            run += c->Wint[k];
+            c->C[k] = run;
+        }
+    }
+
+    /* disorder (reading R5) */
+    c->phi = (double *)malloc(sizeof(double) * c->N);
+    c->n = (uint8_t *)calloc((size_t)c->N, 1);
+    c->eps = (double *)malloc(sizeof(double) * c->N);
+    for (s = 0; s < c->N; ++s) {
+        uint32_t o[4];
+        double u;
+        philox_setup_word(c, (uint32_t)s, 1u, o);
+        u = ((double)o[0] + 0.5) * 0x1p-32;
+        c->phi[s] = W * (u - 0.5);
+    }
+    /* initial occupation (reading R6) */
+    sk = (orc_sortkey *)malloc(sizeof(orc_sortkey) * c->N);
+    for (s = 0; s < c->N; ++s) {
+        uint32_t o[4];
+        philox_setup_word(c, (uint32_t)s, 2u, o);
+        sk[s].key = o[0];
+        sk[s].site = (uint32_t)s;
+    }
+    qsort(sk, (size_t)c->N, sizeof(orc_sortkey), cmp_sortkey);
+    nocc = (int)floor(nuN + 0.5);
+    for (s = 0; s < nocc; ++s) c->n[sk[s].site] = 1;
+    free(sk);
+
+    orc_eps_scratch(c, c->eps);
+    memset(&c->cnt, 0, sizeof(c->cnt));
+    c->cnt.energy = orc_energy_scratch(c);
+    {
+        int64_t P = 0;
+        for (s = 0; s < c->N; ++s) if (c->n[s]) P += s % c->Lx;
+        c->cnt.P = P;
+    }
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Accessors                                                                 */
+/* ------------------------------------------------------------------------ */
+
+int orc_num_vectors(const orc_chain *c) { return c->V; }
+int orc_num_sites(const orc_chain *c) { return c->N; }
+double orc_Z(const orc_chain *c) { return c->Z; }
+double orc_Gamma(const orc_chain *c) { return (double)c->N * c->Z; }
+
+void orc_get_vectors(const orc_chain *c, int32_t *dx, int32_t *dy,
+                     uint64_t *Wint, double *w)
+{
+    int k;
+    for (k = 0; k < c->V; ++k) {
+        if (dx) dx[k] = c->vdx[k];
+        if (dy) dy[k] = c->vdy[k];
+        if (Wint) Wint[k] = c->Wint[k];
+        if (w) w[k] = c->w[k];
+    }
+}
+
+void orc_get_tinv(const orc_chain *c, double *out)
+{
+    memcpy(out, c->tinv, sizeof(double) * (size_t)c->Hx * c->Hy);
+}
+
+void orc_get_state(const orc_chain *c, uint8_t *n, double *eps, double *phi)
+{
+    if (n) memcpy(n, c->n, (size_t)c->N);
+    if (eps) memcpy(eps, c->eps, sizeof(double) * c->N);
+    if (phi) memcpy(phi, c->phi, sizeof(double) * c->N);
+}
+
+/* Replace occupation (and optionally disorder); eps is rebuilt from scratch,
+ * the energy is recomputed from Eq. 1 and P from the coordinates. */
+int orc_set_state(orc_chain *c, const uint8_t *n, const double *phi)
+{
+    int s;
+    int64_t P = 0;
+    for (s = 0; s < c->N; ++s) if (n[s] > 1) return ORC_EINVAL;
+    memcpy(c->n, n, (size_t)c->N);
+    if (phi) memcpy(c->phi, phi, sizeof(double) * c->N);
+    orc_eps_scratch(c, c->eps);
+    c->cnt.energy = orc_energy_scratch(c);
+    for (s = 0; s < c->N; ++s) if (c->n[s]) P += s % c->Lx;
+    c->cnt.P = P;
+    return ORC_OK;
+}
+
+/* Overwrite eps directly (resume from a saved trajectory point). */
+void orc_set_eps(orc_chain *c, const double *eps)
+{
+    memcpy(c->eps, eps, sizeof(double) * c->N);
+}
+
+void orc_get_counters(const orc_chain *c, orc_counters *out) { *out = c->cnt; }
+void orc_set_counters(orc_chain *c, const orc_counters *in) { c->cnt = *in; }
+
+void orc_set_toy(orc_chain *c, int on, double A0)
+{
+    c->toy = on;
+    c->toy_A0 = A0;
+}
+
+/* dH of the hop i -> j with x-displacement dx, from the current eps (R9). */
+double orc_delta_e(const orc_chain *c, int i, int j, int dx)
+{
+    double r_inv = tinv_sites(c, i, j);
+    double d = c->eps[j] - c->eps[i];
+    d = d - r_inv;
+    return d - c->E * (double)dx;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One label: steps 1-2 of the mixed PR algorithm                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t accepted;
+    int32_t vec;          /* displacement index, -1 for a null proposal */
+    uint32_t i, j;
+    int32_t dx, dy;
+    int32_t theta;        /* n_i = 1 and n_j = 0 */
+    double dE;
+    double u;
+    uint32_t x[4];        /* raw Philox words */
+} orc_label;
+
+static int tower_sample(const orc_chain *c, uint32_t x1)
+{
+    /* smallest k with x1 < C_k; -1 when x1 >= C_{V-1} (null proposal) */
+    int lo = 0, hi = c->V;               /* answer in [lo, hi] */
+    if ((uint64_t)x1 >= c->C[c->V - 1]) return -1;
+    while (lo < hi) {
+        int mid = lo + (hi - lo) / 2;
+        if ((uint64_t)x1 < c->C[mid]) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *out)
+{
+    uint32_t ctr[4], key[2];
+    int v, xi, yi, xj, yj;
+    memset(out, 0, sizeof(*out));
+    ctr[0] = k;
+    ctr[1] = (uint32_t)round;
+    ctr[2] = (uint32_t)(round >> 32);
+    ctr[3] = c->replica;
+    key[0] = (uint32_t)c->seed;
+    key[1] = (uint32_t)(c->seed >> 32);
+    orc_philox(ctr, key, out->x);
+
+    out->i = (uint32_t)(((uint64_t)out->x[0] * (uint64_t)c->N) >> 32);
+    out->u = ((double)out->x[2] + 0.5) * 0x1p-32;
+    v = tower_sample(c, out->x[1]);
+    out->vec = v;
+    if (c->toy) {                        /* test-only: constant acceptance */
+        out->accepted = out->u < c->toy_A0;
+        return;
+    }
+    if (v < 0) { out->accepted = 0; return; }
+    out->dx = c->vdx[v];
+    out->dy = c->vdy[v];
+    xi = (int)(out->i % (uint32_t)c->Lx);
+    yi = (int)(out->i / (uint32_t)c->Lx);
+    xj = (xi + out->dx + c->Lx) % c->Lx;
+    yj = (yi + out->dy + c->Ly) % c->Ly;
+    out->j = (uint32_t)(yj * c->Lx + xj);
+    out->theta = (c->n[out->i] == 1) && (c->n[out->j] == 0);
+    if (!out->theta) { out->accepted = 0; return; }
+    out->dE = orc_delta_e(c, (int)out->i, (int)out->j, out->dx);
+    if (out->dE <= 0.0) { out->accepted = 1; return; }
+    out->accepted = out->u < orc_cg_exp((-out->dE) / c->T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 3: execute the hop                                                   */
+/* ------------------------------------------------------------------------ */
+
+static void commit_hop(orc_chain *c, const orc_label *lab)
+{
+    int l;
+    uint32_t i = lab->i, j = lab->j;
+    if (c->toy) return;                  /* toy mode moves no electron */
+    c->n[i] = 0;
+    c->n[j] = 1;
+    c->cnt.P += lab->dx;
+    c->cnt.energy = c->cnt.energy + lab->dE;
+    for (l = 0; l < c->N; ++l) {
+        double delta = tinv_sites(c, l, (int)j) - tinv_sites(c, l, (int)i);
+        c->eps[l] = c->eps[l] + delta;
+    }
+}
+
+/* Run until n_hops more hops are executed.  M labels per round; a hop whose
+ * rounds reach max_rounds without an accept ends the call with ORC_ESTUCK
+ * (the failed rounds are counted).  log, when given, receives one entry per
+ * executed hop. */
+int orc_run(orc_chain *c, uint64_t n_hops, uint32_t M, uint64_t max_rounds,
+            orc_hop *log)
+{
+    uint64_t h;
+    if (M == 0) return ORC_EINVAL;
+    for (h = 0; h < n_hops; ++h) {
+        uint32_t p = 0;
+        for (;;) {
+            uint32_t k;
+            int done = 0;
+            orc_label lab;
+            ++p;
+            for (k = 0; k < M; ++k) {
+                orc_eval_label(c, c->cnt.rounds, k, &lab);
+                c->cnt.evaluated++;
+                if (lab.accepted) { done = 1; break; }
+            }
+            if (done) {
+                uint32_t q = k + 1;
+                if (log) {
+                    orc_hop *e = &log[h];
+                    e->i = lab.i; e->j = lab.j; e->q = q; e->p = p;
+                    e->round = c->cnt.rounds;
+                    e->dx = lab.dx; e->dy = lab.dy; e->dE = lab.dE;
+                }
+                c->cnt.attempts += q;
+                c->cnt.rounds += 1;
+                c->cnt.hops += 1;
+                commit_hop(c, &lab);
+                break;
+            }
+            c->cnt.attempts += M;
+            c->cnt.rounds += 1;
+            if ((uint64_t)p >= max_rounds) return ORC_ESTUCK;
+        }
+    }
+    return ORC_OK;
+}

@@ -1,0 +1,45 @@
+"""Independent numpy evaluations of Eq. 1 used to pin the oracle.
+
+These are written from the Hamiltonian of Eq. 1 (site energies, pair term
+with minimum-image distances on the torus, field term) with numpy's own
+``hypot`` and dense algebra; they share nothing with the oracle's C tables.
+"""
+import numpy as np
+
+
+def min_image_distance_matrix(Lx, Ly):
+    """Euclidean minimum-image distance between every pair of sites."""
+    N = Lx * Ly
+    s = np.arange(N)
+    x, y = s % Lx, s // Lx
+    dx = np.abs(x[:, None] - x[None, :])
+    dy = np.abs(y[:, None] - y[None, :])
+    dx = np.minimum(dx, Lx - dx)
+    dy = np.minimum(dy, Ly - dy)
+    return np.hypot(dx, dy)
+
+
+def coupling_matrix(Lx, Ly):
+    """G[s, t] = 1 / r_st for s != t and 0 on the diagonal."""
+    D = min_image_distance_matrix(Lx, Ly)
+    with np.errstate(divide="ignore"):
+        G = np.where(D > 0, 1.0 / np.where(D > 0, D, 1.0), 0.0)
+    return G
+
+
+def site_energies(n, phi, nu, G):
+    """eps = phi + G (n - nu)."""
+    return phi + G @ (n.astype(np.float64) - nu)
+
+
+def interaction_energy(n, phi, nu, G):
+    """H of Eq. 1 without the field term (well defined on the torus)."""
+    s = n.astype(np.float64) - nu
+    return float(phi @ n.astype(np.float64) + 0.5 * s @ (G @ s))
+
+
+def interaction_energy_batch(S, phi, nu, G):
+    """Rows of S are occupations; returns H_int for each."""
+    Sf = S.astype(np.float64)
+    c = Sf - nu
+    return Sf @ phi + 0.5 * np.einsum("ij,ij->i", c @ G, c)
