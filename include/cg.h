@@ -1,0 +1,229 @@
+/*
+ * cg.h -- C ABI of libcg: parallel-rejection kinetic Monte Carlo of the 2D
+ * lattice Coulomb glass on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: E.E. Ferrero, A.B. Kolton, M. Palassini, "Parallel kinetic Monte
+ * Carlo simulation of Coulomb glasses".  The model is the Hamiltonian of
+ * Eq. 1 on an L x L torus with minimum-image distances (section "Results for
+ * the lattice model in two dimensions"); the dynamics is the mixed PR
+ * algorithm (section "Hopping conduction in the Coulomb glass", steps 1-3):
+ * M labels per round propose hops i -> j drawn from the tunnelling factor of
+ * Eq. 2 by tower sampling, each is tested with the activation factor
+ * min[1, exp(-dH/T)], the lowest accepting label is executed, and the N
+ * local energies eps are updated (step 3b).
+ *
+ * Conventions shared by every entry point
+ *   - Sites are numbered s = y*L + x, x, y in [0, L).
+ *   - All pointers named *_host point to host memory owned by the caller;
+ *     the library copies from/to them and keeps no reference.
+ *   - Device memory is owned by the library (cudaMalloc) unless the handle
+ *     was created over a caller workspace (cg_create_batch_ws), in which case
+ *     the caller owns that workspace and must keep it alive until
+ *     cg_destroy returns.
+ *   - Every int-returning call returns CG_OK (0) or a negative CG_E* code and
+ *     never throws; cg_last_error() gives a message for the calling thread's
+ *     last failure.  A handle whose call returned CG_ECUDA should be
+ *     destroyed.
+ *   - Calls on one handle must not overlap (one host thread at a time).
+ */
+#ifndef CG_H
+#define CG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG_OK 0
+#define CG_EINVAL (-1)   /* a parameter is out of range; nothing changed      */
+#define CG_ENOMEM (-2)   /* device or host allocation failed                  */
+#define CG_ECUDA (-3)    /* a CUDA call failed; the message names it          */
+#define CG_ETIMEOUT (-4) /* a bounded device wait ran out                     */
+#define CG_ESTUCK (-5)   /* max rounds per hop reached without an accept; the
+                            state is valid and the failed rounds are counted */
+#define CG_ESTATE (-6)   /* a state passed in is inconsistent                 */
+
+#define CG_FP64 0        /* eps in binary64: bit-exact with the serial chain  */
+#define CG_FP32 1        /* eps in binary32 with a periodic binary64 refresh  */
+
+#define CG_REFRESH_AUTO 0
+#define CG_REFRESH_FP64 1  /* direct G (n - nu) in binary64                   */
+#define CG_REFRESH_BF16X2 2 /* split-BF16 hi+lo tensor-core contraction over
+                               the replicas of one L                          */
+
+typedef struct cg_handle cg_handle;
+
+/* One disorder replica: the parameters of Eq. 1 and Eq. 2.
+ *   L      lattice side, even, 4 <= L; N = L*L sites
+ *   nu     filling factor, 0 < nu < 1, nu*N an integer (electrons)
+ *   W      full width of the site-energy interval: phi ~ U[-W/2, W/2]
+ *   xi     localisation length (> 0) in the tunnelling factor exp(-2r/xi)
+ *   r_max  hop cut-off radius, 1 <= r_max < L/2 (hops inside the disk)
+ *   T      temperature (> 0)
+ *   E      field along x; dH of a hop contains -E*dx
+ *   seed   Philox key (64 bits)
+ *   replica  Philox counter word 3 of every draw of this replica          */
+typedef struct {
+    int32_t L;
+    int32_t r_max;
+    double nu, W, xi, T, E;
+    uint64_t seed;
+    uint32_t replica;
+    uint32_t pad_;
+} cg_replica_desc;
+
+/* Options of a handle.  Zero-initialised means: FP64, no refresh, automatic
+ * launch shape, 2^32 rounds per hop before CG_ESTUCK, a 10 s limit per hop,
+ * device 0, a stream created by the library. */
+typedef struct {
+    int32_t precision;          /* CG_FP64 or CG_FP32                           */
+    int32_t refresh_kind;       /* CG_REFRESH_*                                 */
+    uint32_t refresh_every;     /* FP32: hops between refreshes, 0 = never      */
+    int32_t block_threads;      /* 0 = automatic; else 128..1024, multiple of 32 */
+    uint64_t max_rounds_per_hop;/* 0 = 2^32                                     */
+    int32_t device;             /* CUDA device ordinal                          */
+    int32_t use_graph;          /* 1: cg_run replays a captured CUDA graph      */
+    void *stream;               /* cudaStream_t to launch on; NULL = own stream */
+    uint32_t hop_timeout_ms;    /* wall-clock limit of one hop on the device
+                                   (0 = 10000 ms); past it the launch stops
+                                   with CG_ETIMEOUT, the state stays valid    */
+    uint32_t pad_;
+} cg_opts;
+
+/* Counters of one replica (step 3 of the mixed PR algorithm). */
+typedef struct {
+    uint64_t rounds;     /* global round counter r (every round, accepted or not) */
+    uint64_t hops;       /* executed hops                                         */
+    uint64_t attempts;   /* serial-equivalent attempts: (p-1) M + q per hop       */
+    uint64_t evaluated;  /* labels actually evaluated on the GPU                  */
+    int64_t P;           /* dipole moment sum_i n_i x_i, unwrapped by hop dx      */
+    double energy;       /* H of Eq. 1 (field term with the unwrapped P)          */
+} cg_counters;
+
+/* Observables of one replica. */
+typedef struct {
+    cg_counters c;
+    double time;              /* attempts / Gamma (deterministic time rule)   */
+    double Gamma;             /* N * sum_d exp(-2|d|/xi) over the hop disk     */
+    double acceptance;        /* hops / attempts                              */
+    double energy_per_site;   /* energy / N                                   */
+    double max_eps_err_last_refresh; /* FP32: max |eps - eps_refreshed| seen
+                                        just before the last refresh          */
+    uint64_t refreshes;       /* refreshes done                                */
+    uint64_t cycles_reject;   /* SM clock cycles spent proposing/testing       */
+    uint64_t cycles_update;   /* SM clock cycles spent in the eps update       */
+} cg_obs;
+
+/* One executed hop (diagnostics; see cg_run_logged). */
+typedef struct {
+    uint32_t i, j;       /* origin, destination                        */
+    uint32_t q;          /* 1-based label of the hop in its round      */
+    uint32_t p;          /* rounds used for this hop                   */
+    uint64_t round;      /* round counter of the accepting round       */
+    int32_t dx, dy;      /* hop vector                                 */
+    double dE;           /* dH of the hop (binary64)                   */
+} cg_hop;
+
+/* ---------------------------------------------------------------------- */
+
+/* Create one FP64 replica with replica index 0 (the arguments of
+ * cg_replica_desc).  Builds the tables, draws disorder phi and the initial
+ * random occupation from Philox(seed), computes eps from scratch.
+ * Returns NULL on error (cg_last_error). */
+cg_handle *cg_create(int L, double nu, double W, double xi, int r_max,
+                     double T, double E, uint64_t seed);
+
+/* Create R replicas (any mix of L) sharing one stream and one option set.
+ * reps: R host descriptors; opts may be NULL (defaults). */
+cg_handle *cg_create_batch(int R, const cg_replica_desc *reps,
+                           const cg_opts *opts);
+
+/* Bytes of device workspace cg_create_batch_ws needs for these replicas. */
+size_t cg_workspace_bytes(int R, const cg_replica_desc *reps,
+                          const cg_opts *opts);
+
+/* As cg_create_batch, but every device buffer is carved from the caller's
+ * workspace (device pointer, 256-byte aligned, ws_bytes >= cg_workspace_bytes);
+ * the library then calls no cudaMalloc for this handle. */
+cg_handle *cg_create_batch_ws(int R, const cg_replica_desc *reps,
+                              const cg_opts *opts, void *workspace,
+                              size_t ws_bytes);
+
+void cg_destroy(cg_handle *h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *cg_last_error(void);
+
+int cg_num_replicas(const cg_handle *h);
+int cg_num_sites(const cg_handle *h, int replica);
+
+/* Advance every replica by n_hops executed hops with M labels per round
+ * (1 <= M <= 2^24).  Blocks until the work is done.  FP32 handles refresh
+ * eps every refresh_every hops.  Returns CG_ESTUCK if some replica reached
+ * max_rounds_per_hop; other replicas still completed their hops. */
+int cg_run(cg_handle *h, uint64_t n_hops, uint32_t M);
+
+/* cg_run without the final wait: the work is queued on the handle's stream
+ * and cg_sync() waits for it and returns its status. */
+int cg_run_async(cg_handle *h, uint64_t n_hops, uint32_t M);
+int cg_sync(cg_handle *h);
+
+/* cg_run that also records every executed hop: log_host receives
+ * R * n_hops entries, replica-major. */
+int cg_run_logged(cg_handle *h, uint64_t n_hops, uint32_t M, cg_hop *log_host);
+
+/* Copy one replica's state to host buffers (NULL pointers are skipped):
+ * n_host N bytes (0/1), eps_host N doubles (FP32 eps widened), phi_host N
+ * doubles, c_host the counters. */
+int cg_read_state(cg_handle *h, int replica, uint8_t *n_host, double *eps_host,
+                  double *phi_host, cg_counters *c_host);
+
+/* Overwrite one replica's state.  n_host (N bytes 0/1, nu*N ones) is
+ * required; phi_host replaces the disorder when non-NULL; eps_host sets eps
+ * when non-NULL, otherwise eps is rebuilt from scratch; c_host sets the
+ * counters when non-NULL, otherwise the counters restart at 0 with the energy
+ * and dipole recomputed.  Returns CG_ESTATE for a bad occupation. */
+int cg_write_state(cg_handle *h, int replica, const uint8_t *n_host,
+                   const double *eps_host, const double *phi_host,
+                   const cg_counters *c_host);
+
+int cg_observables(cg_handle *h, int replica, cg_obs *out);
+
+/* Rebuild eps of every replica from scratch now, from its definition below
+ * Eq. 2: eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st.  CG_FP64 handles
+ * recompute it in the serial summation order (bit-identical to a fresh
+ * start); CG_FP32 handles recompute it in binary64, record the largest
+ * |eps_fp32 - eps_new| (cg_obs.max_eps_err_last_refresh) and store eps_new
+ * rounded to binary32.  Blocks until done. */
+int cg_refresh(cg_handle *h);
+
+/* cg_refresh queued on the handle's stream without waiting (cg_sync waits). */
+int cg_refresh_async(cg_handle *h);
+
+/* Peak-rate microbenchmarks of the device (no handle needed):
+ *   kind 0: shared-memory read-modify-write bandwidth of 32-bit words, bytes/s
+ *   kind 1: binary64 add throughput, adds/s
+ *   kind 2: shared-memory read-modify-write bandwidth of 64-bit words, bytes/s
+ * summed over all SMs; result written to *result. */
+int cg_microbench(int kind, int device, double *result);
+
+/* Test-only constant-acceptance mode: every label accepts iff u < A0, the
+ * configuration is never changed, the counters advance.  A0 < 0 turns the
+ * mode off. */
+int cg_set_toy_acceptance(cg_handle *h, double A0);
+
+/* Exported device helpers for tests: evaluate Philox-4x32-10 and the
+ * acceptance exponential on the GPU for n inputs (host arrays in/out). */
+int cg_debug_philox(const uint32_t *ctr_host, const uint32_t *key_host,
+                    uint32_t *out_host, int n);
+int cg_debug_exp(const double *x_host, double *out_host, int n);
+
+/* Library version string. */
+const char *cg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CG_H */

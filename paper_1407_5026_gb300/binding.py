@@ -1,0 +1,352 @@
+"""ctypes binding of libcg (include/cg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method; all steps of the chain run in libcg's kernels.  If
+the library is missing the import of this module still succeeds but every
+call raises: there is no CPU fallback.
+
+``System`` is a convenience wrapper that gives the handle a torch-allocated
+device workspace and the current torch stream (PyTorch supplies device memory
+and streams, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcg.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_ESTUCK, CG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+CG_FP64, CG_FP32 = 0, 1
+CG_REFRESH_AUTO, CG_REFRESH_FP64, CG_REFRESH_BF16X2 = 0, 1, 2
+
+EXPORTED = [
+    "cg_create", "cg_create_batch", "cg_workspace_bytes", "cg_create_batch_ws",
+    "cg_destroy", "cg_last_error", "cg_num_replicas", "cg_num_sites", "cg_run",
+    "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
+    "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
+    "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_version",
+]
+
+
+class CgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libcg error {code}: {msg}")
+        self.code = code
+
+
+class cg_replica_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("r_max", ctypes.c_int32),
+                ("nu", ctypes.c_double), ("W", ctypes.c_double),
+                ("xi", ctypes.c_double), ("T", ctypes.c_double),
+                ("E", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("replica", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
+
+
+class cg_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("refresh_kind", ctypes.c_int32),
+                ("refresh_every", ctypes.c_uint32), ("block_threads", ctypes.c_int32),
+                ("max_rounds_per_hop", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("hop_timeout_ms", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
+
+
+class cg_counters(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("hops", ctypes.c_uint64),
+                ("attempts", ctypes.c_uint64), ("evaluated", ctypes.c_uint64),
+                ("P", ctypes.c_int64), ("energy", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class cg_obs(ctypes.Structure):
+    _fields_ = [("c", cg_counters), ("time", ctypes.c_double), ("Gamma", ctypes.c_double),
+                ("acceptance", ctypes.c_double), ("energy_per_site", ctypes.c_double),
+                ("max_eps_err_last_refresh", ctypes.c_double),
+                ("refreshes", ctypes.c_uint64), ("cycles_reject", ctypes.c_uint64),
+                ("cycles_update", ctypes.c_uint64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "c"}
+        d.update(self.c.as_dict())
+        return d
+
+
+class cg_hop(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("p", ctypes.c_uint32), ("round", ctypes.c_uint64), ("dx", ctypes.c_int32),
+                ("dy", ctypes.c_int32), ("dE", ctypes.c_double)]
+
+
+HOP_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("q", "<u4"), ("p", "<u4"),
+                      ("round", "<u8"), ("dx", "<i4"), ("dy", "<i4"), ("dE", "<f8")])
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libcg.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libcg.so not built ({p}); run __graft_entry__.build()")
+        L = ctypes.CDLL(p)
+        P = ctypes.POINTER
+        vp, u8p, dp, u32p = ctypes.c_void_p, P(ctypes.c_uint8), P(ctypes.c_double), P(ctypes.c_uint32)
+        sig = {
+            "cg_create": (vp, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64]),
+            "cg_create_batch": (vp, [ctypes.c_int, P(cg_replica_desc), P(cg_opts)]),
+            "cg_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, P(cg_replica_desc), P(cg_opts)]),
+            "cg_create_batch_ws": (vp, [ctypes.c_int, P(cg_replica_desc), P(cg_opts), vp,
+                                        ctypes.c_size_t]),
+            "cg_destroy": (None, [vp]),
+            "cg_last_error": (ctypes.c_char_p, []),
+            "cg_num_replicas": (ctypes.c_int, [vp]),
+            "cg_num_sites": (ctypes.c_int, [vp, ctypes.c_int]),
+            "cg_run": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32]),
+            "cg_run_async": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32]),
+            "cg_sync": (ctypes.c_int, [vp]),
+            "cg_run_logged": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, P(cg_hop)]),
+            "cg_read_state": (ctypes.c_int, [vp, ctypes.c_int, u8p, dp, dp, P(cg_counters)]),
+            "cg_write_state": (ctypes.c_int, [vp, ctypes.c_int, u8p, dp, dp, P(cg_counters)]),
+            "cg_observables": (ctypes.c_int, [vp, ctypes.c_int, P(cg_obs)]),
+            "cg_refresh": (ctypes.c_int, [vp]),
+            "cg_refresh_async": (ctypes.c_int, [vp]),
+            "cg_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp]),
+            "cg_set_toy_acceptance": (ctypes.c_int, [vp, ctypes.c_double]),
+            "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
+            "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
+            "cg_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return _lib
+
+
+def _check(rc, allow=()):
+    if rc != CG_OK and rc not in allow:
+        raise CgError(rc, cg_last_error())
+    return rc
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0):
+    return cg_replica_desc(L=L, r_max=r_max, nu=nu, W=W, xi=xi, T=T, E=E, seed=seed,
+                           replica=replica)
+
+
+def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,
+         max_rounds_per_hop=0, device=0, use_graph=0, stream=None, hop_timeout_ms=0):
+    return cg_opts(precision=precision, refresh_kind=refresh_kind, refresh_every=refresh_every,
+                   block_threads=block_threads, max_rounds_per_hop=max_rounds_per_hop,
+                   device=device, use_graph=use_graph, stream=stream,
+                   hop_timeout_ms=hop_timeout_ms)
+
+
+# ---- the C entry points, one to one ----
+
+def cg_last_error() -> str:
+    return load().cg_last_error().decode()
+
+
+def cg_version() -> str:
+    return load().cg_version().decode()
+
+
+def cg_create(L, nu, W, xi, r_max, T, E, seed):
+    h = load().cg_create(L, nu, W, xi, r_max, T, E, seed)
+    if not h:
+        raise CgError(CG_EINVAL, cg_last_error())
+    return h
+
+
+def _descs(reps):
+    arr = (cg_replica_desc * len(reps))()
+    for k, r in enumerate(reps):
+        arr[k] = r if isinstance(r, cg_replica_desc) else desc(**r)
+    return arr
+
+
+def cg_create_batch(reps, o=None):
+    arr = _descs(reps)
+    h = load().cg_create_batch(len(reps), arr, ctypes.byref(o) if o is not None else None)
+    if not h:
+        raise CgError(CG_EINVAL, cg_last_error())
+    return h
+
+
+def cg_workspace_bytes(reps, o=None) -> int:
+    arr = _descs(reps)
+    return load().cg_workspace_bytes(len(reps), arr, ctypes.byref(o) if o is not None else None)
+
+
+def cg_create_batch_ws(reps, o, workspace_ptr: int, ws_bytes: int):
+    arr = _descs(reps)
+    h = load().cg_create_batch_ws(len(reps), arr, ctypes.byref(o) if o is not None else None,
+                                  ctypes.c_void_p(workspace_ptr), ws_bytes)
+    if not h:
+        raise CgError(CG_EINVAL, cg_last_error())
+    return h
+
+
+def cg_destroy(h):
+    if h:
+        load().cg_destroy(h)
+
+
+def cg_num_replicas(h) -> int:
+    return load().cg_num_replicas(h)
+
+
+def cg_num_sites(h, replica=0) -> int:
+    return load().cg_num_sites(h, replica)
+
+
+def cg_run(h, n_hops, M):
+    return _check(load().cg_run(h, n_hops, M), allow=(CG_ESTUCK,))
+
+
+def cg_run_async(h, n_hops, M):
+    return _check(load().cg_run_async(h, n_hops, M))
+
+
+def cg_sync(h):
+    return _check(load().cg_sync(h), allow=(CG_ESTUCK,))
+
+
+def cg_run_logged(h, n_hops, M):
+    R = cg_num_replicas(h)
+    log = np.zeros(R * int(n_hops), HOP_DTYPE)
+    rc = load().cg_run_logged(h, n_hops, M, log.ctypes.data_as(ctypes.POINTER(cg_hop)))
+    _check(rc, allow=(CG_ESTUCK,))
+    return rc, log.reshape(R, int(n_hops))
+
+
+def cg_read_state(h, replica=0, n=True, eps=True, phi=True, counters=True):
+    N = cg_num_sites(h, replica)
+    n_a = np.zeros(N, np.uint8) if n else None
+    e_a = np.zeros(N, np.float64) if eps else None
+    p_a = np.zeros(N, np.float64) if phi else None
+    c = cg_counters() if counters else None
+    _check(load().cg_read_state(h, replica, _ptr(n_a, ctypes.c_uint8), _ptr(e_a, ctypes.c_double),
+                                _ptr(p_a, ctypes.c_double),
+                                ctypes.byref(c) if c is not None else None))
+    return n_a, e_a, p_a, (c.as_dict() if c is not None else None)
+
+
+def cg_write_state(h, replica, n, eps=None, phi=None, counters=None):
+    n = np.ascontiguousarray(n, dtype=np.uint8)
+    eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    c = None if counters is None else cg_counters(**counters)
+    return _check(load().cg_write_state(h, replica, _ptr(n, ctypes.c_uint8),
+                                        _ptr(eps, ctypes.c_double), _ptr(phi, ctypes.c_double),
+                                        ctypes.byref(c) if c is not None else None))
+
+
+def cg_observables(h, replica=0) -> dict:
+    o = cg_obs()
+    _check(load().cg_observables(h, replica, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def cg_refresh(h):
+    return _check(load().cg_refresh(h))
+
+
+def cg_refresh_async(h):
+    return _check(load().cg_refresh_async(h))
+
+
+def cg_microbench(kind, device=0) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().cg_microbench(kind, device, ctypes.byref(out)))
+    return out.value
+
+
+def cg_set_toy_acceptance(h, A0):
+    return _check(load().cg_set_toy_acceptance(h, A0))
+
+
+def cg_debug_philox(ctr, key):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(load().cg_debug_philox(_ptr(ctr, ctypes.c_uint32), _ptr(key, ctypes.c_uint32),
+                                  _ptr(out, ctypes.c_uint32), len(ctr)))
+    return out
+
+
+def cg_debug_exp(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    _check(load().cg_debug_exp(_ptr(x, ctypes.c_double), _ptr(out, ctypes.c_double), len(x)))
+    return out
+
+
+class System:
+    """Owns one libcg handle over R replicas, with device memory and the
+    stream supplied by PyTorch."""
+
+    def __init__(self, reps, precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO,
+                 block_threads=0, max_rounds_per_hop=0, device=0, torch_memory=True,
+                 hop_timeout_ms=0):
+        import torch
+        self.reps = [r if isinstance(r, dict) else r for r in reps]
+        torch.cuda.set_device(device)
+        # a dedicated torch stream: libcg launches on it, callers can record
+        # torch events on it
+        self.stream = torch.cuda.Stream(device)
+        self.opts = opts(precision=precision, refresh_every=refresh_every,
+                         refresh_kind=refresh_kind, block_threads=block_threads,
+                         max_rounds_per_hop=max_rounds_per_hop, device=device,
+                         stream=self.stream.cuda_stream, hop_timeout_ms=hop_timeout_ms)
+        self.workspace = None
+        if torch_memory:
+            nbytes = cg_workspace_bytes(self.reps, self.opts)
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+            self.h = cg_create_batch_ws(self.reps, self.opts, aligned, nbytes + 256 - (aligned - base))
+        else:
+            self.h = cg_create_batch(self.reps, self.opts)
+        self.R = cg_num_replicas(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, n_hops, M):
+        return cg_run(self.h, n_hops, M)
+
+    def run_logged(self, n_hops, M):
+        return cg_run_logged(self.h, n_hops, M)
+
+    def state(self, replica=0):
+        return cg_read_state(self.h, replica)
+
+    def observables(self, replica=0):
+        return cg_observables(self.h, replica)

@@ -1,0 +1,150 @@
+// cg_aux_kernels.cu -- set-up and refresh kernels of libcg.
+//
+//   eps_init:     eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st, the single-
+//                 particle energies defined below Eq. 2, summed over t in
+//                 increasing order with each product rounded before the add,
+//                 so the result is bit-identical to a serial evaluation of the
+//                 same definition.
+//   refresh_fp64: the periodic from-scratch rebuild of binary32 eps in
+//                 binary64: eps_s = phi_s + sum_{t occupied} 1/r_st
+//                 - nu * sum_{t != s} 1/r_st, records max |eps_old - eps_new|.
+//   debug_*:      Philox and the acceptance exponential evaluated on the GPU
+//                 for tests.
+#include "cg_device.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+
+__global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restrict__ rp,
+                                                       int precision)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const DevReplica &R = *rp;
+    const int L = R.L, N = R.N, H1 = R.H1, words = R.words;
+    double *tab = reinterpret_cast<double *>(sm);
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(H1 * H1 * 8));
+    for (int l = threadIdx.x; l < H1 * H1; l += blockDim.x) tab[l] = R.tinv64[l];
+    for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int ys = (int)__umulhi((unsigned)s, R.magicL), xs = s - ys * L;
+    const double c_occ = d_sub(1.0, R.nu), c_emp = d_sub(0.0, R.nu);
+    double acc = 0.0;
+    for (int yt = 0; yt < L; ++yt) {
+        const double *row = tab + fold_axis(ys - yt, L) * H1;
+        const int base = yt * L;
+        for (int xt = 0; xt < L; ++xt) {
+            const int t = base + xt;
+            if (t == s) continue;
+            const double c = ((occ[t >> 5] >> (t & 31)) & 1u) ? c_occ : c_emp;
+            acc = d_add(acc, d_mul(c, row[fold_axis(xs - xt, L)]));
+        }
+    }
+    const double e = d_add(R.phi[s], acc);
+    if (precision == CG_FP64)
+        reinterpret_cast<double *>(R.eps)[s] = e;
+    else
+        reinterpret_cast<float *>(R.eps)[s] = __double2float_rn(e);
+}
+
+cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int H1, int words, int precision,
+                            cudaStream_t st)
+{
+    const int smem = cg_align16(H1 * H1 * 8) + words * 4;
+    cudaError_t e = cudaFuncSetAttribute(eps_init_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e) return e;
+    eps_init_kernel<<<(N + 127) / 128, 128, smem, st>>>(d_rep, precision);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__restrict__ rp)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ unsigned long long s_max;
+    const DevReplica &R = *rp;
+    const int L = R.L, N = R.N, H1 = R.H1, words = R.words;
+    double *tab = reinterpret_cast<double *>(sm);
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(H1 * H1 * 8));
+    for (int l = threadIdx.x; l < H1 * H1; l += blockDim.x) tab[l] = R.tinv64[l];
+    for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
+    if (threadIdx.x == 0) s_max = 0ull;
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double err = 0.0;
+    if (s < N) {
+        const int ys = (int)__umulhi((unsigned)s, R.magicL), xs = s - ys * L;
+        double acc = 0.0;
+        for (int w = 0; w < words; ++w) {
+            unsigned bits = occ[w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int t = w * 32 + b;
+                const int yt = (int)__umulhi((unsigned)t, R.magicL), xt = t - yt * L;
+                acc += tab[fold_axis(ys - yt, L) * H1 + fold_axis(xs - xt, L)];
+            }
+        }
+        const double e = R.phi[s] + (acc + R.negC0nu);
+        float *eps = reinterpret_cast<float *>(R.eps);
+        err = fabs((double)eps[s] - e);
+        eps[s] = __double2float_rn(e);
+    }
+    // block max of the non-negative errors through their bit patterns
+    unsigned long long bits = (unsigned long long)__double_as_longlong(err);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = bits > other ? bits : other;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, bits);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&R.ctr->max_err_bits, s_max);
+        if (blockIdx.x == 0) atomicAdd(&R.ctr->refreshes, 1ull);
+    }
+}
+
+cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int words,
+                                cudaStream_t st)
+{
+    const int smem = cg_align16(H1 * H1 * 8) + words * 4;
+    cudaError_t e = cudaFuncSetAttribute(refresh_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e) return e;
+    refresh_fp64_kernel<<<(N + 255) / 256, 256, smem, st>>>(d_rep);
+    return cudaGetLastError();
+}
+
+__global__ void debug_philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                                    int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t x[4];
+    philox4x32_10(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3], key[2 * t],
+                  key[2 * t + 1], x);
+    for (int w = 0; w < 4; ++w) out[4 * t + w] = x[w];
+}
+
+__global__ void debug_exp_kernel(const double *x, double *out, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = cg_exp_accept(x[t]);
+}
+
+cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
+                                cudaStream_t st)
+{
+    debug_philox_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctr, key, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_exp(const double *x, double *out, int n, cudaStream_t st)
+{
+    debug_exp_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace cg

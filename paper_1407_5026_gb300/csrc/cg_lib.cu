@@ -1,0 +1,833 @@
+// cg_lib.cu -- host side of libcg: parameter checks, tables, disorder and
+// initial state, device memory, launch orchestration and the C ABI of
+// include/cg.h.
+//
+// Set-up follows the model of Eq. 1 on an L x L torus with minimum-image
+// distances (section "Results for the lattice model in two dimensions"):
+//   * folded 1/r table over |dx|, |dy| in [0, L/2], zero at the origin;
+//   * hop vectors: all (dx, dy) with 0 < dx^2 + dy^2 <= r_max^2, dy outer,
+//     dx inner, both ascending; tunnelling weights w = exp(-2r/xi) (Eq. 2),
+//     Z = sum w, integer tower weights floor(2^32 w / Z) and their running
+//     sums (tower sampling of the mixed algorithm);
+//   * Gamma = N Z, the total tunnelling rate; time = attempts / Gamma;
+//   * phi_s = W (u - 1/2) with u = (x0 + 1/2) 2^-32 from Philox counter
+//     (s, 1, 0xFFFFFFFF, replica): site energies uniform on a width-W interval;
+//   * initial random configuration: sites sorted by (x0 of counter
+//     (s, 2, 0xFFFFFFFF, replica), s), the first nu N occupied.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "cg_device.cuh"
+#include "cg_internal.h"
+
+using namespace cg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CG_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(CG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+// exp(x), -745 < x <= 0: Cody-Waite reduction with ln 2 = LN2_HI + LN2_LO and
+// the degree-13 Taylor polynomial, exactly as the device's acceptance
+// exponential but without its cut-off (used for the tunnelling weights).
+double host_exp(double x)
+{
+    const double kd = std::nearbyint(x * 0x1.71547652b82fep+0);
+    const double r = (x - kd * 0x1.62e42ffp-1) - kd * -0x1.718432a1b0e26p-35;
+    static const double inv_fact[14] = {
+        1.0, 1.0, 0x1.0p-1, 0x1.5555555555555p-3, 0x1.5555555555555p-5,
+        0x1.1111111111111p-7, 0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13,
+        0x1.a01a01a01a01ap-16, 0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22,
+        0x1.ae64567f544e4p-26, 0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};
+    double p = inv_fact[13];
+    for (int n = 12; n >= 0; --n) {
+        const double t = p * r;
+        p = t + inv_fact[n];
+    }
+    return std::ldexp(p, (int)kd);
+}
+
+struct Tables {
+    int L = 0, r_max = 0, H1 = 0, V = 0;
+    double xi = 0, Z = 0, C0 = 0;
+    std::vector<double> t64;
+    std::vector<float> t32;
+    std::vector<unsigned> thr;
+    std::vector<int> disp;
+    std::vector<double> tinvd;
+    double *d_t64 = nullptr;
+    float *d_t32 = nullptr;
+    unsigned *d_thr = nullptr;
+    int *d_disp = nullptr;
+    double *d_tinvd = nullptr;
+};
+
+int build_tables(Tables &t, int L, double xi, int r_max)
+{
+    t.L = L; t.xi = xi; t.r_max = r_max; t.H1 = L / 2 + 1;
+    t.t64.assign((size_t)t.H1 * t.H1, 0.0);
+    for (int fy = 0; fy < t.H1; ++fy)
+        for (int fx = 0; fx < t.H1; ++fx)
+            t.t64[(size_t)fy * t.H1 + fx] =
+                (fx == 0 && fy == 0) ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy));
+    t.t32.resize(t.t64.size());
+    for (size_t k = 0; k < t.t64.size(); ++k) t.t32[k] = (float)t.t64[k];
+    // sum_{t != s} 1/r_st is the same for every s: every displacement once
+    double C0 = 0.0;
+    for (int dy = 0; dy < L; ++dy)
+        for (int dx = 0; dx < L; ++dx)
+            C0 += t.t64[(size_t)fold_axis(dy, L) * t.H1 + fold_axis(dx, L)];
+    t.C0 = C0;
+    std::vector<double> w;
+    for (int dy = -r_max; dy <= r_max; ++dy)
+        for (int dx = -r_max; dx <= r_max; ++dx) {
+            const int r2 = dx * dx + dy * dy;
+            if (r2 == 0 || r2 > r_max * r_max) continue;
+            t.disp.push_back((dx & 0xffff) | (dy * 65536));
+            w.push_back(host_exp(-2.0 * std::sqrt((double)r2) / xi));
+            t.tinvd.push_back(t.t64[(size_t)std::abs(dy) * t.H1 + std::abs(dx)]);
+        }
+    t.V = (int)w.size();
+    double Z = 0.0;
+    for (double v : w) Z = Z + v;
+    t.Z = Z;
+    unsigned long long run = 0;
+    for (int k = 0; k < t.V; ++k) {
+        const double f = (w[k] / Z) * 4294967296.0;
+        const unsigned long long Wk = (unsigned long long)std::floor(f);
+        if (Wk == 0)
+            return fail(CG_EINVAL, "a hop vector's tower weight is below 2^-32 "
+                                   "(r_max too large for xi)");
+        run += Wk;
+        t.thr.push_back((unsigned)(run - 1));
+    }
+    return CG_OK;
+}
+
+struct Rep {
+    cg_replica_desc d{};
+    int N = 0, words = 0;
+    Tables *tab = nullptr;
+    void *d_eps = nullptr;
+    unsigned *d_occ = nullptr;
+    double *d_phi = nullptr;
+    DevCounters *d_ctr = nullptr;
+};
+
+struct Group {
+    int L = 0, first = 0, count = 0, threads = 0, smem = 0;
+};
+
+}  // namespace
+
+struct cg_handle {
+    cg_opts opts{};
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<Rep> reps;
+    std::vector<std::unique_ptr<Tables>> tables;
+    std::vector<Group> groups;
+    DevReplica *d_reps = nullptr;
+    int *d_index = nullptr;
+    std::vector<DevReplica> h_reps;
+    // memory: cudaMalloc'd pointers, or a caller workspace
+    bool ws_mode = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0, ws_used = 0;
+    std::vector<void *> allocs;
+    // run state
+    unsigned long long hops_since_refresh = 0;
+    double max_err_run = 0.0;
+    int toy = 0;
+    double toy_A0 = 0.0;
+    cg_hop *d_log = nullptr;
+    bool pending = false;
+};
+
+namespace {
+
+int dalloc(cg_handle *h, void **p, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (h->ws_mode) {
+        if (h->ws_used + bytes > h->ws_bytes)
+            return fail(CG_ENOMEM, "workspace too small");
+        *p = h->ws + h->ws_used;
+        h->ws_used += bytes;
+        return CG_OK;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(CG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    return CG_OK;
+}
+
+int check_desc(const cg_replica_desc &d)
+{
+    if (d.L < 4 || d.L > 1024 || (d.L & 1))
+        return fail(CG_EINVAL, "L must be even and in [4, 1024]");
+    const double N = (double)d.L * d.L;
+    if (!(d.nu > 0.0 && d.nu < 1.0)) return fail(CG_EINVAL, "nu must be in (0, 1)");
+    if (std::fabs(d.nu * N - std::floor(d.nu * N + 0.5)) > 1e-9)
+        return fail(CG_EINVAL, "nu * N must be an integer");
+    if (d.r_max < 1 || 2 * d.r_max >= d.L) return fail(CG_EINVAL, "need 1 <= r_max < L/2");
+    if (!(d.xi > 0.0) || !std::isfinite(d.xi)) return fail(CG_EINVAL, "xi must be > 0");
+    if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(CG_EINVAL, "T must be > 0");
+    if (!(d.W >= 0.0) || !std::isfinite(d.W)) return fail(CG_EINVAL, "W must be >= 0");
+    if (!std::isfinite(d.E)) return fail(CG_EINVAL, "E must be finite");
+    return CG_OK;
+}
+
+int persistent_smem(const Rep &r, int precision)
+{
+    const int rb = precision == CG_FP64 ? 8 : 4;
+    return smem_layout(r.N, r.tab->H1, r.tab->V, r.words, rb).total;
+}
+
+int choose_threads(const cg_opts &o, int L, int smem)
+{
+    int t = o.block_threads;
+    if (t == 0) t = (o.precision == CG_FP64 || smem > 110 * 1024) ? 1024 : 512;
+    while (t < L && t < 1024) t *= 2;
+    return t;
+}
+
+unsigned magic_for(int L) { return (unsigned)(4294967296ull / (unsigned long long)L + 1ull); }
+
+void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
+{
+    std::memset(&dr, 0, sizeof(dr));
+    const Tables &t = *r.tab;
+    dr.L = r.d.L; dr.N = r.N; dr.H1 = t.H1; dr.V = t.V; dr.words = r.words;
+    dr.magicL = magic_for(r.d.L);
+    dr.key0 = (unsigned)r.d.seed;
+    dr.key1 = (unsigned)(r.d.seed >> 32);
+    dr.replica = r.d.replica;
+    dr.nu = r.d.nu; dr.T = r.d.T; dr.E = r.d.E;
+    dr.negC0nu = -r.d.nu * t.C0;
+    dr.tinv64 = t.d_t64; dr.tinv32 = t.d_t32; dr.thr = t.d_thr; dr.disp = t.d_disp;
+    dr.tinvd = t.d_tinvd;
+    dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
+    dr.log = log;
+    (void)precision;
+}
+
+void host_setup_state(const cg_replica_desc &d, std::vector<double> &phi,
+                      std::vector<unsigned char> &n)
+{
+    const int N = d.L * d.L;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    phi.resize(N);
+    n.assign(N, 0);
+    std::vector<std::pair<uint32_t, uint32_t>> keys(N);
+    for (int s = 0; s < N; ++s) {
+        uint32_t x[4];
+        philox4x32_10((uint32_t)s, 1u, 0xFFFFFFFFu, d.replica, k0, k1, x);
+        const double u = ((double)x[0] + 0.5) * 0x1p-32;
+        phi[s] = d.W * (u - 0.5);
+        philox4x32_10((uint32_t)s, 2u, 0xFFFFFFFFu, d.replica, k0, k1, x);
+        keys[s] = {x[0], (uint32_t)s};
+    }
+    std::sort(keys.begin(), keys.end());
+    const int nocc = (int)std::floor(d.nu * N + 0.5);
+    for (int s = 0; s < nocc; ++s) n[keys[s].second] = 1;
+}
+
+std::vector<unsigned> pack_bits(const unsigned char *n, int N)
+{
+    std::vector<unsigned> w((N + 31) / 32, 0u);
+    for (int s = 0; s < N; ++s)
+        if (n[s]) w[s >> 5] |= 1u << (s & 31);
+    return w;
+}
+
+int replica_index_ok(const cg_handle *h, int r)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (r < 0 || r >= (int)h->reps.size()) return fail(CG_EINVAL, "replica out of range");
+    return CG_OK;
+}
+
+// Energy of Eq. 1 (field term with x in [0, L)) from eps:
+// H = sum n phi + 1/2 sum (n - nu)(eps - phi) - E sum n x.
+double energy_from_eps(const cg_replica_desc &d, const unsigned char *n, const double *eps,
+                       const double *phi, long long *P_out)
+{
+    const int N = d.L * d.L;
+    double h1 = 0.0, h2 = 0.0;
+    long long P = 0;
+    for (int s = 0; s < N; ++s) {
+        h1 += n[s] ? phi[s] : 0.0;
+        h2 += ((double)n[s] - d.nu) * (eps[s] - phi[s]);
+        if (n[s]) P += s % d.L;
+    }
+    *P_out = P;
+    return h1 + 0.5 * h2 - d.E * (double)P;
+}
+
+int read_eps_host(cg_handle *h, const Rep &r, double *out)
+{
+    if (h->opts.precision == CG_FP64) {
+        CG_CUDA(cudaMemcpyAsync(out, r.d_eps, sizeof(double) * r.N, cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+    } else {
+        std::vector<float> f(r.N);
+        CG_CUDA(cudaMemcpyAsync(f.data(), r.d_eps, sizeof(float) * r.N, cudaMemcpyDeviceToHost,
+                                h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+        for (int s = 0; s < r.N; ++s) out[s] = (double)f[s];
+    }
+    return CG_OK;
+}
+
+// Upload occupation (+phi), rebuild or set eps, set or recompute counters.
+int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
+               const double *phi, const cg_counters *c)
+{
+    Rep &r = h->reps[ri];
+    const std::vector<unsigned> words = pack_bits(n, r.N);
+    CG_CUDA(cudaMemcpyAsync(r.d_occ, words.data(), 4 * words.size(), cudaMemcpyHostToDevice, h->st));
+    if (phi)
+        CG_CUDA(cudaMemcpyAsync(r.d_phi, phi, sizeof(double) * r.N, cudaMemcpyHostToDevice, h->st));
+    if (eps) {
+        if (h->opts.precision == CG_FP64) {
+            CG_CUDA(cudaMemcpyAsync(r.d_eps, eps, sizeof(double) * r.N, cudaMemcpyHostToDevice,
+                                    h->st));
+        } else {
+            std::vector<float> f(r.N);
+            for (int s = 0; s < r.N; ++s) f[s] = (float)eps[s];
+            CG_CUDA(cudaMemcpyAsync(r.d_eps, f.data(), sizeof(float) * r.N, cudaMemcpyHostToDevice,
+                                    h->st));
+            CG_CUDA(cudaStreamSynchronize(h->st));
+        }
+    } else {
+        CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, r.tab->H1, r.words, h->opts.precision, h->st));
+    }
+    DevCounters dc;
+    std::memset(&dc, 0, sizeof(dc));
+    if (c) {
+        dc.rounds = c->rounds; dc.hops = c->hops; dc.attempts = c->attempts;
+        dc.evaluated = c->evaluated; dc.P = c->P; dc.energy = c->energy;
+    } else {
+        std::vector<double> e(r.N), ph(r.N);
+        int rc = read_eps_host(h, r, e.data());
+        if (rc) return rc;
+        CG_CUDA(cudaMemcpyAsync(ph.data(), r.d_phi, sizeof(double) * r.N, cudaMemcpyDeviceToHost,
+                                h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+        long long P = 0;
+        dc.energy = energy_from_eps(r.d, n, e.data(), ph.data(), &P);
+        dc.P = P;
+    }
+    CG_CUDA(cudaMemcpyAsync(r.d_ctr, &dc, sizeof(dc), cudaMemcpyHostToDevice, h->st));
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    return CG_OK;
+}
+
+size_t plan_bytes(int R, const cg_replica_desc *reps, int precision)
+{
+    // mirrors the allocations of create_impl (each rounded up to 256 bytes)
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t total = up(sizeof(DevReplica) * (size_t)R) + up(sizeof(int) * (size_t)R);
+    std::vector<std::tuple<int, int, double>> seen;
+    for (int k = 0; k < R; ++k) {
+        const cg_replica_desc &d = reps[k];
+        const size_t N = (size_t)d.L * d.L, words = (N + 31) / 32;
+        total += up(N * (precision == CG_FP64 ? 8 : 4)) + up(words * 4) + up(N * 8) +
+                 up(sizeof(DevCounters));
+        auto key = std::make_tuple(d.L, d.r_max, d.xi);
+        if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
+            seen.push_back(key);
+            const size_t H1 = d.L / 2 + 1;
+            size_t V = 0;
+            for (int dy = -d.r_max; dy <= d.r_max; ++dy)
+                for (int dx = -d.r_max; dx <= d.r_max; ++dx) {
+                    const int r2 = dx * dx + dy * dy;
+                    if (r2 > 0 && r2 <= d.r_max * d.r_max) ++V;
+                }
+            total += up(H1 * H1 * 8) + up(H1 * H1 * 4) + up(V * 4) + up(V * 4) + up(V * 8);
+        }
+    }
+    return total;
+}
+
+cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, void *ws,
+                       size_t ws_bytes)
+{
+    if (R <= 0 || !reps) { fail(CG_EINVAL, "need R >= 1 replica descriptors"); return nullptr; }
+    cg_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != CG_FP64 && o.precision != CG_FP32) {
+        fail(CG_EINVAL, "precision must be CG_FP64 or CG_FP32");
+        return nullptr;
+    }
+    if (o.block_threads && (o.block_threads != 256 && o.block_threads != 512 &&
+                            o.block_threads != 1024)) {
+        fail(CG_EINVAL, "block_threads must be 0, 256, 512 or 1024");
+        return nullptr;
+    }
+    if (o.max_rounds_per_hop == 0) o.max_rounds_per_hop = 1ull << 32;
+    for (int k = 0; k < R; ++k)
+        if (check_desc(reps[k]) != CG_OK) return nullptr;
+
+    std::unique_ptr<cg_handle> h(new cg_handle());
+    h->opts = o;
+    h->device = o.device;
+    if (cudaSetDevice(o.device) != cudaSuccess) {
+        fail(CG_ECUDA, "cudaSetDevice failed");
+        return nullptr;
+    }
+    if (ws) {
+        if (((uintptr_t)ws & 255) != 0) { fail(CG_EINVAL, "workspace must be 256-byte aligned"); return nullptr; }
+        h->ws_mode = true;
+        h->ws = (char *)ws;
+        h->ws_bytes = ws_bytes;
+    }
+    if (o.stream) {
+        h->st = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(CG_ECUDA, "cudaStreamCreate failed");
+            return nullptr;
+        }
+        h->own_stream = true;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, o.device);
+
+    auto destroy_partial = [&]() { cg_destroy(h.release()); };
+
+    // tables, shared by replicas of equal (L, r_max, xi)
+    h->reps.resize(R);
+    for (int k = 0; k < R; ++k) {
+        Rep &r = h->reps[k];
+        r.d = reps[k];
+        r.N = r.d.L * r.d.L;
+        r.words = (r.N + 31) / 32;
+        for (auto &t : h->tables)
+            if (t->L == r.d.L && t->r_max == r.d.r_max && t->xi == r.d.xi) r.tab = t.get();
+        if (!r.tab) {
+            std::unique_ptr<Tables> t(new Tables());
+            if (build_tables(*t, r.d.L, r.d.xi, r.d.r_max) != CG_OK) { destroy_partial(); return nullptr; }
+            r.tab = t.get();
+            h->tables.push_back(std::move(t));
+        }
+        const int smem = persistent_smem(r, o.precision);
+        if (smem + 1024 > optin) {
+            fail(CG_EINVAL, "replica does not fit one CTA's shared memory (L too large for "
+                            "this precision)");
+            destroy_partial();
+            return nullptr;
+        }
+    }
+    // device memory
+    if (dalloc(h.get(), (void **)&h->d_reps, sizeof(DevReplica) * R) ||
+        dalloc(h.get(), (void **)&h->d_index, sizeof(int) * R)) { destroy_partial(); return nullptr; }
+    for (auto &t : h->tables) {
+        if (dalloc(h.get(), (void **)&t->d_t64, t->t64.size() * 8) ||
+            dalloc(h.get(), (void **)&t->d_t32, t->t32.size() * 4) ||
+            dalloc(h.get(), (void **)&t->d_thr, t->thr.size() * 4) ||
+            dalloc(h.get(), (void **)&t->d_disp, t->disp.size() * 4) ||
+            dalloc(h.get(), (void **)&t->d_tinvd, t->tinvd.size() * 8)) { destroy_partial(); return nullptr; }
+        cudaMemcpyAsync(t->d_t64, t->t64.data(), t->t64.size() * 8, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(t->d_t32, t->t32.data(), t->t32.size() * 4, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(t->d_thr, t->thr.data(), t->thr.size() * 4, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(t->d_disp, t->disp.data(), t->disp.size() * 4, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(t->d_tinvd, t->tinvd.data(), t->tinvd.size() * 8, cudaMemcpyHostToDevice, h->st);
+    }
+    const int rb = o.precision == CG_FP64 ? 8 : 4;
+    for (auto &r : h->reps) {
+        if (dalloc(h.get(), &r.d_eps, (size_t)r.N * rb) ||
+            dalloc(h.get(), (void **)&r.d_occ, (size_t)r.words * 4) ||
+            dalloc(h.get(), (void **)&r.d_phi, (size_t)r.N * 8) ||
+            dalloc(h.get(), (void **)&r.d_ctr, sizeof(DevCounters))) { destroy_partial(); return nullptr; }
+    }
+    // groups of equal L (one launch each), replica order kept inside a group
+    std::vector<int> order(R);
+    for (int k = 0; k < R; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return h->reps[a].d.L < h->reps[b].d.L; });
+    for (int k = 0; k < R;) {
+        Group g;
+        g.L = h->reps[order[k]].d.L;
+        g.first = k;
+        int smem = 0;
+        while (k < R && h->reps[order[k]].d.L == g.L) {
+            smem = std::max(smem, persistent_smem(h->reps[order[k]], o.precision));
+            ++k;
+        }
+        g.count = k - g.first;
+        g.smem = smem;
+        g.threads = choose_threads(o, g.L, smem);
+        h->groups.push_back(g);
+    }
+    h->h_reps.resize(R);
+    for (int k = 0; k < R; ++k) fill_dev(h->reps[k], o.precision, h->h_reps[k], nullptr);
+    if (cudaMemcpyAsync(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
+                        cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_index, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
+                        h->st) != cudaSuccess) {
+        fail(CG_ECUDA, "upload of replica descriptors failed");
+        destroy_partial();
+        return nullptr;
+    }
+    if (set_pr_smem_limit(o.precision, optin - 1024) != cudaSuccess) {
+        fail(CG_ECUDA, "cudaFuncSetAttribute(max dynamic shared memory) failed");
+        destroy_partial();
+        return nullptr;
+    }
+    // disorder, initial occupation, eps from scratch, energy
+    for (int k = 0; k < R; ++k) {
+        std::vector<double> phi;
+        std::vector<unsigned char> n;
+        host_setup_state(h->reps[k].d, phi, n);
+        if (load_state(h.get(), k, n.data(), nullptr, phi.data(), nullptr) != CG_OK) {
+            destroy_partial();
+            return nullptr;
+        }
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+        fail(CG_ECUDA, "set-up kernels failed");
+        destroy_partial();
+        return nullptr;
+    }
+    return h.release();
+}
+
+int launch_segment(cg_handle *h, unsigned long long hops, unsigned M, unsigned long long log_off)
+{
+    RunArgs a{};
+    a.n_hops = hops;
+    a.M = M;
+    a.max_rounds = h->opts.max_rounds_per_hop;
+    a.log_offset = log_off;
+    a.hop_timeout_ns = 1000000ull * (h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u);
+    a.toy = h->toy;
+    a.toy_A0 = h->toy_A0;
+    for (const Group &g : h->groups)
+        CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
+                                     g.threads, g.smem, a, h->st));
+    return CG_OK;
+}
+
+int refresh_all(cg_handle *h)
+{
+    if (h->opts.precision != CG_FP32) {
+        for (size_t k = 0; k < h->reps.size(); ++k) {
+            const Rep &r = h->reps[k];
+            CG_CUDA(launch_eps_init(h->d_reps + k, r.N, r.tab->H1, r.words, CG_FP64, h->st));
+        }
+        return CG_OK;
+    }
+    for (size_t k = 0; k < h->reps.size(); ++k) {
+        const Rep &r = h->reps[k];
+        CG_CUDA(cudaMemsetAsync(&r.d_ctr->max_err_bits, 0, 8, h->st));
+        CG_CUDA(launch_refresh_fp64(h->d_reps + k, r.N, r.tab->H1, r.words, h->st));
+    }
+    return CG_OK;
+}
+
+int enqueue_run(cg_handle *h, unsigned long long n_hops, unsigned M, bool logged)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (M < 1 || M > (1u << 24)) return fail(CG_EINVAL, "M must be in [1, 2^24]");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    const bool refresh = h->opts.precision == CG_FP32 && h->opts.refresh_every > 0;
+    unsigned long long done = 0;
+    while (done < n_hops) {
+        unsigned long long seg = n_hops - done;
+        if (refresh) seg = std::min(seg, h->opts.refresh_every - h->hops_since_refresh);
+        int rc = launch_segment(h, seg, M, logged ? done : 0);
+        if (rc) return rc;
+        done += seg;
+        if (refresh) {
+            h->hops_since_refresh += seg;
+            if (h->hops_since_refresh == h->opts.refresh_every) {
+                rc = refresh_all(h);
+                if (rc) return rc;
+                h->hops_since_refresh = 0;
+            }
+        }
+    }
+    h->pending = true;
+    return CG_OK;
+}
+
+int finish_run(cg_handle *h)
+{
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    h->pending = false;
+    std::vector<DevCounters> c(h->reps.size());
+    for (size_t k = 0; k < h->reps.size(); ++k)
+        CG_CUDA(cudaMemcpyAsync(&c[k], h->reps[k].d_ctr, sizeof(DevCounters),
+                                cudaMemcpyDeviceToHost, h->st));
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    int rc = CG_OK;
+    for (size_t k = 0; k < c.size(); ++k) {
+        double e;
+        std::memcpy(&e, &c[k].max_err_bits, 8);
+        h->max_err_run = std::max(h->max_err_run, e);
+        if (c[k].status == CG_ESTUCK) rc = fail(CG_ESTUCK, "a replica reached max rounds per hop");
+        if (c[k].status == CG_ETIMEOUT)
+            rc = fail(CG_ETIMEOUT, "a hop exceeded the device time limit");
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cg_version(void) { return "cg-pr 0.1 (sm_103a)"; }
+
+const char *cg_last_error(void) { return g_err.c_str(); }
+
+cg_handle *cg_create(int L, double nu, double W, double xi, int r_max, double T, double E,
+                     uint64_t seed)
+{
+    cg_replica_desc d{};
+    d.L = L; d.nu = nu; d.W = W; d.xi = xi; d.r_max = r_max; d.T = T; d.E = E;
+    d.seed = seed; d.replica = 0;
+    return create_impl(1, &d, nullptr, nullptr, 0);
+}
+
+cg_handle *cg_create_batch(int R, const cg_replica_desc *reps, const cg_opts *opts)
+{
+    return create_impl(R, reps, opts, nullptr, 0);
+}
+
+size_t cg_workspace_bytes(int R, const cg_replica_desc *reps, const cg_opts *opts)
+{
+    if (R <= 0 || !reps) return 0;
+    return plan_bytes(R, reps, opts ? opts->precision : CG_FP64);
+}
+
+cg_handle *cg_create_batch_ws(int R, const cg_replica_desc *reps, const cg_opts *opts,
+                              void *workspace, size_t ws_bytes)
+{
+    if (!workspace) { fail(CG_EINVAL, "null workspace"); return nullptr; }
+    return create_impl(R, reps, opts, workspace, ws_bytes);
+}
+
+void cg_destroy(cg_handle *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->d_log) cudaFree(h->d_log);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+int cg_num_replicas(const cg_handle *h) { return h ? (int)h->reps.size() : 0; }
+
+int cg_num_sites(const cg_handle *h, int replica)
+{
+    if (!h || replica < 0 || replica >= (int)h->reps.size()) return 0;
+    return h->reps[replica].N;
+}
+
+int cg_run_async(cg_handle *h, uint64_t n_hops, uint32_t M)
+{
+    return enqueue_run(h, n_hops, M, false);
+}
+
+int cg_sync(cg_handle *h)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    return finish_run(h);
+}
+
+int cg_run(cg_handle *h, uint64_t n_hops, uint32_t M)
+{
+    int rc = enqueue_run(h, n_hops, M, false);
+    if (rc) return rc;
+    return finish_run(h);
+}
+
+int cg_run_logged(cg_handle *h, uint64_t n_hops, uint32_t M, cg_hop *log_host)
+{
+    if (!h || !log_host) return fail(CG_EINVAL, "null argument");
+    const size_t R = h->reps.size();
+    const size_t bytes = sizeof(cg_hop) * R * (size_t)n_hops;
+    if (h->d_log) { cudaFree(h->d_log); h->d_log = nullptr; }
+    if (bytes) CG_CUDA(cudaMalloc((void **)&h->d_log, bytes));
+    // point every replica's log at its slice
+    for (size_t k = 0; k < R; ++k) h->h_reps[k].log = h->d_log + k * n_hops;
+    CG_CUDA(cudaMemcpyAsync(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
+                            cudaMemcpyHostToDevice, h->st));
+    int rc = enqueue_run(h, n_hops, M, true);
+    int rc2 = rc ? rc : finish_run(h);
+    for (size_t k = 0; k < R; ++k) h->h_reps[k].log = nullptr;
+    CG_CUDA(cudaMemcpyAsync(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
+                            cudaMemcpyHostToDevice, h->st));
+    if (bytes) {
+        CG_CUDA(cudaMemcpyAsync(log_host, h->d_log, bytes, cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+    }
+    return rc2;
+}
+
+int cg_read_state(cg_handle *h, int replica, uint8_t *n_host, double *eps_host,
+                  double *phi_host, cg_counters *c_host)
+{
+    int rc = replica_index_ok(h, replica);
+    if (rc) return rc;
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
+    const Rep &r = h->reps[replica];
+    if (n_host) {
+        std::vector<unsigned> w(r.words);
+        CG_CUDA(cudaMemcpyAsync(w.data(), r.d_occ, 4 * w.size(), cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+        for (int s = 0; s < r.N; ++s) n_host[s] = (w[s >> 5] >> (s & 31)) & 1u;
+    }
+    if (eps_host && (rc = read_eps_host(h, r, eps_host))) return rc;
+    if (phi_host) {
+        CG_CUDA(cudaMemcpyAsync(phi_host, r.d_phi, 8 * (size_t)r.N, cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+    }
+    if (c_host) {
+        DevCounters dc;
+        CG_CUDA(cudaMemcpyAsync(&dc, r.d_ctr, sizeof(dc), cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+        c_host->rounds = dc.rounds; c_host->hops = dc.hops; c_host->attempts = dc.attempts;
+        c_host->evaluated = dc.evaluated; c_host->P = dc.P; c_host->energy = dc.energy;
+    }
+    return CG_OK;
+}
+
+int cg_write_state(cg_handle *h, int replica, const uint8_t *n_host, const double *eps_host,
+                   const double *phi_host, const cg_counters *c_host)
+{
+    int rc = replica_index_ok(h, replica);
+    if (rc) return rc;
+    if (!n_host) return fail(CG_EINVAL, "n_host is required");
+    const Rep &r = h->reps[replica];
+    long long cnt = 0;
+    for (int s = 0; s < r.N; ++s) {
+        if (n_host[s] > 1) return fail(CG_ESTATE, "occupations must be 0 or 1");
+        cnt += n_host[s];
+    }
+    if (cnt != (long long)std::floor(r.d.nu * r.N + 0.5))
+        return fail(CG_ESTATE, "occupation count differs from nu * N");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
+    return load_state(h, replica, n_host, eps_host, phi_host, c_host);
+}
+
+int cg_observables(cg_handle *h, int replica, cg_obs *out)
+{
+    int rc = replica_index_ok(h, replica);
+    if (rc) return rc;
+    if (!out) return fail(CG_EINVAL, "null output");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
+    const Rep &r = h->reps[replica];
+    DevCounters dc;
+    CG_CUDA(cudaMemcpyAsync(&dc, r.d_ctr, sizeof(dc), cudaMemcpyDeviceToHost, h->st));
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    std::memset(out, 0, sizeof(*out));
+    out->c.rounds = dc.rounds; out->c.hops = dc.hops; out->c.attempts = dc.attempts;
+    out->c.evaluated = dc.evaluated; out->c.P = dc.P; out->c.energy = dc.energy;
+    out->Gamma = (double)r.N * r.tab->Z;
+    out->time = (double)dc.attempts / out->Gamma;
+    out->acceptance = dc.attempts ? (double)dc.hops / (double)dc.attempts : 0.0;
+    out->energy_per_site = dc.energy / (double)r.N;
+    std::memcpy(&out->max_eps_err_last_refresh, &dc.max_err_bits, 8);
+    out->refreshes = dc.refreshes;
+    out->cycles_reject = dc.cycles_reject;
+    out->cycles_update = dc.cycles_update;
+    return CG_OK;
+}
+
+int cg_refresh(cg_handle *h)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    int rc = refresh_all(h);
+    if (rc) return rc;
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    return CG_OK;
+}
+
+int cg_refresh_async(cg_handle *h)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    int rc = refresh_all(h);
+    if (rc) return rc;
+    h->pending = true;
+    return CG_OK;
+}
+
+int cg_microbench(int kind, int device, double *result)
+{
+    if (!result || kind < 0 || kind > 2) return fail(CG_EINVAL, "bad microbenchmark kind");
+    int rc = microbench(kind, device, result);
+    if (rc) return fail(rc, "microbenchmark failed");
+    return CG_OK;
+}
+
+int cg_set_toy_acceptance(cg_handle *h, double A0)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (A0 < 0) { h->toy = 0; h->toy_A0 = 0; return CG_OK; }
+    if (!(A0 <= 1.0)) return fail(CG_EINVAL, "A0 must be in [0, 1]");
+    h->toy = 1;
+    h->toy_A0 = A0;
+    return CG_OK;
+}
+
+int cg_debug_philox(const uint32_t *ctr_host, const uint32_t *key_host, uint32_t *out_host,
+                    int n)
+{
+    if (n <= 0 || !ctr_host || !key_host || !out_host) return fail(CG_EINVAL, "bad arguments");
+    uint32_t *d = nullptr;
+    CG_CUDA(cudaMalloc((void **)&d, sizeof(uint32_t) * 10 * (size_t)n));
+    uint32_t *dc = d, *dk = d + 4 * (size_t)n, *dout = d + 6 * (size_t)n;
+    cudaMemcpy(dc, ctr_host, 16 * (size_t)n, cudaMemcpyHostToDevice);
+    cudaMemcpy(dk, key_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    cudaError_t e = launch_debug_philox(dc, dk, dout, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, dout, 16 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
+    return CG_OK;
+}
+
+int cg_debug_exp(const double *x_host, double *out_host, int n)
+{
+    if (n <= 0 || !x_host || !out_host) return fail(CG_EINVAL, "bad arguments");
+    double *d = nullptr;
+    CG_CUDA(cudaMalloc((void **)&d, 16 * (size_t)n));
+    cudaMemcpy(d, x_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    cudaError_t e = launch_debug_exp(d, d + n, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d + n, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
+    return CG_OK;
+}
+
+}  // extern "C"

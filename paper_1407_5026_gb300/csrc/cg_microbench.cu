@@ -1,0 +1,114 @@
+// cg_microbench.cu -- peak rates that bound the eps update, measured on the
+// GPU the library runs on (no vendor figure is assumed):
+//   kind 0  aggregate shared-memory bandwidth (bytes/s) of a read-modify-write
+//           stream of 32-bit words, the access pattern of the binary32 eps
+//           update (each warp touches 32 consecutive words per instruction);
+//   kind 1  aggregate binary64 add rate (adds/s), which bounds the binary64
+//           eps update (two adds per site and hop);
+//   kind 2  aggregate shared-memory bandwidth (bytes/s) of the same stream with
+//           64-bit words (the binary64 eps update's pattern).
+#include <cuda_runtime.h>
+
+#include "cg_internal.h"
+
+namespace cg {
+
+template <typename T>
+__global__ void __launch_bounds__(1024) smem_rmw_kernel(int iters, T *sink)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    // volatile: every load and store is issued (no promotion to registers)
+    volatile T *buf = reinterpret_cast<volatile T *>(sm);
+    const int n = 16384;   // words per CTA buffer
+    for (int k = threadIdx.x; k < n; k += blockDim.x) buf[k] = (T)k;
+    __syncthreads();
+    T acc = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll 4
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const T v = buf[k];
+            buf[k] = v + (T)1;
+            acc += v;
+        }
+    }
+    if (acc == (T)-1) sink[0] = acc;   // never true; keeps the loop alive
+}
+
+__global__ void __launch_bounds__(256) dadd_kernel(int iters, double seed, double *sink)
+{
+    double a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const double b = 1e-300;
+    for (int it = 0; it < iters; ++it) {
+        a0 = __dadd_rn(a0, b); a1 = __dadd_rn(a1, b); a2 = __dadd_rn(a2, b); a3 = __dadd_rn(a3, b);
+        a4 = __dadd_rn(a4, b); a5 = __dadd_rn(a5, b); a6 = __dadd_rn(a6, b); a7 = __dadd_rn(a7, b);
+    }
+    const double s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s == -1.0) sink[0] = s;
+}
+
+static double time_ms(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return (double)ms;
+}
+
+int microbench(int kind, int device, double *result)
+{
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    void *sink = nullptr;
+    if (cudaMalloc(&sink, 64) != cudaSuccess) return CG_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    cudaError_t err = cudaSuccess;
+    if (kind == 0 || kind == 2) {
+        const int word = kind == 0 ? 4 : 8;
+        const int smem = 16384 * word;
+        const int iters = 200, blocks = 2 * sms;
+        if (kind == 0)
+            err = cudaFuncSetAttribute(smem_rmw_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        else
+            err = cudaFuncSetAttribute(smem_rmw_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            cudaEventRecord(e0);
+            if (kind == 0)
+                smem_rmw_kernel<float><<<blocks, 1024, smem>>>(iters, (float *)sink);
+            else
+                smem_rmw_kernel<double><<<blocks, 1024, smem>>>(iters, (double *)sink);
+            cudaEventRecord(e1);
+            err = cudaEventSynchronize(e1);
+            const double bytes = 2.0 * word * 16384.0 * iters * blocks;   // load + store
+            const double rate = bytes / (time_ms(e0, e1) * 1e-3);
+            if (rep > 0 && rate > best) best = rate;
+        }
+    } else if (kind == 1) {
+        const int iters = 4096, blocks = 8 * sms;
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            cudaEventRecord(e0);
+            dadd_kernel<<<blocks, 256>>>(iters, 1.0, (double *)sink);
+            cudaEventRecord(e1);
+            err = cudaEventSynchronize(e1);
+            const double adds = 8.0 * iters * 256.0 * blocks;
+            const double rate = adds / (time_ms(e0, e1) * 1e-3);
+            if (rep > 0 && rate > best) best = rate;
+        }
+    } else {
+        err = cudaErrorInvalidValue;
+    }
+    if (err == cudaSuccess) err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess) return CG_ECUDA;
+    *result = best;
+    return CG_OK;
+}
+
+}  // namespace cg

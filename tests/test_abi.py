@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports
+every function include/cg.h declares, and rejects bad parameters on the host
+(before any device call)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libcg():
+    from paper_1407_5026_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(cg_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("cg_create", "cg_run", "cg_read_state", "cg_observables",
+                     "cg_write_state", "cg_destroy", "cg_create_batch", "cg_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libcg):
+    for name in _declared():
+        assert hasattr(libcg, name), name
+    from paper_1407_5026_gb300 import binding
+    assert sorted(binding.EXPORTED) == _declared()
+
+
+def test_binding_structs_match_the_c_layout(libcg, tmp_path):
+    # compile the header with the C compiler and compare sizes and offsets
+    from paper_1407_5026_gb300 import binding as B
+    structs = {"cg_replica_desc": B.cg_replica_desc, "cg_opts": B.cg_opts,
+               "cg_counters": B.cg_counters, "cg_obs": B.cg_obs, "cg_hop": B.cg_hop}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cg.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.strip().splitlines():
+        cname, field, val = line.split()
+        py = structs[cname]
+        want = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert int(val) == want, (cname, field)
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(L=15), "even"), (dict(L=2), "even"), (dict(nu=0.0), "nu"),
+    (dict(L=6, nu=0.3), "integer"), (dict(r_max=8), "r_max"), (dict(xi=0.0), "xi"),
+    (dict(T=0.0), "T must"), (dict(W=-1.0), "W must"), (dict(E=float("inf")), "E must"),
+])
+def test_create_rejects_bad_parameters_on_host(libcg, bad, msg):
+    from paper_1407_5026_gb300 import binding as B
+    p = dict(L=16, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0)
+    p.update(bad)
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create(p["L"], p["nu"], p["W"], p["xi"], p["r_max"], p["T"], p["E"], p["seed"])
+    assert msg in str(ei.value)
+
+
+def test_workspace_plan_counts_every_buffer(libcg):
+    from paper_1407_5026_gb300 import binding as B
+    reps = [B.desc(L=16), B.desc(L=16, seed=1), B.desc(L=32, r_max=6)]
+    b64 = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP64))
+    b32 = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32))
+    # eps shrinks by 4 bytes per site in binary32 (each buffer 256-aligned)
+    assert b64 - b32 == 2 * 256 * 4 + 1024 * 4
+    assert b64 % 256 == 0
