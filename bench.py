@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the parallel-rejection KMC hot path on one node.
+
+Metric: accepted hops/s (and serial-equivalent attempts/s) of the L=128
+(N=16384), T=0.01 lattice Coulomb glass (nu=1/2, phi ~ U[-1,1], xi=1,
+r_max=8, E=0.005), binary32 eps with a binary64 refresh every 1024 hops, R
+disorder replicas per GPU in one persistent launch; the plain binary64 form of
+the same workload (one replica) is measured beside it.
+
+A step: every replica executes 1024 hops (one refresh period: proposals,
+acceptance, lowest accepting label, commit, eps update) and then the eps
+refresh.  Inputs (tables, disorder, initial random configuration) are built
+once; the timed region starts with the state resident in device memory.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+For N > 1 launch with torch.distributed.run; ranks run disjoint replica sets
+(replicas only, no collective on the data path).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "accepted hops/s & equiv. attempts/s at L=128 T=0.01, FP32-batched vs FP64 form"
+WORKLOAD = dict(L=128, nu=0.5, W=2.0, xi=1.0, r_max=8, T=0.01, E=0.005)
+HOPS_PER_STEP = 1024          # one refresh period
+L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--replicas", type=int, default=0, help="per GPU; 0 = 2 per SM")
+    ap.add_argument("--M", type=int, default=4096)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--fp64-hops", type=int, default=2000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def replicas_for(rank, R):
+    from paper_1407_5026_gb300.workloads import Replica
+    base = rank * R
+    return [Replica(seed=base + k, replica=base + k, **WORKLOAD).as_dict() for k in range(R)]
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# --------------------------------------------------------------------------
+
+def _oracle_chain(seed):
+    import oracle
+    p = dict(WORKLOAD)
+    return oracle.Chain(p["L"], nu=p["nu"], W=p["W"], xi=p["xi"], r_max=p["r_max"],
+                        T=p["T"], E=p["E"], seed=seed, replica=seed)
+
+
+def cpu_baseline(seconds, M):
+    """The oracle as it stands, one chain on one core, bounded by time."""
+    ch = _oracle_chain(0)
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        ch.run(16, M)
+    dt = time.perf_counter() - t0
+    c = ch.counters()
+    return {"value": c["hops"] / dt, "unit": "hops/s", "cores": 1, "kind": "oracle",
+            "attempts_per_s": c["attempts"] / dt,
+            "sample": (f"replica seed 0 of the L=128 T=0.01 workload, hops 0..{c['hops']} from "
+                       f"its random initial configuration, M={M}, {dt:.1f} s, binary64")}
+
+
+_worker_chain = None
+
+
+def _ref_init(seed):
+    global _worker_chain
+    _worker_chain = _oracle_chain(seed)
+
+
+def _ref_step(args):
+    hops, M = args
+    t0 = time.perf_counter()
+    c0 = _worker_chain.counters()
+    _worker_chain.run(hops, M)
+    c1 = _worker_chain.counters()
+    return c1["hops"] - c0["hops"], c1["attempts"] - c0["attempts"], time.perf_counter() - t0
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm: one chain per host core."""
+    import multiprocessing as mp
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    hops_per_chain = 24
+    pools = [ctx.Pool(1, initializer=_ref_init, initargs=(s,)) for s in range(cores)]
+    try:
+        def step():
+            res = [p.apply_async(_ref_step, ((hops_per_chain, args.M),)) for p in pools]
+            return [r.get() for r in res]
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        hops = att = 0
+        for _ in range(args.steps):
+            for h, a, _dt in step():
+                hops += h
+                att += a
+        dt = time.perf_counter() - t0
+    finally:
+        for p in pools:
+            p.terminate()
+    value = hops / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "hops/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "attempts_per_s": att / dt,
+        "config": {"workload": "L128_T0.01 serial oracle, one chain per host core",
+                   "replicas": cores, "hops_per_chain_per_step": hops_per_chain, "M": args.M},
+        "cpu_baseline": {"value": value, "unit": "hops/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} chains (seeds 0..{cores - 1}) from their random "
+                                   f"initial configurations, {hops_per_chain} hops per chain "
+                                   f"per step"},
+        "e2e": {"value": value, "unit": "hops/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1407_5026_gb300 import binding as B
+    from paper_1407_5026_gb300 import build as libbuild
+
+    ws, rank, local = dist_env()
+    libbuild.build()
+    B.load()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    R = args.replicas or 2 * sms
+    reps = replicas_for(rank, R)
+    N = WORKLOAD["L"] ** 2
+
+    # peaks that bound the eps update (measured on this GPU)
+    smem_peak = B.cg_microbench(0, local)          # bytes/s, 32-bit RMW
+    dadd_peak = B.cg_microbench(1, local)          # adds/s
+
+    sysm = B.System(reps, precision=B.CG_FP32, refresh_every=0, block_threads=args.threads,
+                    device=local)
+    st = sysm.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def one_step(ev):
+        with torch.cuda.stream(st):
+            if ev:
+                ev[0].record(st)
+            B.cg_run_async(sysm.h, HOPS_PER_STEP, args.M)
+            if ev:
+                ev[1].record(st)
+            B.cg_refresh_async(sysm.h)
+            if ev:
+                ev[2].record(st)
+
+    for _ in range(args.warmup):
+        one_step(None)
+        rc = B.cg_sync(sysm.h)
+        assert rc == B.CG_OK, rc
+    obs0 = [B.cg_observables(sysm.h, k) for k in range(R)]
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        one_step(events[k])
+        with torch.cuda.stream(st):
+            flush.zero_()                      # L2 flush between steps, outside the events
+    rc = B.cg_sync(sysm.h)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    assert rc == B.CG_OK, rc
+
+    run_ms = [e[0].elapsed_time(e[1]) for e in events]
+    ref_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = [a + b for a, b in zip(run_ms, ref_ms)]
+    total_s = sum(step_ms) * 1e-3
+    obs1 = [B.cg_observables(sysm.h, k) for k in range(R)]
+    hops = sum(o1["hops"] - o0["hops"] for o0, o1 in zip(obs0, obs1))
+    attempts = sum(o1["attempts"] - o0["attempts"] for o0, o1 in zip(obs0, obs1))
+    evaluated = sum(o1["evaluated"] - o0["evaluated"] for o0, o1 in zip(obs0, obs1))
+    cyc_upd = sum(o1["cycles_update"] - o0["cycles_update"] for o0, o1 in zip(obs0, obs1))
+    cyc_rej = sum(o1["cycles_reject"] - o0["cycles_reject"] for o0, o1 in zip(obs0, obs1))
+    max_err = max(o["max_eps_err_last_refresh"] for o in obs1)
+
+    if ws > 1:
+        t = torch.tensor([total_s, float(hops), float(attempts)], device=f"cuda:{local}",
+                         dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_s_all, hops_all, att_all = float(tmax[0]), float(t[1]), float(t[2])
+    else:
+        total_s_all, hops_all, att_all = total_s, float(hops), float(attempts)
+
+    # roofline of the dominant kernel (the persistent PR kernel): algorithmic
+    # bytes of the eps update per launch / mean launch time
+    bytes_per_hop = N * (2 * 4 + 2 * 4)
+    launch_s = statistics.mean(run_ms) * 1e-3
+    achieved = R * HOPS_PER_STEP * bytes_per_hop / launch_s
+    upd_s_per_cta = (cyc_upd / R) / (clk["sm_mhz"] * 1e6) if clk else None
+
+    result = {
+        "metric": METRIC, "value": hops_all / total_s_all, "unit": "hops/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "attempts_per_s": att_all / total_s_all,
+        "acceptance": attempts and hops / attempts,
+        "labels_evaluated_per_s": evaluated / total_s,
+        "config": {"workload": "L128_T0.01_fp32_batched", "L": 128, "T": 0.01,
+                   "replicas_per_gpu": R, "hops_per_replica_per_step": HOPS_PER_STEP,
+                   "M": args.M, "refresh": "binary64 direct every 1024 hops",
+                   "l2": "256 MB buffer zeroed between steps (outside the timed events)",
+                   "state": f"continues the chains after {args.warmup} warm-up steps"},
+        "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": smem_peak / 1e9,
+                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": None,
+                     "kernel": "pr_persistent<float>",
+                     "bytes_per_hop": bytes_per_hop,
+                     "peak_source": "measured: shared-memory 32-bit read-modify-write "
+                                    "microbenchmark over all SMs (cg_microbench kind 0)"},
+        "phase_split": {"refresh_ms_per_step": statistics.mean(ref_ms),
+                        "run_ms_per_step": statistics.mean(run_ms),
+                        "update_cycles_frac": cyc_upd / max(1, cyc_upd + cyc_rej),
+                        "max_eps_err_last_refresh": max_err},
+        "gpu_launches": args.steps * (len(set(r["L"] for r in reps)) + R),
+        "clocks": clk,
+        "peaks_measured": {"smem_rmw32_GBps": smem_peak / 1e9, "dadd_per_s": dadd_peak},
+        "wall_s_timed": t_wall,
+    }
+    sysm.close()
+
+    # the plain binary64 form of the same workload, one replica
+    if args.fp64_hops > 0:
+        s64 = B.System(replicas_for(rank, 1), precision=B.CG_FP64, device=local)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(s64.stream):
+            B.cg_run_async(s64.h, 200, args.M)
+            B.cg_sync(s64.h)
+            o0 = B.cg_observables(s64.h, 0)
+            ev[0].record(s64.stream)
+            B.cg_run_async(s64.h, args.fp64_hops, args.M)
+            ev[1].record(s64.stream)
+            B.cg_sync(s64.h)
+        o1 = B.cg_observables(s64.h, 0)
+        dt = ev[0].elapsed_time(ev[1]) * 1e-3
+        result["fp64_form"] = {
+            "hops_per_s": (o1["hops"] - o0["hops"]) / dt,
+            "attempts_per_s": (o1["attempts"] - o0["attempts"]) / dt,
+            "replicas": 1, "hops": o1["hops"] - o0["hops"],
+            "acceptance": (o1["hops"] - o0["hops"]) / max(1, o1["attempts"] - o0["attempts"]),
+            "update_bound_dadd_per_hop": 2 * N, "dadd_peak_per_s": dadd_peak}
+        s64.close()
+
+    # end to end through the C ABI with host buffers: upload the state from
+    # pinned host memory, run one step, read the state back
+    if not args.no_e2e:
+        result["e2e"] = e2e(args, B, reps, local)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.M)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def e2e(args, B, reps, local):
+    import numpy as np
+    import torch
+    R = len(reps)
+    N = WORKLOAD["L"] ** 2
+    sysm = B.System(reps, precision=B.CG_FP32, refresh_every=0, block_threads=args.threads,
+                    device=local)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+    n_h = [pin((N,), torch.uint8) for _ in range(R)]
+    e_h = [pin((N,), torch.float64) for _ in range(R)]
+    cnt = []
+    for k in range(R):
+        n, e, _, c = B.cg_read_state(sysm.h, k, phi=False)
+        n_h[k][:] = n
+        e_h[k][:] = e
+        cnt.append(c)
+    steps = max(3, min(args.steps, 8))
+    # warm
+    B.cg_run(sysm.h, HOPS_PER_STEP, args.M)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hops = 0
+    for _ in range(steps):
+        for k in range(R):
+            B.cg_write_state(sysm.h, k, n_h[k], eps=e_h[k], counters=cnt[k])
+        B.cg_run_async(sysm.h, HOPS_PER_STEP, args.M)
+        B.cg_refresh_async(sysm.h)
+        B.cg_sync(sysm.h)
+        for k in range(R):
+            _, _, _, c = B.cg_read_state(sysm.h, k, n=n_h[k], eps=e_h[k], phi=False)
+            hops += c["hops"] - cnt[k]["hops"]
+            cnt[k] = c
+    dt = time.perf_counter() - t0
+    sysm.close()
+    words = (N + 31) // 32
+    # device transfers per replica: bitmask words, binary32 eps, counters block
+    per_rep = 4 * words + 4 * N + 96
+    return {"value": hops / dt, "unit": "hops/s", "h2d_bytes_per_step": R * per_rep,
+            "d2h_bytes_per_step": R * per_rep, "steps": steps,
+            "note": "per step: cg_write_state + cg_run + cg_refresh + cg_read_state "
+                    "for every replica from/to pinned host buffers"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

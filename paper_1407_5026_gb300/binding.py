@@ -238,11 +238,20 @@ def cg_run_logged(h, n_hops, M):
     return rc, log.reshape(R, int(n_hops))
 
 
+def _out(spec, N, dtype):
+    """True -> a new array, False/None -> skipped, an array -> used as is."""
+    if isinstance(spec, np.ndarray):
+        assert spec.dtype == dtype and spec.size == N and spec.flags.c_contiguous
+        return spec
+    return np.zeros(N, dtype) if spec else None
+
+
 def cg_read_state(h, replica=0, n=True, eps=True, phi=True, counters=True):
+    """Each of n / eps / phi is True (new array), False (skip) or a caller array."""
     N = cg_num_sites(h, replica)
-    n_a = np.zeros(N, np.uint8) if n else None
-    e_a = np.zeros(N, np.float64) if eps else None
-    p_a = np.zeros(N, np.float64) if phi else None
+    n_a = _out(n, N, np.uint8)
+    e_a = _out(eps, N, np.float64)
+    p_a = _out(phi, N, np.float64)
     c = cg_counters() if counters else None
     _check(load().cg_read_state(h, replica, _ptr(n_a, ctypes.c_uint8), _ptr(e_a, ctypes.c_double),
                                 _ptr(p_a, ctypes.c_double),

@@ -117,6 +117,20 @@ cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int word
     return cudaGetLastError();
 }
 
+__global__ void reset_refresh_err_kernel(const DevReplica *__restrict__ reps,
+                                         const int *__restrict__ index, int R)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) reps[index[r]].ctr->max_err_bits = 0ull;
+}
+
+cudaError_t launch_reset_refresh_err(const DevReplica *d_reps, const int *d_index, int R,
+                                     cudaStream_t st)
+{
+    reset_refresh_err_kernel<<<(R + 127) / 128, 128, 0, st>>>(d_reps, d_index, R);
+    return cudaGetLastError();
+}
+
 __global__ void debug_philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                                     int n)
 {

@@ -24,9 +24,17 @@ struct alignas(16) DevCounters {
     unsigned long long cycles_update;
     unsigned long long refreshes;
     unsigned long long max_err_bits;   // max |eps - eps_ref| of the last refresh (binary64 bits)
-    int status;                        // CG_OK or CG_ESTUCK
-    int pad_[3];
+    int status;                        // CG_OK, CG_ESTUCK or CG_ETIMEOUT
+    float m_ema;                       // running mean of attempts per hop (chunk sizing)
+    int pad_[2];
 };
+
+// Guide table of the tower: bucket b = x1 >> (32 - kGuideBits) holds the
+// smallest vector index whose threshold is >= the bucket's first value, with
+// bit 15 set when a threshold falls inside the bucket (then a short scan
+// finds the exact vector).
+constexpr int kGuideBits = 12;
+constexpr int kGuide = 1 << kGuideBits;
 
 // Everything one CTA needs to run one replica.
 struct alignas(16) DevReplica {
@@ -38,12 +46,14 @@ struct alignas(16) DevReplica {
     int pad0_;
     double nu, T, E;
     double negC0nu;           // -nu * sum_{t != s} 1/r_st (same for every s)
+    double C0;                // sum_{t != s} 1/r_st
     // tables (device)
     const double *tinv64;     // H1*H1, [fy*H1 + fx] = 1/sqrt(fx^2+fy^2), 0 at origin
     const float *tinv32;      // the same rounded to binary32
     const unsigned int *thr;  // V tower thresholds C_k - 1
     const int *disp;          // V packed hop vectors: (dx & 0xffff) | (dy << 16)
     const double *tinvd;      // V: 1/r of each hop vector (binary64)
+    const unsigned short *guide; // kGuide entries
     // state (device)
     void *eps;                // N binary64 (CG_FP64) or binary32 (CG_FP32)
     unsigned int *occ;        // occupation bitmask, bit s%32 of word s/32
@@ -64,7 +74,8 @@ struct RunArgs {
 
 // Shared-memory carve-up of the persistent kernel (bytes, 16-aligned).
 struct SmemLayout {
-    int off_eps, off_tinv, off_occ, off_thr, off_disp, off_tinvd, total;
+    int off_eps, off_tinv, off_occ, off_guide, off_thr, off_disp;
+    int off_vr64, off_edx64, off_vr32, off_edx32, total;
 };
 
 __host__ __device__ inline int cg_align16(int x) { return (x + 15) & ~15; }
@@ -77,9 +88,13 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int H1, int V, int word
     s.off_eps = o;   o = cg_align16(o + N * real_bytes);
     s.off_tinv = o;  o = cg_align16(o + H1 * H1 * real_bytes);
     s.off_occ = o;   o = cg_align16(o + words * 4);
+    s.off_guide = o; o = cg_align16(o + kGuide * 2);
     s.off_thr = o;   o = cg_align16(o + V * 4);
     s.off_disp = o;  o = cg_align16(o + V * 4);
-    s.off_tinvd = o; o = cg_align16(o + V * 8);
+    s.off_vr64 = o;  o = cg_align16(o + V * 8);
+    s.off_edx64 = o; o = cg_align16(o + V * 8);
+    s.off_vr32 = o;  o = cg_align16(o + V * 4);
+    s.off_edx32 = o; o = cg_align16(o + V * 4);
     s.total = o;
     return s;
 }
@@ -99,5 +114,16 @@ cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key,
 cudaError_t launch_debug_exp(const double *x, double *out, int n, cudaStream_t st);
 cudaError_t set_pr_smem_limit(int precision, int bytes);
 int microbench(int kind, int device, double *result);
+cudaError_t launch_reset_refresh_err(const DevReplica *d_reps, const int *d_index, int R,
+                                     cudaStream_t st);
+// Tensor-core refresh of R <= 512 binary32 replicas of one L (L*L % 128 == 0).
+// d_scratch: refresh_tc_scratch_bytes(L, R) bytes (the S image and the K-split
+// partial sums), 256-byte aligned.
+cudaError_t launch_refresh_tc(const DevReplica *d_reps, const int *d_index, int R, int L,
+                              const uint32_t *d_tab, unsigned char *d_scratch, int *d_err,
+                              cudaStream_t st);
+int refresh_tc_smem_bytes(int R_pad, int H1);
+int refresh_tc_ksplit(int L);
+size_t refresh_tc_scratch_bytes(int L, int R);
 
 }  // namespace cg

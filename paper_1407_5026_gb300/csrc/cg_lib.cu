@@ -64,6 +64,23 @@ double host_exp(double x)
     return std::ldexp(p, (int)kd);
 }
 
+// Round-to-nearest-even binary32 -> BF16 (finite inputs), and back.
+uint32_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    return (u + 0x7fffu + lsb) >> 16;
+}
+
+float bf16_to_float(uint32_t h)
+{
+    const uint32_t u = h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 struct Tables {
     int L = 0, r_max = 0, H1 = 0, V = 0;
     double xi = 0, Z = 0, C0 = 0;
@@ -72,6 +89,10 @@ struct Tables {
     std::vector<unsigned> thr;
     std::vector<int> disp;
     std::vector<double> tinvd;
+    std::vector<unsigned short> guide;
+    std::vector<uint32_t> split;      // BF16 hi | lo << 16 of each 1/r entry
+    unsigned short *d_guide = nullptr;
+    uint32_t *d_split = nullptr;
     double *d_t64 = nullptr;
     float *d_t32 = nullptr;
     unsigned *d_thr = nullptr;
@@ -89,6 +110,15 @@ int build_tables(Tables &t, int L, double xi, int r_max)
                 (fx == 0 && fy == 0) ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy));
     t.t32.resize(t.t64.size());
     for (size_t k = 0; k < t.t64.size(); ++k) t.t32[k] = (float)t.t64[k];
+    // two-term BF16 split of 1/r for the tensor-core refresh: hi = bf16(T),
+    // lo = bf16(T - hi), so T - hi - lo is below 2^-16 of T
+    t.split.resize(t.t64.size());
+    for (size_t k = 0; k < t.t64.size(); ++k) {
+        const uint32_t hi = bf16_rne((float)t.t64[k]);
+        const double rest = t.t64[k] - (double)bf16_to_float(hi);
+        const uint32_t lo = bf16_rne((float)rest);
+        t.split[k] = hi | (lo << 16);
+    }
     // sum_{t != s} 1/r_st is the same for every s: every displacement once
     double C0 = 0.0;
     for (int dy = 0; dy < L; ++dy)
@@ -118,6 +148,18 @@ int build_tables(Tables &t, int L, double xi, int r_max)
         run += Wk;
         t.thr.push_back((unsigned)(run - 1));
     }
+    // guide table: smallest vector whose threshold reaches each bucket, flag
+    // set when a threshold lies inside the bucket
+    t.guide.assign(kGuide, 0);
+    const int shift = 32 - kGuideBits;
+    int v = 0;
+    for (int b = 0; b < kGuide; ++b) {
+        const unsigned long long lo = (unsigned long long)b << shift;
+        const unsigned long long hi = lo + (1ull << shift) - 1;
+        while (v < t.V - 1 && t.thr[v] < lo) ++v;
+        const bool scan = t.thr[v] >= lo && t.thr[v] < hi;
+        t.guide[b] = (unsigned short)(v | (scan ? 0x8000 : 0));
+    }
     return CG_OK;
 }
 
@@ -133,7 +175,27 @@ struct Rep {
 
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
+    bool tc = false;                 // refresh on the tensor cores
+    unsigned char *d_img = nullptr;  // S image scratch of the tensor-core refresh
+    int *d_err = nullptr;            // its error word
 };
+
+constexpr int kTcMaxReplicas = 512;  // TMEM columns of one accumulator
+
+// Whether a group of `count` binary32 replicas of side L refreshes on the
+// tensor cores (it needs L*L to be a multiple of 128).
+bool group_uses_tc(const cg_opts &o, int L, int count)
+{
+    if (o.precision != CG_FP32 || (L * L) % 128 != 0) return false;
+    if (o.refresh_kind == CG_REFRESH_BF16X2) return true;
+    if (o.refresh_kind == CG_REFRESH_AUTO) return count >= 8;
+    return false;
+}
+
+size_t tc_img_bytes(int L, int count)
+{
+    return refresh_tc_scratch_bytes(L, std::min(count, kTcMaxReplicas));
+}
 
 }  // namespace
 
@@ -147,6 +209,7 @@ struct cg_handle {
     std::vector<Group> groups;
     DevReplica *d_reps = nullptr;
     int *d_index = nullptr;
+    std::vector<int> order;          // group position -> replica index (host copy of d_index)
     std::vector<DevReplica> h_reps;
     // memory: cudaMalloc'd pointers, or a caller workspace
     bool ws_mode = false;
@@ -228,6 +291,8 @@ void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
     dr.negC0nu = -r.d.nu * t.C0;
     dr.tinv64 = t.d_t64; dr.tinv32 = t.d_t32; dr.thr = t.d_thr; dr.disp = t.d_disp;
     dr.tinvd = t.d_tinvd;
+    dr.guide = t.d_guide;
+    dr.C0 = t.C0;
     dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
     dr.log = log;
     (void)precision;
@@ -345,10 +410,22 @@ int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
     return CG_OK;
 }
 
-size_t plan_bytes(int R, const cg_replica_desc *reps, int precision)
+size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
 {
     // mirrors the allocations of create_impl (each rounded up to 256 bytes)
+    const int precision = o.precision;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    std::vector<std::pair<int, int>> groups;   // (L, count)
+    for (int k = 0; k < R; ++k) {
+        bool found = false;
+        for (auto &g : groups)
+            if (g.first == reps[k].L) { ++g.second; found = true; }
+        if (!found) groups.push_back({reps[k].L, 1});
+    }
+    size_t tc_total = 0;
+    for (auto &g : groups)
+        if (group_uses_tc(o, g.first, g.second))
+            tc_total += up(tc_img_bytes(g.first, g.second)) + up(sizeof(int));
     size_t total = up(sizeof(DevReplica) * (size_t)R) + up(sizeof(int) * (size_t)R);
     std::vector<std::tuple<int, int, double>> seen;
     for (int k = 0; k < R; ++k) {
@@ -366,10 +443,11 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, int precision)
                     const int r2 = dx * dx + dy * dy;
                     if (r2 > 0 && r2 <= d.r_max * d.r_max) ++V;
                 }
-            total += up(H1 * H1 * 8) + up(H1 * H1 * 4) + up(V * 4) + up(V * 4) + up(V * 8);
+            total += up(H1 * H1 * 8) + up(H1 * H1 * 4) + up(V * 4) + up(V * 4) + up(V * 8) +
+                     up((size_t)kGuide * 2) + up(H1 * H1 * 4);
         }
     }
-    return total;
+    return total + tc_total;
 }
 
 cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, void *ws,
@@ -449,12 +527,16 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             dalloc(h.get(), (void **)&t->d_t32, t->t32.size() * 4) ||
             dalloc(h.get(), (void **)&t->d_thr, t->thr.size() * 4) ||
             dalloc(h.get(), (void **)&t->d_disp, t->disp.size() * 4) ||
-            dalloc(h.get(), (void **)&t->d_tinvd, t->tinvd.size() * 8)) { destroy_partial(); return nullptr; }
+            dalloc(h.get(), (void **)&t->d_tinvd, t->tinvd.size() * 8) ||
+            dalloc(h.get(), (void **)&t->d_guide, t->guide.size() * 2) ||
+            dalloc(h.get(), (void **)&t->d_split, t->split.size() * 4)) { destroy_partial(); return nullptr; }
+        cudaMemcpyAsync(t->d_split, t->split.data(), t->split.size() * 4, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_t64, t->t64.data(), t->t64.size() * 8, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_t32, t->t32.data(), t->t32.size() * 4, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_thr, t->thr.data(), t->thr.size() * 4, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_disp, t->disp.data(), t->disp.size() * 4, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_tinvd, t->tinvd.data(), t->tinvd.size() * 8, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(t->d_guide, t->guide.data(), t->guide.size() * 2, cudaMemcpyHostToDevice, h->st);
     }
     const int rb = o.precision == CG_FP64 ? 8 : 4;
     for (auto &r : h->reps) {
@@ -480,8 +562,16 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         g.count = k - g.first;
         g.smem = smem;
         g.threads = choose_threads(o, g.L, smem);
+        g.tc = group_uses_tc(o, g.L, g.count);
+        if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.count)) ||
+                     dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
+            destroy_partial();
+            return nullptr;
+        }
+        if (g.tc) cudaMemsetAsync(g.d_err, 0, sizeof(int), h->st);
         h->groups.push_back(g);
     }
+    h->order = order;
     h->h_reps.resize(R);
     for (int k = 0; k < R; ++k) fill_dev(h->reps[k], o.precision, h->h_reps[k], nullptr);
     if (cudaMemcpyAsync(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
@@ -540,10 +630,22 @@ int refresh_all(cg_handle *h)
         }
         return CG_OK;
     }
-    for (size_t k = 0; k < h->reps.size(); ++k) {
-        const Rep &r = h->reps[k];
-        CG_CUDA(cudaMemsetAsync(&r.d_ctr->max_err_bits, 0, 8, h->st));
-        CG_CUDA(launch_refresh_fp64(h->d_reps + k, r.N, r.tab->H1, r.words, h->st));
+    for (const Group &g : h->groups) {
+        CG_CUDA(launch_reset_refresh_err(h->d_reps, h->d_index + g.first, g.count, h->st));
+        if (g.tc) {
+            const uint32_t *split = h->reps[h->order[g.first]].tab->d_split;
+            for (int c0 = 0; c0 < g.count; c0 += kTcMaxReplicas) {
+                const int n = std::min(kTcMaxReplicas, g.count - c0);
+                CG_CUDA(launch_refresh_tc(h->d_reps, h->d_index + g.first + c0, n, g.L, split,
+                                          g.d_img, g.d_err, h->st));
+            }
+        } else {
+            for (int k = g.first; k < g.first + g.count; ++k) {
+                const int ri = h->order[k];
+                const Rep &r = h->reps[ri];
+                CG_CUDA(launch_refresh_fp64(h->d_reps + ri, r.N, r.tab->H1, r.words, h->st));
+            }
+        }
     }
     return CG_OK;
 }
@@ -592,6 +694,15 @@ int finish_run(cg_handle *h)
         if (c[k].status == CG_ETIMEOUT)
             rc = fail(CG_ETIMEOUT, "a hop exceeded the device time limit");
     }
+    for (const Group &g : h->groups) {
+        if (!g.tc) continue;
+        int err = 0;
+        CG_CUDA(cudaMemcpy(&err, g.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            CG_CUDA(cudaMemset(g.d_err, 0, sizeof(int)));
+            rc = fail(CG_ETIMEOUT, "a tensor-core refresh wait exceeded its time limit");
+        }
+    }
     return rc;
 }
 
@@ -620,7 +731,9 @@ cg_handle *cg_create_batch(int R, const cg_replica_desc *reps, const cg_opts *op
 size_t cg_workspace_bytes(int R, const cg_replica_desc *reps, const cg_opts *opts)
 {
     if (R <= 0 || !reps) return 0;
-    return plan_bytes(R, reps, opts ? opts->precision : CG_FP64);
+    cg_opts o{};
+    if (opts) o = *opts;
+    return plan_bytes(R, reps, o);
 }
 
 cg_handle *cg_create_batch_ws(int R, const cg_replica_desc *reps, const cg_opts *opts,

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(1024) smem_rmw_kernel(int iters, T *sink)
             acc += v;
         }
     }
-    if (acc == (T)-1) sink[0] = acc;   // never true; keeps the loop alive
+    if (acc == (T)12345) sink[0] = acc;   // practically never true; keeps the loop alive
 }
 
 __global__ void __launch_bounds__(256) dadd_kernel(int iters, double seed, double *sink)
@@ -70,18 +70,21 @@ int microbench(int kind, int device, double *result)
         const int word = kind == 0 ? 4 : 8;
         const int smem = 16384 * word;
         const int iters = 200, blocks = 2 * sms;
+        // integer adds keep the ALU side trivial next to the shared-memory
+        // traffic (a binary64 add would measure GB300's slow FP64 pipe)
         if (kind == 0)
-            err = cudaFuncSetAttribute(smem_rmw_kernel<float>,
+            err = cudaFuncSetAttribute(smem_rmw_kernel<unsigned int>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         else
-            err = cudaFuncSetAttribute(smem_rmw_kernel<double>,
+            err = cudaFuncSetAttribute(smem_rmw_kernel<unsigned long long>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
             cudaEventRecord(e0);
             if (kind == 0)
-                smem_rmw_kernel<float><<<blocks, 1024, smem>>>(iters, (float *)sink);
+                smem_rmw_kernel<unsigned int><<<blocks, 1024, smem>>>(iters, (unsigned int *)sink);
             else
-                smem_rmw_kernel<double><<<blocks, 1024, smem>>>(iters, (double *)sink);
+                smem_rmw_kernel<unsigned long long>
+                    <<<blocks, 1024, smem>>>(iters, (unsigned long long *)sink);
             cudaEventRecord(e1);
             err = cudaEventSynchronize(e1);
             const double bytes = 2.0 * word * 16384.0 * iters * blocks;   // load + store

@@ -2,27 +2,37 @@
 //
 // One CTA runs one disorder replica for a whole launch.  Its local energies
 // eps (N values), the folded minimum-image 1/r table, the occupation bitmask
-// and the tower live in shared memory; global memory is touched only to load
-// the state at the start and store it at the end.
+// and the tower (thresholds + a guide table) live in shared memory; global
+// memory is touched only to load the state at the start and store it at the
+// end.
 //
 // Per executed hop (mixed PR algorithm, section "Hopping conduction in the
 // Coulomb glass", steps 1-3):
 //   rounds r = 0, 1, ...: the M labels of a round are evaluated in chunks of
-//   blockDim labels in increasing order, one label per thread.  Label k draws
+//   C labels in increasing order, two labels per thread.  Label k draws
 //   Philox(key = seed, ctr = (k, r lo, r hi, replica)) -> site i from word 0,
 //   hop vector from word 1 by tower sampling, acceptance variate from word 2
 //   (step 1 and the three random numbers per label of the GPU paragraph);
 //   theta = n_i (1 - n_j) and the Metropolis test on
 //   dH = eps_j - eps_i - 1/r_ij - E dx (step 2, Eq. 2).  A chunk with no
 //   accept costs one block-wide OR barrier; the first chunk with an accept
-//   gives the lowest accepting label q by warp ballot + find-first-set and
-//   a minimum over the warps.  Labels after q are never looked at, so the
-//   result equals the serial rejection chain on the same random numbers.
-//   Commit (step 3a/3b/3c): flip n_i, n_j, P += dx, attempts += (p-1)M + q.
+//   gives the lowest accepting label q by warp ballot + find-first-set and a
+//   minimum over the warps.  Labels after q are never looked at, so the hop
+//   equals the serial rejection chain's on the same random numbers.  C follows
+//   the replica's recent attempts per hop (C ~ sqrt(128 m), clamped to
+//   [64, 2 * blockDim]); it changes which labels are evaluated, never the hop.
+//   Commit (step 3a/3c): flip n_i, n_j, P += dx, attempts += (p-1)M + q.
 //   Update (step 3b): eps_l += 1/r_lj - 1/r_li for every l, with the table
 //   holding 0 at the origin so l = i and l = j need no special case.
-#include <cstdio>
-
+//
+// Binary64 form: every operation that feeds the chain is a round-to-nearest
+// intrinsic in the serial chain's order, so the trajectory is bit-identical
+// to the serial CPU chain.  The Metropolis comparison u < exp(-dH/T) is first
+// decided by a binary32 estimate with a relative margin of 2e-4 (ten times
+// its error bound); only the undecided cases evaluate the binary64
+// exponential, so every decision is the binary64 one.
+// Binary32 form: eps, the table and dH in binary32 (dH in binary64 when
+// |dH| < 1e-5), exp from the fast intrinsic.
 #include "cg_device.cuh"
 #include "cg_internal.h"
 
@@ -30,7 +40,7 @@ namespace cg {
 
 struct Cand {
     unsigned int i, j;
-    int dxy;           // packed hop vector
+    int dxy;
     unsigned int pad_;
     double dE;
 };
@@ -50,52 +60,6 @@ struct Prec<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 };
 
-// Step 2 for one proposal whose theta holds: returns accept, writes dE.
-template <typename Real>
-__device__ __forceinline__ bool accept_test(const Real *eps, const double *tinvd, int v,
-                                            unsigned i, unsigned j, int dx, uint32_t x2,
-                                            double E, double T, float Ef, float invTf,
-                                            double &dE_out);
-
-template <>
-__device__ __forceinline__ bool accept_test<double>(const double *eps, const double *tinvd,
-                                                    int v, unsigned i, unsigned j, int dx,
-                                                    uint32_t x2, double E, double T, float,
-                                                    float, double &dE_out)
-{
-    double d = d_sub(eps[j], eps[i]);
-    d = d_sub(d, tinvd[v]);
-    const double dE = d_sub(d, d_mul(E, (double)dx));
-    dE_out = dE;
-    if (dE <= 0.0) return true;
-    const double u = d_mul(d_add((double)x2, 0.5), 0x1p-32);
-    return u < cg_exp_accept(d_div(-dE, T));
-}
-
-template <>
-__device__ __forceinline__ bool accept_test<float>(const float *eps, const double *tinvd,
-                                                   int v, unsigned i, unsigned j, int dx,
-                                                   uint32_t x2, double E, double T, float Ef,
-                                                   float invTf, double &dE_out)
-{
-    const float ei = eps[i], ej = eps[j];
-    const float dEf = ((ej - ei) - (float)tinvd[v]) - Ef * (float)dx;
-    if (fabsf(dEf) < 1e-5f) {
-        // near tie: decide in binary64 from the widened energies
-        double d = d_sub((double)ej, (double)ei);
-        d = d_sub(d, tinvd[v]);
-        const double dE = d_sub(d, d_mul(E, (double)dx));
-        dE_out = dE;
-        if (dE <= 0.0) return true;
-        const double u = d_mul(d_add((double)x2, 0.5), 0x1p-32);
-        return u < cg_exp_accept(d_div(-dE, T));
-    }
-    dE_out = (double)dEf;
-    if (dEf <= 0.0f) return true;
-    const float u = ((float)(x2 >> 9) + 0.5f) * 0x1p-23f;
-    return u < expf(-dEf * invTf);
-}
-
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;
@@ -103,13 +67,155 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
+// Binary32 value of a binary64 from its high word: truncated to 20 mantissa
+// bits (relative error < 2^-20); integer operations only.  Returns 0 when
+// |x| < 2^-126 (callers fall back to the exact path).
+__device__ __forceinline__ float approx_f32(double x)
+{
+    const int hi = __double2hiint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex < 1023 - 126 || ex > 1023 + 127) return 0.0f;
+    const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(ex - 896) << 23) |
+                          (((unsigned)hi & 0xfffffu) << 3);
+    return __uint_as_float(bits);
+}
+
+struct Shared {
+    void *eps;
+    void *tinv;
+    unsigned *occ;
+    unsigned short *guide;
+    unsigned *thr;
+    int *disp;
+    double *vr64, *edx64;
+    float *vr32, *edx32;
+};
+
+struct Prop {
+    unsigned i, j;
+    int v, dxy;
+    uint32_t x2;
+    bool theta;
+};
+
+// Step 1 of one label (Philox, site, tower, destination) and theta.
+__device__ __forceinline__ Prop propose(const Shared &S, unsigned k, unsigned long long r,
+                                        uint32_t rep, uint32_t key0, uint32_t key1, int L,
+                                        unsigned N, unsigned magic, unsigned thr_last,
+                                        bool valid)
+{
+    Prop p;
+    uint32_t x[4];
+    philox4x32_10(k, (uint32_t)r, (uint32_t)(r >> 32), rep, key0, key1, x);
+    p.x2 = x[2];
+    p.i = __umulhi(x[0], N);
+    p.theta = false;
+    p.j = 0;
+    p.v = 0;
+    p.dxy = 0;
+    const uint32_t x1 = x[1];
+    if (!valid || x1 > thr_last) return p;       // beyond M, or a null proposal
+    const unsigned g = S.guide[x1 >> (32 - kGuideBits)];
+    int v = (int)(g & 0x7fffu);
+    if (g & 0x8000u)
+        while (x1 > S.thr[v]) ++v;               // the bucket holds a threshold
+    const int dxy = S.disp[v];
+    const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
+    const int yi = (int)__umulhi(p.i, magic), xi = (int)p.i - yi * L;
+    int xj = xi + dx, yj = yi + dy;
+    xj += (xj < 0) ? L : 0;
+    xj -= (xj >= L) ? L : 0;
+    yj += (yj < 0) ? L : 0;
+    yj -= (yj >= L) ? L : 0;
+    p.j = (unsigned)(yj * L + xj);
+    p.v = v;
+    p.dxy = dxy;
+    const unsigned wi = S.occ[p.i >> 5], wj = S.occ[p.j >> 5];
+    p.theta = ((wi >> (p.i & 31)) & 1u) && !((wj >> (p.j & 31)) & 1u);
+    return p;
+}
+
+// Step 2 (accept test) for a proposal whose theta holds.
+template <typename Real>
+__device__ __forceinline__ bool accept(const Shared &S, const Prop &p, double T, float invTf,
+                                       double &dE_out);
+
+template <>
+__device__ __forceinline__ bool accept<double>(const Shared &S, const Prop &p, double T,
+                                               float invTf, double &dE_out)
+{
+    const double *eps = reinterpret_cast<const double *>(S.eps);
+    double d = d_sub(eps[p.j], eps[p.i]);
+    d = d_sub(d, S.vr64[p.v]);
+    const double dE = d_sub(d, S.edx64[p.v]);
+    dE_out = dE;
+    if (dE <= 0.0) return true;
+    // binary32 estimate of y = -dE/T and of e^y, then a margin test
+    const float df = approx_f32(dE);
+    if (df > 0.0f) {
+        const float y = -df * invTf;
+        if (y < -23.01f) return false;                      // e^y below every u
+        const float e = __expf(y);
+        // u ~ x2 2^-32 differs from (x2 + 1/2) 2^-32 by at most 2^-33 plus a
+        // relative 2^-24: the absolute slack 2^-31 covers the first, the
+        // relative margin the second and the exponential's error
+        const float u = __uint2float_rn(p.x2) * 0x1p-32f;
+        if (u + 0x1p-31f < e * (1.0f - 2e-4f)) return true;
+        if (u > e * (1.0f + 2e-4f) + 0x1p-31f) return false;
+    }
+    const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
+    return u < cg_exp_accept(d_div(-dE, T));
+}
+
+template <>
+__device__ __forceinline__ bool accept<float>(const Shared &S, const Prop &p, double T,
+                                              float invTf, double &dE_out)
+{
+    const float *eps = reinterpret_cast<const float *>(S.eps);
+    const float ei = eps[p.i], ej = eps[p.j];
+    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(ej, ei), S.vr32[p.v]), S.edx32[p.v]);
+    if (fabsf(dEf) < 1e-5f) {
+        // near tie: decide in binary64 from the widened energies
+        double d = d_sub((double)ej, (double)ei);
+        d = d_sub(d, S.vr64[p.v]);
+        const double dE = d_sub(d, S.edx64[p.v]);
+        dE_out = dE;
+        if (dE <= 0.0) return true;
+        const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
+        return u < cg_exp_accept(d_div(-dE, T));
+    }
+    dE_out = 0.0;   // widened for the executed hop only
+    if (dEf <= 0.0f) return true;
+    const float u = ((float)(p.x2 >> 9) + 0.5f) * 0x1p-23f;
+    return u < __expf(-dEf * invTf);
+}
+
+// dH of the executed hop in binary64 (the binary32 form widens it here, once
+// per hop, instead of on every label).
+template <typename Real>
+__device__ __forceinline__ double hop_dE(const Shared &S, const Prop &p, double dE)
+{
+    if (sizeof(Real) == 8 || dE != 0.0) return dE;
+    const float *eps = reinterpret_cast<const float *>(S.eps);
+    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(eps[p.j], eps[p.i]), S.vr32[p.v]),
+                                S.edx32[p.v]);
+    return (double)dEf;
+}
+
 template <typename Real, int kThreads>
-__global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 2048 / kThreads / 2))
+__global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
+    // counters only thread 0 advances (registers stay free for the labels)
+    __shared__ struct {
+        unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd, wall0;
+        long long P, t0;
+        double energy;
+        float m_ema;
+    } s_c;
 
     const DevReplica &Rg = reps[index[blockIdx.x]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -117,15 +223,22 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     const unsigned magic = Rg.magicL;
     const uint32_t key0 = Rg.key0, key1 = Rg.key1, rep = Rg.replica;
     const double T = Rg.T, E = Rg.E;
-    const float Ef = (float)E, invTf = (float)(1.0 / T);
+    const float invTf = (float)(1.0 / T);
 
     const SmemLayout lay = smem_layout(N, H1, V, words, (int)sizeof(Real));
-    Real *eps = reinterpret_cast<Real *>(smem + lay.off_eps);
-    Real *tinv = reinterpret_cast<Real *>(smem + lay.off_tinv);
-    unsigned *occ = reinterpret_cast<unsigned *>(smem + lay.off_occ);
-    unsigned *thr = reinterpret_cast<unsigned *>(smem + lay.off_thr);
-    int *disp = reinterpret_cast<int *>(smem + lay.off_disp);
-    double *tinvd = reinterpret_cast<double *>(smem + lay.off_tinvd);
+    Shared S;
+    S.eps = smem + lay.off_eps;
+    S.tinv = smem + lay.off_tinv;
+    S.occ = reinterpret_cast<unsigned *>(smem + lay.off_occ);
+    S.guide = reinterpret_cast<unsigned short *>(smem + lay.off_guide);
+    S.thr = reinterpret_cast<unsigned *>(smem + lay.off_thr);
+    S.disp = reinterpret_cast<int *>(smem + lay.off_disp);
+    S.vr64 = reinterpret_cast<double *>(smem + lay.off_vr64);
+    S.edx64 = reinterpret_cast<double *>(smem + lay.off_edx64);
+    S.vr32 = reinterpret_cast<float *>(smem + lay.off_vr32);
+    S.edx32 = reinterpret_cast<float *>(smem + lay.off_edx32);
+    Real *eps = reinterpret_cast<Real *>(S.eps);
+    const Real *tinv = reinterpret_cast<const Real *>(S.tinv);
 
     // ---- stage the replica into shared memory ----
     {
@@ -134,113 +247,123 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         const Real *tab_g = (sizeof(Real) == 8)
                                 ? reinterpret_cast<const Real *>(Rg.tinv64)
                                 : reinterpret_cast<const Real *>(Rg.tinv32);
-        for (int l = tid; l < H1 * H1; l += kThreads) tinv[l] = tab_g[l];
-        for (int l = tid; l < words; l += kThreads) occ[l] = Rg.occ[l];
+        Real *tab_s = reinterpret_cast<Real *>(S.tinv);
+        for (int l = tid; l < H1 * H1; l += kThreads) tab_s[l] = tab_g[l];
+        for (int l = tid; l < words; l += kThreads) S.occ[l] = Rg.occ[l];
+        for (int l = tid; l < kGuide; l += kThreads) S.guide[l] = Rg.guide[l];
         for (int l = tid; l < V; l += kThreads) {
-            thr[l] = Rg.thr[l];
-            disp[l] = Rg.disp[l];
-            tinvd[l] = Rg.tinvd[l];
+            const int dxy = Rg.disp[l];
+            const int dx = (int)(short)(dxy & 0xffff);
+            S.thr[l] = Rg.thr[l];
+            S.disp[l] = dxy;
+            S.vr64[l] = Rg.tinvd[l];
+            S.edx64[l] = d_mul(E, (double)dx);          // E * dx, as in the serial chain
+            S.vr32[l] = (float)Rg.tinvd[l];
+            S.edx32[l] = (float)E * (float)dx;
         }
     }
     DevCounters *cnt = Rg.ctr;
-    unsigned long long rounds = cnt->rounds, hops = cnt->hops;
-    unsigned long long attempts = cnt->attempts, evaluated = cnt->evaluated;
-    long long P = cnt->P;
-    double energy = cnt->energy;
-    unsigned long long cyc_rej = 0, cyc_upd = 0;
+    unsigned long long rounds = cnt->rounds;
+    if (tid == 0) {
+        s_c.hops = cnt->hops;
+        s_c.attempts = cnt->attempts;
+        s_c.evaluated = cnt->evaluated;
+        s_c.P = cnt->P;
+        s_c.energy = cnt->energy;
+        s_c.m_ema = cnt->m_ema > 0.f ? cnt->m_ema : 64.0f;
+        s_c.cyc_rej = 0;
+        s_c.cyc_upd = 0;
+    }
     int status = CG_OK;
     __syncthreads();
 
     const unsigned M = a.M;
-    const unsigned thr_last = thr[V - 1];
+    const unsigned thr_last = S.thr[V - 1];
     // update mapping: thread -> fixed column ux, rows uy0, uy0 + rows_per_pass, ...
     const int rows_per_pass = kThreads / L;
     const int active = rows_per_pass * L;
     const int ux = tid % L, uy0 = tid / L;
+    const bool pow2 = (L & (L - 1)) == 0;
 
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
-        long long t0 = 0;
-        unsigned long long wall0 = 0;
         if (tid == 0) {
-            t0 = clock64();
-            wall0 = globaltimer_ns();
+            s_c.t0 = clock64();
+            s_c.wall0 = globaltimer_ns();
         }
+        // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
+        // worth b ~ 64 labels (uniform: m_ema is identical in every thread)
+        unsigned C = 64;
+        {
+            const float want = sqrtf(128.0f * s_c.m_ema);
+            while (C < (unsigned)(2 * kThreads) && (float)C < want) C <<= 1;
+        }
+        const unsigned half = C >> 1;
         unsigned long long p = 0;
         unsigned q = 0, win = 0;
         bool found = false;
         while (!found) {
             ++p;
-            for (unsigned kb = 0; kb < M; kb += kThreads) {
-                const unsigned k = kb + (unsigned)tid;
-                bool acc = false;
-                unsigned i = 0, j = 0;
-                int dxy = 0;
-                double dE = 0.0;
-                if (k < M) {
-                    uint32_t x[4];
-                    philox4x32_10(k, (uint32_t)rounds, (uint32_t)(rounds >> 32), rep,
-                                  key0, key1, x);
-                    i = __umulhi(x[0], (unsigned)N);
-                    if (a.toy) {
-                        const double u = d_mul(d_add((double)x[2], 0.5), 0x1p-32);
-                        acc = u < a.toy_A0;
-                    } else if (x[1] <= thr_last) {
-                        // tower: smallest v with x1 <= C_v - 1
-                        int lo = 0, hi = V - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (x[1] <= thr[mid]) hi = mid; else lo = mid + 1;
-                        }
-                        dxy = disp[lo];
-                        const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
-                        const int yi = (int)__umulhi(i, magic), xi = (int)i - yi * L;
-                        int xj = xi + dx, yj = yi + dy;
-                        xj += (xj < 0) ? L : 0; xj -= (xj >= L) ? L : 0;
-                        yj += (yj < 0) ? L : 0; yj -= (yj >= L) ? L : 0;
-                        j = (unsigned)(yj * L + xj);
-                        const bool ni = (occ[i >> 5] >> (i & 31)) & 1u;
-                        if (ni) {
-                            const bool nj = (occ[j >> 5] >> (j & 31)) & 1u;
-                            if (!nj)
-                                acc = accept_test<Real>(eps, tinvd, lo, i, j, dx, x[2], E, T,
-                                                        Ef, invTf, dE);
-                        }
-                    }
+            for (unsigned kb = 0; kb < M; kb += C) {
+                const bool mine = (unsigned)tid < half;
+                const unsigned k0 = kb + (unsigned)tid, k1 = k0 + half;
+                const Prop p0 = propose(S, k0, rounds, rep, key0, key1, L, (unsigned)N, magic,
+                                        thr_last, mine && k0 < M);
+                const Prop p1 = propose(S, k1, rounds, rep, key0, key1, L, (unsigned)N, magic,
+                                        thr_last, mine && k1 < M);
+                double dE0 = 0.0, dE1 = 0.0;
+                bool acc0 = false, acc1 = false;
+                if (a.toy) {
+                    const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
+                    const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
+                    acc0 = mine && k0 < M && u0 < a.toy_A0;
+                    acc1 = mine && k1 < M && u1 < a.toy_A0;
+                } else {
+                    if (p0.theta) acc0 = accept<Real>(S, p0, T, invTf, dE0);
+                    if (p1.theta) acc1 = accept<Real>(S, p1, T, invTf, dE1);
                 }
-                const int any = __syncthreads_or(acc);
-                const unsigned span = (M - kb < (unsigned)kThreads) ? (M - kb) : (unsigned)kThreads;
-                evaluated += span;
+                const int any = __syncthreads_or(acc0 || acc1);
+                if (tid == 0) s_c.evaluated += (M - kb < C) ? (M - kb) : C;
                 if (any) {
-                    const unsigned b = __ballot_sync(0xffffffffu, acc);
-                    if (b) {
-                        const int first = __ffs(b) - 1;
+                    const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
+                    const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
+                    unsigned off = 0xffffffffu;
+                    if (b0) {
+                        const int first = __ffs(b0) - 1;
+                        off = (unsigned)(warp * 32 + first);
                         if (lane == first) {
-                            s_cand[warp].i = i;
-                            s_cand[warp].j = j;
-                            s_cand[warp].dxy = dxy;
-                            s_cand[warp].dE = dE;
+                            s_cand[warp].i = p0.i;
+                            s_cand[warp].j = p0.j;
+                            s_cand[warp].dxy = p0.dxy;
+                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p0, dE0);
                         }
-                        if (lane == 0) s_wlabel[warp] = (unsigned)(warp * 32 + first);
-                    } else if (lane == 0) {
-                        s_wlabel[warp] = 0xffffffffu;
+                    } else if (b1) {
+                        const int first = __ffs(b1) - 1;
+                        off = half + (unsigned)(warp * 32 + first);
+                        if (lane == first) {
+                            s_cand[warp].i = p1.i;
+                            s_cand[warp].j = p1.j;
+                            s_cand[warp].dxy = p1.dxy;
+                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p1, dE1);
+                        }
                     }
+                    if (lane == 0) s_wlabel[warp] = off;
                     __syncthreads();
                     unsigned wl = (lane < kThreads / 32) ? s_wlabel[lane] : 0xffffffffu;
 #pragma unroll
                     for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-                    q = kb + wl + 1;               // 1-based label in the round
-                    win = wl;
+                    q = kb + wl + 1;                 // 1-based label in the round
+                    win = (wl >= half ? wl - half : wl) >> 5;
                     found = true;
                     break;
                 }
             }
             if (!found) {
-                attempts += M;
+                if (tid == 0) s_c.attempts += M;
                 rounds += 1;
                 // bounded hop: thread 0 reads the wall clock, the block-wide OR
                 // makes the decision uniform
                 const int late = __syncthreads_or(
-                    tid == 0 && (globaltimer_ns() - wall0) > a.hop_timeout_ns);
+                    tid == 0 && (globaltimer_ns() - s_c.wall0) > a.hop_timeout_ns);
                 if (late) {
                     status = CG_ETIMEOUT;
                     break;
@@ -254,18 +377,21 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         if (!found) break;
 
         // ---- commit (step 3a, 3c) ----
-        const Cand c = s_cand[win >> 5];
+        const Cand c = s_cand[win];
         const unsigned ci = c.i, cj = c.j;
         const int cdx = (int)(short)(c.dxy & 0xffff), cdy = c.dxy >> 16;
-        attempts += q;
-        if (!a.toy) {
-            P += cdx;
-            energy = d_add(energy, c.dE);
-        }
         long long t1 = 0;
         if (tid == 0) {
+            const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
+            s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
+            s_c.attempts += q;
+            s_c.hops += 1;
+            if (!a.toy) {
+                s_c.P += cdx;
+                s_c.energy = d_add(s_c.energy, c.dE);
+            }
             t1 = clock64();
-            cyc_rej += (unsigned long long)(t1 - t0);
+            s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
             if (Rg.log) {
                 cg_hop e;
                 e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
@@ -274,44 +400,57 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 Rg.log[a.log_offset + h] = e;
             }
             if (!a.toy) {
-                occ[ci >> 5] &= ~(1u << (ci & 31));
-                occ[cj >> 5] |= (1u << (cj & 31));
+                S.occ[ci >> 5] &= ~(1u << (ci & 31));
+                S.occ[cj >> 5] |= (1u << (cj & 31));
             }
         }
         rounds += 1;
-        hops += 1;
 
         // ---- local-energy update (step 3b) ----
         if (!a.toy && tid < active) {
             const int yi = (int)__umulhi(ci, magic), xi = (int)ci - yi * L;
             const int yj = (int)__umulhi(cj, magic), xj = (int)cj - yj * L;
             const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
-            for (int y = uy0; y < L; y += rows_per_pass) {
-                const int fyj = fold_axis(y - yj, L), fyi = fold_axis(y - yi, L);
-                const Real ta = tinv[fyj * H1 + fxj], tb = tinv[fyi * H1 + fxi];
-                const int l = y * L + ux;
-                eps[l] = Prec<Real>::add(eps[l], Prec<Real>::sub(ta, tb));
+            const Real *colj = tinv + fxj, *coli = tinv + fxi;
+            if (pow2) {
+                const int Lm = L - 1;
+#pragma unroll 4
+                for (int y = uy0; y < L; y += rows_per_pass) {
+                    const int dj = (y - yj) & Lm, di = (y - yi) & Lm;
+                    const int fyj = min(dj, L - dj), fyi = min(di, L - di);
+                    const Real ta = colj[fyj * H1], tb = coli[fyi * H1];
+                    Real *e = eps + y * L + ux;
+                    *e = Prec<Real>::add(*e, Prec<Real>::sub(ta, tb));
+                }
+            } else {
+                for (int y = uy0; y < L; y += rows_per_pass) {
+                    const int fyj = fold_axis(y - yj, L), fyi = fold_axis(y - yi, L);
+                    const Real ta = colj[fyj * H1], tb = coli[fyi * H1];
+                    Real *e = eps + y * L + ux;
+                    *e = Prec<Real>::add(*e, Prec<Real>::sub(ta, tb));
+                }
             }
         }
         __syncthreads();
-        if (tid == 0) cyc_upd += (unsigned long long)(clock64() - t1);
+        if (tid == 0) s_c.cyc_upd += (unsigned long long)(clock64() - t1);
     }
 
     // ---- store the replica back ----
     {
         Real *eps_g = reinterpret_cast<Real *>(Rg.eps);
         for (int l = tid; l < N; l += kThreads) eps_g[l] = eps[l];
-        for (int l = tid; l < words; l += kThreads) Rg.occ[l] = occ[l];
+        for (int l = tid; l < words; l += kThreads) Rg.occ[l] = S.occ[l];
     }
     if (tid == 0) {
         cnt->rounds = rounds;
-        cnt->hops = hops;
-        cnt->attempts = attempts;
-        cnt->evaluated = evaluated;
-        cnt->P = P;
-        cnt->energy = energy;
-        cnt->cycles_reject += cyc_rej;
-        cnt->cycles_update += cyc_upd;
+        cnt->hops = s_c.hops;
+        cnt->attempts = s_c.attempts;
+        cnt->evaluated = s_c.evaluated;
+        cnt->P = s_c.P;
+        cnt->energy = s_c.energy;
+        cnt->cycles_reject += s_c.cyc_rej;
+        cnt->cycles_update += s_c.cyc_upd;
+        cnt->m_ema = s_c.m_ema;
         cnt->status = status;
     }
 }

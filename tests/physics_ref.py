@@ -43,3 +43,20 @@ def interaction_energy_batch(S, phi, nu, G):
     Sf = S.astype(np.float64)
     c = Sf - nu
     return Sf @ phi + 0.5 * np.einsum("ij,ij->i", c @ G, c)
+
+
+def coupling_kernel(L):
+    """g[dy, dx] = 1 / r for the minimum-image displacement, g[0, 0] = 0."""
+    d = np.arange(L)
+    d = np.minimum(d, L - d)
+    r = np.hypot(d[:, None], d[None, :])
+    with np.errstate(divide="ignore"):
+        return np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), 0.0)
+
+
+def site_energies_fft(n, phi, nu, L):
+    """eps = phi + G (n - nu) as a circular convolution on the L x L torus."""
+    g = coupling_kernel(L)
+    s = (n.astype(np.float64) - nu).reshape(L, L)
+    conv = np.fft.irfft2(np.fft.rfft2(g) * np.fft.rfft2(s), s=(L, L))
+    return phi + conv.reshape(-1)

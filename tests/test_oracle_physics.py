@@ -118,3 +118,13 @@ def test_field_drives_dipole_along_field():
         c.run(20_000, 32)
         drift[E] = c.counters()["P"] - P0
     assert drift[0.05] > 200 and drift[-0.05] < -200
+
+
+@pytest.mark.parametrize("L", [6, 10, 16])
+def test_fft_site_energies_equal_dense_contraction(L):
+    # the torus convolution used for large-L checks equals the dense G (n - nu)
+    n = workloads.random_occupation(L * L, L * L // 2, seed=L)
+    phi = workloads.random_phi(L * L, 1.0, seed=L + 1)
+    a = ref.site_energies(n, phi, 0.5, ref.coupling_matrix(L, L))
+    b = ref.site_energies_fft(n, phi, 0.5, L)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
