@@ -202,6 +202,41 @@ int cg_refresh(cg_handle *h);
 /* cg_refresh queued on the handle's stream without waiting (cg_sync waits). */
 int cg_refresh_async(cg_handle *h);
 
+/* The tensor-core refresh of cg_refresh for callers that cannot allocate
+ * device memory (a host program that owns the allocator, a service whose
+ * device footprint is fixed after start-up, code that must make no
+ * allocation call).  The paper has no counterpart: this is a deployment
+ * variant of the refresh, not a step of the method.
+ *
+ * Rebuilds eps of R binary32 replicas of one side L from their occupations:
+ * eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st, computed exactly as
+ * cg_refresh computes it for a tensor-core batch (split-BF16 contraction,
+ * binary64 reduction), and reports max |eps_old - eps_new| per replica.
+ *   L        even, 16 <= L <= 1024, L*L a multiple of 128
+ *   R        1 <= R <= 512
+ *   nu       filling factor of every replica
+ *   occ      device, R x ceil(L*L/32) words, replica-major; bit s%32 of word
+ *            s/32 is the occupation of site s
+ *   phi      device, R x L*L binary64 site energies
+ *   eps      device, R x L*L binary32; read (old eps) and overwritten
+ *   max_err  device, R binary64 outputs, or NULL
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream)
+ * All pointers are owned by the caller.  The call allocates nothing: its
+ * scratch is one static device array of 32 MiB that every GPU loading the
+ * library holds until the process exits; sizes that need more scratch
+ * (noalloc bytes ~ 2 N R_pad + 32 N R_pad + small tables, R_pad = R rounded
+ * up to 16) return CG_EINVAL with the limit in the message.  The first call
+ * on a device looks up the array's device address (once per device) and
+ * should come before any stream capture.  Every call shares the array and
+ * leaves its contents behind: calls that overlap on the GPU (other streams,
+ * other host threads, same device) race and must be serialised by the
+ * caller.  The call waits for its stream before returning.
+ * Returns CG_OK, CG_EINVAL, CG_ECUDA, or CG_ETIMEOUT if a bounded device wait
+ * ran out. */
+int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int *occ,
+                          const double *phi, float *eps, double *max_err,
+                          void *stream);
+
 /* Peak-rate microbenchmarks of the device (no handle needed):
  *   kind 0: shared-memory read-modify-write bandwidth of 32-bit words, bytes/s
  *   kind 1: binary64 add throughput, adds/s

@@ -30,6 +30,7 @@ EXPORTED = [
     "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_version",
+    "cg_refresh_tc_noalloc",
 ]
 
 
@@ -127,6 +128,8 @@ def load(path: str | None = None):
             "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
             "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
             "cg_version": (ctypes.c_char_p, []),
+            "cg_refresh_tc_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                     vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -287,6 +290,14 @@ def cg_microbench(kind, device=0) -> float:
     out = ctypes.c_double(0.0)
     _check(load().cg_microbench(kind, device, ctypes.byref(out)))
     return out.value
+
+
+def cg_refresh_tc_noalloc(L, R, nu, occ_ptr, phi_ptr, eps_ptr, max_err_ptr=None, stream=None):
+    """Device pointers (ints) in, CG status out; raises on error."""
+    return _check(load().cg_refresh_tc_noalloc(
+        L, R, nu, ctypes.c_void_p(occ_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(eps_ptr),
+        ctypes.c_void_p(max_err_ptr) if max_err_ptr else None,
+        ctypes.c_void_p(stream) if stream else None))
 
 
 def cg_set_toy_acceptance(h, A0):

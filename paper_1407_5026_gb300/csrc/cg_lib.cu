@@ -708,6 +708,11 @@ int finish_run(cg_handle *h)
 
 }  // namespace
 
+namespace cg {
+// Error message for entry points defined in other translation units.
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace cg
+
 extern "C" {
 
 const char *cg_version(void) { return "cg-pr 0.1 (sm_103a)"; }
