@@ -35,6 +35,22 @@ WORKLOAD = dict(L=128, nu=0.5, W=2.0, xi=1.0, r_max=8, T=0.01, E=0.005)
 HOPS_PER_STEP = 1024          # one refresh period
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 
+# DRAM bytes (read + write) of one launch of the persistent kernel in this
+# workload (304 replicas x 1024 hops), from the ncu capture summarised in
+# profiles/pr_persistent_fp32_L128_R304_relaxed.md; valid only while the
+# kernel sources hash to the captured version.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "1cc8713741233dd3", "bytes_per_launch": 30.7e6,
+                   "replicas": 304, "hops_per_replica": 1024}
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("cg_pr_kernel.cu", "cg_pr_common.cuh", "cg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1407_5026_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -327,7 +343,11 @@ def run_ours(args):
                    "state": f"chains relaxed {args.relax_steps * HOPS_PER_STEP} hops from "
                             f"their random start, then {args.warmup} warm-up steps"},
         "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": smem_peak / 1e9,
-                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / smem_peak,
+                     "traffic": (TRAFFIC_CAPTURE["bytes_per_launch"]
+                                 if (kernel_sources_hash() == TRAFFIC_CAPTURE["sources_sha256_16"]
+                                     and R == TRAFFIC_CAPTURE["replicas"]) else None),
+                     "traffic_unit": "DRAM bytes per launch (ncu capture)",
                      "kernel": "pr_persistent<float>",
                      "bytes_per_hop": bytes_per_hop,
                      "peak_source": "measured: shared-memory 32-bit read-modify-write "

@@ -89,7 +89,11 @@ typedef struct {
     uint32_t hop_timeout_ms;    /* wall-clock limit of one hop on the device
                                    (0 = 10000 ms); past it the launch stops
                                    with CG_ETIMEOUT, the state stays valid    */
-    uint32_t pad_;
+    int32_t cluster_size;       /* CTAs per replica: 0 = automatic (one CTA when
+                                   the replica fits its shared memory, else the
+                                   smallest of 2, 4, 8 that fits); 2, 4 or 8
+                                   force a thread-block cluster that splits
+                                   eps by rows                                 */
 } cg_opts;
 
 /* Counters of one replica (step 3 of the mixed PR algorithm). */

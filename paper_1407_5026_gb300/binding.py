@@ -53,7 +53,7 @@ class cg_opts(ctypes.Structure):
                 ("refresh_every", ctypes.c_uint32), ("block_threads", ctypes.c_int32),
                 ("max_rounds_per_hop", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("hop_timeout_ms", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
+                ("hop_timeout_ms", ctypes.c_uint32), ("cluster_size", ctypes.c_int32)]
 
 
 class cg_counters(ctypes.Structure):
@@ -155,11 +155,12 @@ def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0):
 
 
 def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,
-         max_rounds_per_hop=0, device=0, use_graph=0, stream=None, hop_timeout_ms=0):
+         max_rounds_per_hop=0, device=0, use_graph=0, stream=None, hop_timeout_ms=0,
+         cluster_size=0):
     return cg_opts(precision=precision, refresh_kind=refresh_kind, refresh_every=refresh_every,
                    block_threads=block_threads, max_rounds_per_hop=max_rounds_per_hop,
                    device=device, use_graph=use_graph, stream=stream,
-                   hop_timeout_ms=hop_timeout_ms)
+                   hop_timeout_ms=hop_timeout_ms, cluster_size=cluster_size)
 
 
 # ---- the C entry points, one to one ----
@@ -326,7 +327,7 @@ class System:
 
     def __init__(self, reps, precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO,
                  block_threads=0, max_rounds_per_hop=0, device=0, torch_memory=True,
-                 hop_timeout_ms=0):
+                 hop_timeout_ms=0, cluster_size=0, use_graph=0):
         import torch
         self.reps = [r if isinstance(r, dict) else r for r in reps]
         torch.cuda.set_device(device)
@@ -336,7 +337,8 @@ class System:
         self.opts = opts(precision=precision, refresh_every=refresh_every,
                          refresh_kind=refresh_kind, block_threads=block_threads,
                          max_rounds_per_hop=max_rounds_per_hop, device=device,
-                         stream=self.stream.cuda_stream, hop_timeout_ms=hop_timeout_ms)
+                         stream=self.stream.cuda_stream, hop_timeout_ms=hop_timeout_ms,
+                         cluster_size=cluster_size, use_graph=use_graph)
         self.workspace = None
         if torch_memory:
             nbytes = cg_workspace_bytes(self.reps, self.opts)

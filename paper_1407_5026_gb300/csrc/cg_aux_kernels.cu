@@ -136,9 +136,12 @@ __global__ void debug_philox_kernel(const uint32_t *ctr, const uint32_t *key, ui
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    // the split form the PR kernels use (prefix shared by counters that differ
+    // only in word 0)
     uint32_t x[4];
-    philox4x32_10(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3], key[2 * t],
-                  key[2 * t + 1], x);
+    const PhiloxPrefix P = philox_prefix(ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3],
+                                         key[2 * t], key[2 * t + 1]);
+    philox_finish(ctr[4 * t], P, key[2 * t], key[2 * t + 1], x);
     for (int w = 0; w < 4; ++w) out[4 * t + w] = x[w];
 }
 

@@ -40,6 +40,62 @@ __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1,
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// Philox-4x32-10 split for counters (k, c1, c2, c3) whose words 1-3 are shared
+// by many k: the parts of rounds 1 and 2 that do not depend on k are computed
+// once (philox_prefix) and each k finishes the block (philox_finish).  The
+// result is the same block as philox4x32_10(k, c1, c2, c3, k0, k1).
+struct PhiloxPrefix {
+    uint32_t A;     // c3 ^ k0-round-1 key word 1
+    uint32_t B;     // round-2 high product of word 0, ^ key word 1
+    uint32_t C;     // round-1 word 1, ^ round-2 key word 0
+    uint32_t x3;    // round-2 low product of word 0 (the output's word 3 after round 2)
+};
+
+__device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t c1, uint32_t c2, uint32_t c3,
+                                                      uint32_t k0, uint32_t k1)
+{
+    PhiloxPrefix P;
+    // round 1: word 0 of the output and word 1 come from c1, c2 alone
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1;
+    P.A = c3 ^ k1;
+    // round 2 (keys bumped once): the product of word 0 is shared
+    const uint32_t k0b = k0 + 0x9E3779B9u, k1b = k1 + 0xBB67AE85u;
+    P.B = __umulhi(0xD2511F53u, n0) ^ k1b;
+    P.x3 = 0xD2511F53u * n0;
+    P.C = n1 ^ k0b;
+    return P;
+}
+
+__device__ __forceinline__ void philox_finish(uint32_t k, const PhiloxPrefix &P, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4])
+{
+    // round 1, the k-dependent half
+    const uint32_t n2 = __umulhi(0xD2511F53u, k) ^ P.A, n3 = 0xD2511F53u * k;
+    // round 2, the n2-dependent half
+    uint32_t c0 = __umulhi(0xCD9E8D57u, n2) ^ P.C;
+    uint32_t c1 = 0xCD9E8D57u * n2;
+    uint32_t c2 = P.B ^ n3;
+    uint32_t c3 = P.x3;
+    k0 += 2u * 0x9E3779B9u;
+    k1 += 2u * 0xBB67AE85u;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        if (r > 2) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, nn2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = nn2;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
 // Round-to-nearest binary64 operations that are never contracted to FMA.
 __device__ __forceinline__ double d_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double d_sub(double a, double b) { return __dsub_rn(a, b); }

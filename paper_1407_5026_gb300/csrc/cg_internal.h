@@ -103,8 +103,12 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int H1, int V, int word
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps,
                                  const int *d_index, int n_ctas, int threads,
                                  int smem_bytes, const RunArgs &args,
-                                 cudaStream_t st);
-int pr_persistent_max_threads(int precision);
+                                 cudaStream_t st, int L);
+// The same chain over a thread-block cluster of `cluster` CTAs per replica
+// (eps split by rows); grid = n_reps * cluster CTAs.
+cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
+                              int n_reps, int cluster, int threads, int smem_bytes,
+                              const RunArgs &args, cudaStream_t st, int L);
 cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int H1, int words,
                             int precision, cudaStream_t st);
 cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int words,

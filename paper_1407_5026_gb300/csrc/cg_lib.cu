@@ -175,6 +175,7 @@ struct Rep {
 
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
+    int cluster = 1;                 // CTAs per replica
     bool tc = false;                 // refresh on the tensor cores
     unsigned char *d_img = nullptr;  // S image scratch of the tensor-core refresh
     int *d_err = nullptr;            // its error word
@@ -262,10 +263,29 @@ int check_desc(const cg_replica_desc &d)
     return CG_OK;
 }
 
-int persistent_smem(const Rep &r, int precision)
+int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
     const int rb = precision == CG_FP64 ? 8 : 4;
-    return smem_layout(r.N, r.tab->H1, r.tab->V, r.words, rb).total;
+    return smem_layout(r.N / cluster, r.tab->H1, r.tab->V, r.words, rb).total;
+}
+
+// CTAs per replica: 1 when the replica fits one CTA's shared memory, else the
+// smallest cluster of 2, 4 or 8 CTAs (each holding L/C rows of eps) that fits;
+// a forced size is used when it fits.  0 when nothing fits.
+int choose_cluster(const cg_opts &o, const Rep &r, int optin)
+{
+    const int budget = optin - 1024;
+    if (o.cluster_size > 1) {
+        const int c = o.cluster_size;
+        if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
+            persistent_smem(r, o.precision, c) <= budget)
+            return c;
+        return 0;
+    }
+    if (persistent_smem(r, o.precision, 1) <= budget) return 1;
+    for (int c = 2; c <= 8; c *= 2)
+        if (r.d.L % c == 0 && persistent_smem(r, o.precision, c) <= budget) return c;
+    return 0;
 }
 
 int choose_threads(const cg_opts &o, int L, int smem)
@@ -511,10 +531,10 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             r.tab = t.get();
             h->tables.push_back(std::move(t));
         }
-        const int smem = persistent_smem(r, o.precision);
-        if (smem + 1024 > optin) {
-            fail(CG_EINVAL, "replica does not fit one CTA's shared memory (L too large for "
-                            "this precision)");
+        if (choose_cluster(o, r, optin) == 0) {
+            fail(CG_EINVAL, "replica does not fit the shared memory of one CTA or of a "
+                            "cluster of up to 8 CTAs (or the forced cluster size does not "
+                            "fit / divide L)");
             destroy_partial();
             return nullptr;
         }
@@ -554,14 +574,18 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         Group g;
         g.L = h->reps[order[k]].d.L;
         g.first = k;
-        int smem = 0;
+        int smem = 0, cluster = 1;
+        for (int m = k; m < R && h->reps[order[m]].d.L == g.L; ++m)
+            cluster = std::max(cluster, choose_cluster(o, h->reps[order[m]], optin));
         while (k < R && h->reps[order[k]].d.L == g.L) {
-            smem = std::max(smem, persistent_smem(h->reps[order[k]], o.precision));
+            smem = std::max(smem, persistent_smem(h->reps[order[k]], o.precision, cluster));
             ++k;
         }
         g.count = k - g.first;
         g.smem = smem;
+        g.cluster = cluster;
         g.threads = choose_threads(o, g.L, smem);
+        if (cluster > 1 && g.threads < 512) g.threads = 512;
         g.tc = group_uses_tc(o, g.L, g.count);
         if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.count)) ||
                      dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
@@ -615,9 +639,14 @@ int launch_segment(cg_handle *h, unsigned long long hops, unsigned M, unsigned l
     a.hop_timeout_ns = 1000000ull * (h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u);
     a.toy = h->toy;
     a.toy_A0 = h->toy_A0;
-    for (const Group &g : h->groups)
-        CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
-                                     g.threads, g.smem, a, h->st));
+    for (const Group &g : h->groups) {
+        if (g.cluster > 1)
+            CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first,
+                                      g.count, g.cluster, g.threads, g.smem, a, h->st, g.L));
+        else
+            CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first,
+                                         g.count, g.threads, g.smem, a, h->st, g.L));
+    }
     return CG_OK;
 }
 

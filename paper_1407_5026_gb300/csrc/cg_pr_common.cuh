@@ -1,0 +1,200 @@
+// cg_pr_common.cuh -- per-label building blocks of the persistent PR kernels
+// (single CTA and thread-block cluster): Philox proposal, tower sampling,
+// theta, and the Metropolis test in binary64 and binary32.
+#pragma once
+
+#include "cg_device.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+
+struct Cand {
+    unsigned int i, j;
+    int dxy;
+    unsigned int pad_;
+    double dE;
+};
+
+template <typename Real>
+struct Prec;
+
+template <>
+struct Prec<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return d_add(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return d_sub(a, b); }
+};
+
+template <>
+struct Prec<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Binary32 value of a binary64 from its high word: truncated to 20 mantissa
+// bits (relative error < 2^-20); integer operations only.  Returns 0 when
+// |x| < 2^-126 (callers fall back to the exact path).
+__device__ __forceinline__ float approx_f32(double x)
+{
+    const int hi = __double2hiint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex < 1023 - 126 || ex > 1023 + 127) return 0.0f;
+    const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(ex - 896) << 23) |
+                          (((unsigned)hi & 0xfffffu) << 3);
+    return __uint_as_float(bits);
+}
+
+struct Shared {
+    void *eps;
+    void *tinv;
+    unsigned *occ;
+    unsigned short *guide;
+    unsigned *thr;
+    int *disp;
+    double *vr64, *edx64;
+    float *vr32, *edx32;
+};
+
+struct Prop {
+    unsigned i, j;
+    int v, dxy;
+    uint32_t x2;
+    bool theta;
+};
+
+// Step 1 of one label (Philox, site, tower, destination) and theta.  P is the
+// Philox prefix of the label's round (counter words 1-3); kPow2 selects shift
+// and mask site arithmetic when L is a power of two (log2L its exponent).
+template <bool kPow2>
+__device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const PhiloxPrefix &P,
+                                        uint32_t key0, uint32_t key1, int L, int log2L,
+                                        unsigned N, unsigned magic, unsigned thr_last,
+                                        bool valid)
+{
+    Prop p;
+    uint32_t x[4];
+    philox_finish(k, P, key0, key1, x);
+    p.x2 = x[2];
+    p.i = __umulhi(x[0], N);
+    p.theta = false;
+    p.j = 0;
+    p.v = 0;
+    p.dxy = 0;
+    const uint32_t x1 = x[1];
+    if (!valid || x1 > thr_last) return p;       // beyond M, or a null proposal
+    const unsigned g = S.guide[x1 >> (32 - kGuideBits)];
+    int v = (int)(g & 0x7fffu);
+    if (g & 0x8000u)
+        while (x1 > S.thr[v]) ++v;               // the bucket holds a threshold
+    const int dxy = S.disp[v];
+    const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
+    if (kPow2) {
+        const int Lm = L - 1;
+        const int xj = ((int)p.i + dx) & Lm;
+        const int yj = (((int)p.i >> log2L) + dy) & Lm;
+        p.j = (unsigned)((yj << log2L) | xj);
+    } else {
+        const int yi = (int)__umulhi(p.i, magic), xi = (int)p.i - yi * L;
+        int xj = xi + dx, yj = yi + dy;
+        xj += (xj < 0) ? L : 0;
+        xj -= (xj >= L) ? L : 0;
+        yj += (yj < 0) ? L : 0;
+        yj -= (yj >= L) ? L : 0;
+        p.j = (unsigned)(yj * L + xj);
+    }
+    p.v = v;
+    p.dxy = dxy;
+    const unsigned wi = S.occ[p.i >> 5], wj = S.occ[p.j >> 5];
+    p.theta = ((wi >> (p.i & 31)) & 1u) && !((wj >> (p.j & 31)) & 1u);
+    return p;
+}
+
+// Step 2 (accept test) for a proposal whose theta holds, from the two local
+// energies (read from this CTA's shared memory or a cluster peer's).
+template <typename Real>
+__device__ __forceinline__ bool accept_vals(Real ei, Real ej, const Shared &S, const Prop &p,
+                                            double T, float invTf, double &dE_out);
+
+template <>
+__device__ __forceinline__ bool accept_vals<double>(double ei, double ej, const Shared &S,
+                                                    const Prop &p, double T, float invTf,
+                                                    double &dE_out)
+{
+    double d = d_sub(ej, ei);
+    d = d_sub(d, S.vr64[p.v]);
+    const double dE = d_sub(d, S.edx64[p.v]);
+    dE_out = dE;
+    if (dE <= 0.0) return true;
+    // binary32 estimate of y = -dE/T and of e^y, then a margin test
+    const float df = approx_f32(dE);
+    if (df > 0.0f) {
+        const float y = -df * invTf;
+        if (y < -23.01f) return false;                      // e^y below every u
+        const float e = __expf(y);
+        // u ~ x2 2^-32 differs from (x2 + 1/2) 2^-32 by at most 2^-33 plus a
+        // relative 2^-24: the absolute slack 2^-31 covers the first, the
+        // relative margin the second and the exponential's error
+        const float u = __uint2float_rn(p.x2) * 0x1p-32f;
+        if (u + 0x1p-31f < e * (1.0f - 2e-4f)) return true;
+        if (u > e * (1.0f + 2e-4f) + 0x1p-31f) return false;
+    }
+    const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
+    return u < cg_exp_accept(d_div(-dE, T));
+}
+
+template <>
+__device__ __forceinline__ bool accept_vals<float>(float ei, float ej, const Shared &S,
+                                                   const Prop &p, double T, float invTf,
+                                                   double &dE_out)
+{
+    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(ej, ei), S.vr32[p.v]), S.edx32[p.v]);
+    if (fabsf(dEf) < 1e-5f) {
+        // near tie: decide in binary64 from the widened energies
+        double d = d_sub((double)ej, (double)ei);
+        d = d_sub(d, S.vr64[p.v]);
+        const double dE = d_sub(d, S.edx64[p.v]);
+        dE_out = dE;
+        if (dE <= 0.0) return true;
+        const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
+        return u < cg_exp_accept(d_div(-dE, T));
+    }
+    dE_out = 0.0;   // widened for the executed hop only
+    if (dEf <= 0.0f) return true;
+    const float u = ((float)(p.x2 >> 9) + 0.5f) * 0x1p-23f;
+    return u < __expf(-dEf * invTf);
+}
+
+template <typename Real>
+__device__ __forceinline__ bool accept(const Shared &S, const Prop &p, double T, float invTf,
+                                       double &dE_out)
+{
+    const Real *eps = reinterpret_cast<const Real *>(S.eps);
+    return accept_vals<Real>(eps[p.i], eps[p.j], S, p, T, invTf, dE_out);
+}
+
+// dH of the executed hop in binary64 (the binary32 form widens it here, once
+// per hop, instead of on every label).
+template <typename Real>
+__device__ __forceinline__ double hop_dE_vals(Real ei, Real ej, const Shared &S, const Prop &p,
+                                              double dE)
+{
+    if (sizeof(Real) == 8 || dE != 0.0) return dE;
+    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn((float)ej, (float)ei), S.vr32[p.v]),
+                                S.edx32[p.v]);
+    return (double)dEf;
+}
+
+template <typename Real>
+__device__ __forceinline__ double hop_dE(const Shared &S, const Prop &p, double dE)
+{
+    const Real *eps = reinterpret_cast<const Real *>(S.eps);
+    return hop_dE_vals<Real>(eps[p.i], eps[p.j], S, p, dE);
+}
+
+}  // namespace cg

@@ -33,176 +33,11 @@
 // exponential, so every decision is the binary64 one.
 // Binary32 form: eps, the table and dH in binary32 (dH in binary64 when
 // |dH| < 1e-5), exp from the fast intrinsic.
-#include "cg_device.cuh"
-#include "cg_internal.h"
+#include "cg_pr_common.cuh"
 
 namespace cg {
 
-struct Cand {
-    unsigned int i, j;
-    int dxy;
-    unsigned int pad_;
-    double dE;
-};
-
-template <typename Real>
-struct Prec;
-
-template <>
-struct Prec<double> {
-    static __device__ __forceinline__ double add(double a, double b) { return d_add(a, b); }
-    static __device__ __forceinline__ double sub(double a, double b) { return d_sub(a, b); }
-};
-
-template <>
-struct Prec<float> {
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-};
-
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Binary32 value of a binary64 from its high word: truncated to 20 mantissa
-// bits (relative error < 2^-20); integer operations only.  Returns 0 when
-// |x| < 2^-126 (callers fall back to the exact path).
-__device__ __forceinline__ float approx_f32(double x)
-{
-    const int hi = __double2hiint(x);
-    const int ex = (hi >> 20) & 0x7ff;
-    if (ex < 1023 - 126 || ex > 1023 + 127) return 0.0f;
-    const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(ex - 896) << 23) |
-                          (((unsigned)hi & 0xfffffu) << 3);
-    return __uint_as_float(bits);
-}
-
-struct Shared {
-    void *eps;
-    void *tinv;
-    unsigned *occ;
-    unsigned short *guide;
-    unsigned *thr;
-    int *disp;
-    double *vr64, *edx64;
-    float *vr32, *edx32;
-};
-
-struct Prop {
-    unsigned i, j;
-    int v, dxy;
-    uint32_t x2;
-    bool theta;
-};
-
-// Step 1 of one label (Philox, site, tower, destination) and theta.
-__device__ __forceinline__ Prop propose(const Shared &S, unsigned k, unsigned long long r,
-                                        uint32_t rep, uint32_t key0, uint32_t key1, int L,
-                                        unsigned N, unsigned magic, unsigned thr_last,
-                                        bool valid)
-{
-    Prop p;
-    uint32_t x[4];
-    philox4x32_10(k, (uint32_t)r, (uint32_t)(r >> 32), rep, key0, key1, x);
-    p.x2 = x[2];
-    p.i = __umulhi(x[0], N);
-    p.theta = false;
-    p.j = 0;
-    p.v = 0;
-    p.dxy = 0;
-    const uint32_t x1 = x[1];
-    if (!valid || x1 > thr_last) return p;       // beyond M, or a null proposal
-    const unsigned g = S.guide[x1 >> (32 - kGuideBits)];
-    int v = (int)(g & 0x7fffu);
-    if (g & 0x8000u)
-        while (x1 > S.thr[v]) ++v;               // the bucket holds a threshold
-    const int dxy = S.disp[v];
-    const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
-    const int yi = (int)__umulhi(p.i, magic), xi = (int)p.i - yi * L;
-    int xj = xi + dx, yj = yi + dy;
-    xj += (xj < 0) ? L : 0;
-    xj -= (xj >= L) ? L : 0;
-    yj += (yj < 0) ? L : 0;
-    yj -= (yj >= L) ? L : 0;
-    p.j = (unsigned)(yj * L + xj);
-    p.v = v;
-    p.dxy = dxy;
-    const unsigned wi = S.occ[p.i >> 5], wj = S.occ[p.j >> 5];
-    p.theta = ((wi >> (p.i & 31)) & 1u) && !((wj >> (p.j & 31)) & 1u);
-    return p;
-}
-
-// Step 2 (accept test) for a proposal whose theta holds.
-template <typename Real>
-__device__ __forceinline__ bool accept(const Shared &S, const Prop &p, double T, float invTf,
-                                       double &dE_out);
-
-template <>
-__device__ __forceinline__ bool accept<double>(const Shared &S, const Prop &p, double T,
-                                               float invTf, double &dE_out)
-{
-    const double *eps = reinterpret_cast<const double *>(S.eps);
-    double d = d_sub(eps[p.j], eps[p.i]);
-    d = d_sub(d, S.vr64[p.v]);
-    const double dE = d_sub(d, S.edx64[p.v]);
-    dE_out = dE;
-    if (dE <= 0.0) return true;
-    // binary32 estimate of y = -dE/T and of e^y, then a margin test
-    const float df = approx_f32(dE);
-    if (df > 0.0f) {
-        const float y = -df * invTf;
-        if (y < -23.01f) return false;                      // e^y below every u
-        const float e = __expf(y);
-        // u ~ x2 2^-32 differs from (x2 + 1/2) 2^-32 by at most 2^-33 plus a
-        // relative 2^-24: the absolute slack 2^-31 covers the first, the
-        // relative margin the second and the exponential's error
-        const float u = __uint2float_rn(p.x2) * 0x1p-32f;
-        if (u + 0x1p-31f < e * (1.0f - 2e-4f)) return true;
-        if (u > e * (1.0f + 2e-4f) + 0x1p-31f) return false;
-    }
-    const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
-    return u < cg_exp_accept(d_div(-dE, T));
-}
-
-template <>
-__device__ __forceinline__ bool accept<float>(const Shared &S, const Prop &p, double T,
-                                              float invTf, double &dE_out)
-{
-    const float *eps = reinterpret_cast<const float *>(S.eps);
-    const float ei = eps[p.i], ej = eps[p.j];
-    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(ej, ei), S.vr32[p.v]), S.edx32[p.v]);
-    if (fabsf(dEf) < 1e-5f) {
-        // near tie: decide in binary64 from the widened energies
-        double d = d_sub((double)ej, (double)ei);
-        d = d_sub(d, S.vr64[p.v]);
-        const double dE = d_sub(d, S.edx64[p.v]);
-        dE_out = dE;
-        if (dE <= 0.0) return true;
-        const double u = d_mul(d_add((double)p.x2, 0.5), 0x1p-32);
-        return u < cg_exp_accept(d_div(-dE, T));
-    }
-    dE_out = 0.0;   // widened for the executed hop only
-    if (dEf <= 0.0f) return true;
-    const float u = ((float)(p.x2 >> 9) + 0.5f) * 0x1p-23f;
-    return u < __expf(-dEf * invTf);
-}
-
-// dH of the executed hop in binary64 (the binary32 form widens it here, once
-// per hop, instead of on every label).
-template <typename Real>
-__device__ __forceinline__ double hop_dE(const Shared &S, const Prop &p, double dE)
-{
-    if (sizeof(Real) == 8 || dE != 0.0) return dE;
-    const float *eps = reinterpret_cast<const float *>(S.eps);
-    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(eps[p.j], eps[p.i]), S.vr32[p.v]),
-                                S.edx32[p.v]);
-    return (double)dEf;
-}
-
-template <typename Real, int kThreads>
+template <typename Real, int kThreads, bool kPow2>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
@@ -283,7 +118,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     const int rows_per_pass = kThreads / L;
     const int active = rows_per_pass * L;
     const int ux = tid % L, uy0 = tid / L;
-    const bool pow2 = (L & (L - 1)) == 0;
+    const int log2L = __ffs(L) - 1;      // used when L is a power of two
 
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
         if (tid == 0) {
@@ -303,13 +138,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         bool found = false;
         while (!found) {
             ++p;
+            const PhiloxPrefix PP =
+                philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
             for (unsigned kb = 0; kb < M; kb += C) {
                 const bool mine = (unsigned)tid < half;
                 const unsigned k0 = kb + (unsigned)tid, k1 = k0 + half;
-                const Prop p0 = propose(S, k0, rounds, rep, key0, key1, L, (unsigned)N, magic,
-                                        thr_last, mine && k0 < M);
-                const Prop p1 = propose(S, k1, rounds, rep, key0, key1, L, (unsigned)N, magic,
-                                        thr_last, mine && k1 < M);
+                const Prop p0 = propose<kPow2>(S, k0, PP, key0, key1, L, log2L, (unsigned)N,
+                                               magic, thr_last, mine && k0 < M);
+                const Prop p1 = propose<kPow2>(S, k1, PP, key0, key1, L, log2L, (unsigned)N,
+                                               magic, thr_last, mine && k1 < M);
                 double dE0 = 0.0, dE1 = 0.0;
                 bool acc0 = false, acc1 = false;
                 if (a.toy) {
@@ -412,7 +249,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             const int yj = (int)__umulhi(cj, magic), xj = (int)cj - yj * L;
             const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
             const Real *colj = tinv + fxj, *coli = tinv + fxi;
-            if (pow2) {
+            if (kPow2) {
                 const int Lm = L - 1;
 #pragma unroll 4
                 for (int y = uy0; y < L; y += rows_per_pass) {
@@ -457,24 +294,34 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 
 template <typename Real, int kThreads>
 static cudaError_t launch_t(const DevReplica *d_reps, const int *d_index, int n_ctas,
-                            int smem_bytes, const RunArgs &args, cudaStream_t st)
+                            int smem_bytes, const RunArgs &args, cudaStream_t st, bool pow2)
 {
-    pr_persistent<Real, kThreads><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+    if (pow2)
+        pr_persistent<Real, kThreads, true>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+    else
+        pr_persistent<Real, kThreads, false>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
     return cudaGetLastError();
+}
+
+template <typename Real, int kThreads>
+static cudaError_t set_smem_one(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e) return e;
+    return cudaFuncSetAttribute(pr_persistent<Real, kThreads, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <typename Real>
 static cudaError_t set_smem_t(int bytes)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pr_persistent<Real, 1024>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    if ((e = cudaFuncSetAttribute(pr_persistent<Real, 512>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    return cudaFuncSetAttribute(pr_persistent<Real, 256>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if ((e = set_smem_one<Real, 1024>(bytes))) return e;
+    if ((e = set_smem_one<Real, 512>(bytes))) return e;
+    return set_smem_one<Real, 256>(bytes);
 }
 
 cudaError_t set_pr_smem_limit(int precision, int bytes)
@@ -484,19 +331,20 @@ cudaError_t set_pr_smem_limit(int precision, int bytes)
 
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const int *d_index,
                                  int n_ctas, int threads, int smem_bytes, const RunArgs &args,
-                                 cudaStream_t st)
+                                 cudaStream_t st, int L)
 {
+    const bool pow2 = (L & (L - 1)) == 0;
     if (precision == CG_FP64) {
         switch (threads) {
-        case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st);
-        case 512: return launch_t<double, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st);
-        case 256: return launch_t<double, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st);
+        case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 512: return launch_t<double, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 256: return launch_t<double, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
         }
     } else {
         switch (threads) {
-        case 1024: return launch_t<float, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st);
-        case 512: return launch_t<float, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st);
-        case 256: return launch_t<float, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st);
+        case 1024: return launch_t<float, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 512: return launch_t<float, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 256: return launch_t<float, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
         }
     }
     return cudaErrorInvalidValue;
