@@ -77,6 +77,20 @@ def dist_env():
     return ws, rank, local
 
 
+def combine_ranks(total_s, hops, attempts, device=None):
+    """Whole-job numbers over the ranks: the slowest rank's time, summed hops
+    and attempts (replicas only: no collective touches the chains)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return total_s, float(hops), float(attempts)
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    s = torch.tensor([float(hops), float(attempts)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(s[0]), float(s[1])
+
+
 def replicas_for(rank, R):
     from paper_1407_5026_gb300.workloads import Replica
     base = rank * R
@@ -309,15 +323,8 @@ def run_ours(args):
     cyc_rej = sum(o1["cycles_reject"] - o0["cycles_reject"] for o0, o1 in zip(obs0, obs1))
     max_err = max(o["max_eps_err_last_refresh"] for o in obs1)
 
-    if ws > 1:
-        t = torch.tensor([total_s, float(hops), float(attempts)], device=f"cuda:{local}",
-                         dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_s_all, hops_all, att_all = float(tmax[0]), float(t[1]), float(t[2])
-    else:
-        total_s_all, hops_all, att_all = total_s, float(hops), float(attempts)
+    total_s_all, hops_all, att_all = combine_ranks(total_s, hops, attempts,
+                                                   device=f"cuda:{local}")
 
     # roofline of the dominant kernel (the persistent PR kernel): algorithmic
     # bytes of the eps update per launch / mean launch time
@@ -389,6 +396,19 @@ def run_ours(args):
             result[key] = {"hops_per_s": dh / dt, "attempts_per_s": da / dt, "replicas": 1,
                            "hops": dh, "acceptance": dh / max(1, da),
                            "state": f"after {relax} hops from the random start"}
+            if prec == B.CG_FP32 and clk:
+                # eps-update phase of one replica alone on its SM: algorithmic
+                # bytes over the update-phase time (SM clock cycles of the
+                # update, thread 0's clock64) against one SM's share of the
+                # measured shared-memory peak
+                cyc = o1["cycles_update"] - o0["cycles_update"]
+                t_upd = cyc / (clk["sm_mhz"] * 1e6)
+                bw = dh * bytes_per_hop / t_upd
+                per_sm = smem_peak / sms
+                result[key]["update_phase"] = {
+                    "achieved_GBps": bw / 1e9, "peak_per_sm_GBps": per_sm / 1e9,
+                    "frac": bw / per_sm, "update_time_frac": cyc / max(
+                        1, cyc + o1["cycles_reject"] - o0["cycles_reject"])}
             s1.close()
         result["fp64_form"]["update_bound_dadd_per_hop"] = 2 * N
         result["fp64_form"]["dadd_peak_per_s"] = dadd_peak

@@ -164,9 +164,14 @@ int cg_num_replicas(const cg_handle *h);
 int cg_num_sites(const cg_handle *h, int replica);
 
 /* Advance every replica by n_hops executed hops with M labels per round
- * (1 <= M <= 2^24).  Blocks until the work is done.  FP32 handles refresh
- * eps every refresh_every hops.  Returns CG_ESTUCK if some replica reached
- * max_rounds_per_hop; other replicas still completed their hops. */
+ * (mixed PR algorithm, steps 1-3; 1 <= M <= 2^24, or M = 0 for each lattice
+ * size's own M: 4096 unless cg_autotune chose another).  Blocks until the
+ * work is done.  FP32 handles refresh eps every refresh_every hops.  Replicas
+ * of different L run as concurrent launches (one stream each, forked from and
+ * joined to the handle's stream); with opts.use_graph the launches of each
+ * distinct (n_hops, M, refresh phase) are captured once in a CUDA graph and
+ * replayed.  Returns CG_ESTUCK if some replica reached max_rounds_per_hop;
+ * other replicas still completed their hops. */
 int cg_run(cg_handle *h, uint64_t n_hops, uint32_t M);
 
 /* cg_run without the final wait: the work is queued on the handle's stream
@@ -247,6 +252,22 @@ int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int *occ,
  *   kind 2: shared-memory read-modify-write bandwidth of 64-bit words, bytes/s
  * summed over all SMs; result written to *result. */
 int cg_microbench(int kind, int device, double *result);
+
+/* Launch-shape autotuner.  The parallel-rejection section recommends M near
+ * 1/A but larger than the number of concurrent threads; the best M and CTA
+ * size depend on the GPU, so for every group of replicas with one L this
+ * times the persistent launch for CTA sizes 256, 512, 1024 (those that fit)
+ * and M in {1024, 4096, 16384} over hops_per_trial hops (0: 256) on a copy of
+ * the group's state, restores the state bit for bit, and keeps the fastest
+ * (cg_run with M = 0 then uses it).  With $CG_TUNE_CACHE naming a JSON file,
+ * cached shapes are reused and new ones added.  Allocates a temporary device
+ * snapshot; captured graphs are dropped. */
+int cg_autotune(cg_handle *h, uint32_t hops_per_trial);
+
+/* Groups of replicas sharing one L (one persistent launch each). */
+int cg_num_groups(const cg_handle *h);
+int cg_group_shape(const cg_handle *h, int index, int *L, int *threads,
+                   unsigned int *M, int *cluster);
 
 /* Test-only constant-acceptance mode: every label accepts iff u < A0, the
  * configuration is never changed, the counters advance.  A0 < 0 turns the

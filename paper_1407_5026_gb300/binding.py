@@ -30,7 +30,7 @@ EXPORTED = [
     "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_version",
-    "cg_refresh_tc_noalloc",
+    "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
 ]
 
 
@@ -130,6 +130,10 @@ def load(path: str | None = None):
             "cg_version": (ctypes.c_char_p, []),
             "cg_refresh_tc_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      vp, vp, vp, vp, vp]),
+            "cg_autotune": (ctypes.c_int, [vp, ctypes.c_uint32]),
+            "cg_num_groups": (ctypes.c_int, [vp]),
+            "cg_group_shape": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                              P(ctypes.c_uint), P(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -299,6 +303,22 @@ def cg_refresh_tc_noalloc(L, R, nu, occ_ptr, phi_ptr, eps_ptr, max_err_ptr=None,
         L, R, nu, ctypes.c_void_p(occ_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(eps_ptr),
         ctypes.c_void_p(max_err_ptr) if max_err_ptr else None,
         ctypes.c_void_p(stream) if stream else None))
+
+
+def cg_autotune(h, hops_per_trial=0):
+    return _check(load().cg_autotune(h, hops_per_trial))
+
+
+def cg_num_groups(h) -> int:
+    return load().cg_num_groups(h)
+
+
+def cg_group_shape(h, index):
+    L, t, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    M = ctypes.c_uint()
+    _check(load().cg_group_shape(h, index, ctypes.byref(L), ctypes.byref(t), ctypes.byref(M),
+                                 ctypes.byref(c)))
+    return {"L": L.value, "threads": t.value, "M": M.value, "cluster": c.value}
 
 
 def cg_set_toy_acceptance(h, A0):

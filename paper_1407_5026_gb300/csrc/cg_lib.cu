@@ -176,6 +176,10 @@ struct Rep {
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
     int cluster = 1;                 // CTAs per replica
+    unsigned M = 4096;               // labels per round when cg_run is given M = 0
+    bool tuned = false;
+    cudaStream_t st = nullptr;       // side stream (handles with several groups)
+    cudaEvent_t done = nullptr;      // join event on that stream
     bool tc = false;                 // refresh on the tensor cores
     unsigned char *d_img = nullptr;  // S image scratch of the tensor-core refresh
     int *d_err = nullptr;            // its error word
@@ -224,6 +228,14 @@ struct cg_handle {
     double toy_A0 = 0.0;
     cg_hop *d_log = nullptr;
     bool pending = false;
+    cudaEvent_t fork = nullptr;      // fork event for the groups' side streams
+    // captured CUDA graphs of cg_run, keyed by (n_hops, M, hops since refresh)
+    struct GraphEntry {
+        unsigned long long n_hops, hsr_before, hsr_after;
+        unsigned M;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -274,7 +286,7 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
 // a forced size is used when it fits.  0 when nothing fits.
 int choose_cluster(const cg_opts &o, const Rep &r, int optin)
 {
-    const int budget = optin - 1024;
+    const int budget = optin - 2048;     // room for the kernels' static shared memory
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
         if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
@@ -595,6 +607,21 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         if (g.tc) cudaMemsetAsync(g.d_err, 0, sizeof(int), h->st);
         h->groups.push_back(g);
     }
+    if (h->groups.size() > 1) {
+        // one stream per lattice size, forked from and joined to the handle's
+        if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+            fail(CG_ECUDA, "cudaEventCreate failed");
+            destroy_partial();
+            return nullptr;
+        }
+        for (Group &g : h->groups)
+            if (cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
+                fail(CG_ECUDA, "side stream creation failed");
+                destroy_partial();
+                return nullptr;
+            }
+    }
     h->order = order;
     h->h_reps.resize(R);
     for (int k = 0; k < R; ++k) fill_dev(h->reps[k], o.precision, h->h_reps[k], nullptr);
@@ -629,78 +656,135 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     return h.release();
 }
 
-int launch_segment(cg_handle *h, unsigned long long hops, unsigned M, unsigned long long log_off)
+// Rebuild eps of one group's replicas from scratch (binary64: the serial-order
+// kernel; binary32: the tensor-core contraction or the binary64 direct sum).
+int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
 {
-    RunArgs a{};
-    a.n_hops = hops;
-    a.M = M;
-    a.max_rounds = h->opts.max_rounds_per_hop;
-    a.log_offset = log_off;
-    a.hop_timeout_ns = 1000000ull * (h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u);
-    a.toy = h->toy;
-    a.toy_A0 = h->toy_A0;
-    for (const Group &g : h->groups) {
-        if (g.cluster > 1)
-            CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first,
-                                      g.count, g.cluster, g.threads, g.smem, a, h->st, g.L));
-        else
-            CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first,
-                                         g.count, g.threads, g.smem, a, h->st, g.L));
+    if (h->opts.precision != CG_FP32) {
+        for (int k = g.first; k < g.first + g.count; ++k) {
+            const int ri = h->order[k];
+            const Rep &r = h->reps[ri];
+            CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, r.tab->H1, r.words, CG_FP64, st));
+        }
+        return CG_OK;
+    }
+    CG_CUDA(launch_reset_refresh_err(h->d_reps, h->d_index + g.first, g.count, st));
+    if (g.tc) {
+        const uint32_t *split = h->reps[h->order[g.first]].tab->d_split;
+        for (int c0 = 0; c0 < g.count; c0 += kTcMaxReplicas) {
+            const int n = std::min(kTcMaxReplicas, g.count - c0);
+            CG_CUDA(launch_refresh_tc(h->d_reps, h->d_index + g.first + c0, n, g.L, split,
+                                      g.d_img, g.d_err, st));
+        }
+    } else {
+        for (int k = g.first; k < g.first + g.count; ++k) {
+            const int ri = h->order[k];
+            const Rep &r = h->reps[ri];
+            CG_CUDA(launch_refresh_fp64(h->d_reps + ri, r.N, r.tab->H1, r.words, st));
+        }
     }
     return CG_OK;
 }
 
 int refresh_all(cg_handle *h)
 {
-    if (h->opts.precision != CG_FP32) {
-        for (size_t k = 0; k < h->reps.size(); ++k) {
-            const Rep &r = h->reps[k];
-            CG_CUDA(launch_eps_init(h->d_reps + k, r.N, r.tab->H1, r.words, CG_FP64, h->st));
-        }
-        return CG_OK;
-    }
     for (const Group &g : h->groups) {
-        CG_CUDA(launch_reset_refresh_err(h->d_reps, h->d_index + g.first, g.count, h->st));
-        if (g.tc) {
-            const uint32_t *split = h->reps[h->order[g.first]].tab->d_split;
-            for (int c0 = 0; c0 < g.count; c0 += kTcMaxReplicas) {
-                const int n = std::min(kTcMaxReplicas, g.count - c0);
-                CG_CUDA(launch_refresh_tc(h->d_reps, h->d_index + g.first + c0, n, g.L, split,
-                                          g.d_img, g.d_err, h->st));
-            }
-        } else {
-            for (int k = g.first; k < g.first + g.count; ++k) {
-                const int ri = h->order[k];
-                const Rep &r = h->reps[ri];
-                CG_CUDA(launch_refresh_fp64(h->d_reps + ri, r.N, r.tab->H1, r.words, h->st));
-            }
-        }
+        const int rc = refresh_group(h, g, h->st);
+        if (rc) return rc;
     }
     return CG_OK;
 }
 
+int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned M,
+                 unsigned long long log_off, cudaStream_t st)
+{
+    RunArgs a{};
+    a.n_hops = hops;
+    a.M = M ? M : g.M;
+    a.max_rounds = h->opts.max_rounds_per_hop;
+    a.log_offset = log_off;
+    a.hop_timeout_ns = 1000000ull * (h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u);
+    a.toy = h->toy;
+    a.toy_A0 = h->toy_A0;
+    if (g.cluster > 1)
+        CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
+                                  g.cluster, g.threads, g.smem, a, st, g.L));
+    else
+        CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first,
+                                     g.count, g.threads, g.smem, a, st, g.L));
+    return CG_OK;
+}
+
+// Queue n_hops hops of every replica: segments that end where a binary32
+// refresh falls due; with several lattice sizes each group runs its segment
+// (and its refresh) on its own stream between a fork and a join, so the
+// groups' persistent launches overlap.
 int enqueue_run(cg_handle *h, unsigned long long n_hops, unsigned M, bool logged)
 {
     if (!h) return fail(CG_EINVAL, "null handle");
-    if (M < 1 || M > (1u << 24)) return fail(CG_EINVAL, "M must be in [1, 2^24]");
+    if (M > (1u << 24)) return fail(CG_EINVAL, "M must be in [1, 2^24] (0: per-group M)");
     if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
     const bool refresh = h->opts.precision == CG_FP32 && h->opts.refresh_every > 0;
+    const bool forked = h->groups.size() > 1;
     unsigned long long done = 0;
     while (done < n_hops) {
         unsigned long long seg = n_hops - done;
         if (refresh) seg = std::min(seg, h->opts.refresh_every - h->hops_since_refresh);
-        int rc = launch_segment(h, seg, M, logged ? done : 0);
-        if (rc) return rc;
-        done += seg;
-        if (refresh) {
-            h->hops_since_refresh += seg;
-            if (h->hops_since_refresh == h->opts.refresh_every) {
-                rc = refresh_all(h);
-                if (rc) return rc;
-                h->hops_since_refresh = 0;
+        const bool refresh_now = refresh && h->hops_since_refresh + seg == h->opts.refresh_every;
+        if (forked) CG_CUDA(cudaEventRecord(h->fork, h->st));
+        for (const Group &g : h->groups) {
+            cudaStream_t st = forked ? g.st : h->st;
+            if (forked) CG_CUDA(cudaStreamWaitEvent(st, h->fork, 0));
+            int rc = launch_group(h, g, seg, M, logged ? done : 0, st);
+            if (!rc && refresh_now) rc = refresh_group(h, g, st);
+            if (rc) return rc;
+            if (forked) {
+                CG_CUDA(cudaEventRecord(g.done, st));
+                CG_CUDA(cudaStreamWaitEvent(h->st, g.done, 0));
             }
         }
+        done += seg;
+        if (refresh) h->hops_since_refresh = refresh_now ? 0 : h->hops_since_refresh + seg;
     }
+    h->pending = true;
+    return CG_OK;
+}
+
+// cg_run through a CUDA graph: the launches of one (n_hops, M, refresh phase)
+// are captured once and replayed.
+int enqueue_run_graph(cg_handle *h, unsigned long long n_hops, unsigned M)
+{
+    if (M > (1u << 24)) return fail(CG_EINVAL, "M must be in [1, 2^24] (0: per-group M)");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    for (const auto &e : h->graphs)
+        if (e.n_hops == n_hops && e.M == M && e.hsr_before == h->hops_since_refresh) {
+            CG_CUDA(cudaGraphLaunch(e.exec, h->st));
+            h->hops_since_refresh = e.hsr_after;
+            h->pending = true;
+            return CG_OK;
+        }
+    cg_handle::GraphEntry e{};
+    e.n_hops = n_hops;
+    e.M = M;
+    e.hsr_before = h->hops_since_refresh;
+    CG_CUDA(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+    int rc = enqueue_run(h, n_hops, M, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->st, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        h->hops_since_refresh = e.hsr_before;
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(CG_ECUDA, std::string("cudaStreamEndCapture: ") +
+                                                     cudaGetErrorString(ce));
+    e.hsr_after = h->hops_since_refresh;
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess)
+        return fail(CG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    h->graphs.push_back(e);
+    CG_CUDA(cudaGraphLaunch(e.exec, h->st));
     h->pending = true;
     return CG_OK;
 }
@@ -784,6 +868,12 @@ void cg_destroy(cg_handle *h)
     if (h->st) cudaStreamSynchronize(h->st);
     for (void *p : h->allocs) cudaFree(p);
     if (h->d_log) cudaFree(h->d_log);
+    for (auto &e : h->graphs) cudaGraphExecDestroy(e.exec);
+    for (Group &g : h->groups) {
+        if (g.st) cudaStreamDestroy(g.st);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
 }
@@ -798,7 +888,8 @@ int cg_num_sites(const cg_handle *h, int replica)
 
 int cg_run_async(cg_handle *h, uint64_t n_hops, uint32_t M)
 {
-    return enqueue_run(h, n_hops, M, false);
+    if (!h) return fail(CG_EINVAL, "null handle");
+    return h->opts.use_graph ? enqueue_run_graph(h, n_hops, M) : enqueue_run(h, n_hops, M, false);
 }
 
 int cg_sync(cg_handle *h)
@@ -809,7 +900,7 @@ int cg_sync(cg_handle *h)
 
 int cg_run(cg_handle *h, uint64_t n_hops, uint32_t M)
 {
-    int rc = enqueue_run(h, n_hops, M, false);
+    int rc = cg_run_async(h, n_hops, M);
     if (rc) return rc;
     return finish_run(h);
 }
@@ -917,6 +1008,184 @@ int cg_refresh(cg_handle *h)
     int rc = refresh_all(h);
     if (rc) return rc;
     CG_CUDA(cudaStreamSynchronize(h->st));
+    return CG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: per lattice-size group, time the persistent launch for each CTA
+// size and M on a copy of the state, keep the fastest.  Results are cached in
+// the JSON file named by $CG_TUNE_CACHE (flat map key -> {"threads", "M"}).
+// ---------------------------------------------------------------------------
+
+static std::string tune_key(const cg_handle *h, const Group &g)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, h->device);
+    const Rep &r = h->reps[h->order[g.first]];
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|L=%d|prec=%s|cluster=%d|rmax=%d|T=%.6g|R=%d", prop.name,
+                  g.L, h->opts.precision == CG_FP64 ? "fp64" : "fp32", g.cluster, r.d.r_max,
+                  r.d.T, g.count);
+    return std::string(buf);
+}
+
+static bool tune_cache_lookup(const std::string &text, const std::string &key, int *threads,
+                              unsigned *M)
+{
+    const std::string pat = "\"" + key + "\": {\"threads\": ";
+    const size_t p = text.find(pat);
+    if (p == std::string::npos) return false;
+    int t = 0;
+    unsigned m = 0;
+    if (std::sscanf(text.c_str() + p + pat.size(), "%d, \"M\": %u", &t, &m) != 2) return false;
+    *threads = t;
+    *M = m;
+    return true;
+}
+
+int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (hops_per_trial == 0) hops_per_trial = 256;
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    const char *path = std::getenv("CG_TUNE_CACHE");
+    std::string cache;
+    if (path) {
+        if (FILE *f = std::fopen(path, "r")) {
+            char buf[4096];
+            size_t n;
+            while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) cache.append(buf, n);
+            std::fclose(f);
+        }
+    }
+    const int rb = h->opts.precision == CG_FP64 ? 8 : 4;
+    std::vector<std::pair<std::string, std::pair<int, unsigned>>> found;
+    cudaEvent_t e0, e1;
+    CG_CUDA(cudaEventCreate(&e0));
+    CG_CUDA(cudaEventCreate(&e1));
+    int rc = CG_OK;
+    for (Group &g : h->groups) {
+        const std::string key = tune_key(h, g);
+        int ct = 0;
+        unsigned cM = 0;
+        if (tune_cache_lookup(cache, key, &ct, &cM)) {
+            g.threads = ct;
+            g.M = cM;
+            g.tuned = true;
+            continue;
+        }
+        // snapshot of the group's state (eps, bitmask, counters per replica)
+        const Rep &r0 = h->reps[h->order[g.first]];
+        const size_t per = (size_t)r0.N * rb + (size_t)r0.words * 4 + sizeof(DevCounters);
+        char *snap = nullptr;
+        if (cudaMalloc((void **)&snap, per * g.count) != cudaSuccess) {
+            rc = fail(CG_ENOMEM, "autotune snapshot allocation failed");
+            break;
+        }
+        auto copy_group = [&](bool save) -> cudaError_t {
+            for (int k = 0; k < g.count; ++k) {
+                const Rep &r = h->reps[h->order[g.first + k]];
+                char *s = snap + per * k;
+                const size_t be = (size_t)r.N * rb, bo = (size_t)r.words * 4;
+                cudaError_t e;
+                if ((e = cudaMemcpyAsync(save ? s : r.d_eps, save ? r.d_eps : s, be,
+                                         cudaMemcpyDeviceToDevice, h->st)))
+                    return e;
+                if ((e = cudaMemcpyAsync(save ? s + be : (void *)r.d_occ,
+                                         save ? (void *)r.d_occ : s + be, bo,
+                                         cudaMemcpyDeviceToDevice, h->st)))
+                    return e;
+                if ((e = cudaMemcpyAsync(save ? s + be + bo : (void *)r.d_ctr,
+                                         save ? (void *)r.d_ctr : s + be + bo,
+                                         sizeof(DevCounters), cudaMemcpyDeviceToDevice, h->st)))
+                    return e;
+            }
+            return cudaStreamSynchronize(h->st);
+        };
+        cudaError_t ce = copy_group(true);
+        double best = -1.0;
+        int best_t = g.threads;
+        unsigned best_M = g.M;
+        const int shapes[3] = {256, 512, 1024};
+        const unsigned Ms[3] = {1024, 4096, 16384};
+        for (int ti = 0; ti < 3 && ce == cudaSuccess; ++ti) {
+            const int t = shapes[ti];
+            if (t < g.L || (g.cluster > 1 && t < 512)) continue;
+            for (int mi = 0; mi < 3 && ce == cudaSuccess; ++mi) {
+                Group trial = g;
+                trial.threads = t;
+                cudaEventRecord(e0, h->st);
+                int lrc = launch_group(h, trial, hops_per_trial, Ms[mi], 0, h->st);
+                cudaEventRecord(e1, h->st);
+                ce = cudaStreamSynchronize(h->st);
+                if (lrc || ce != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                DevCounters c;
+                cudaMemcpy(&c, r0.d_ctr, sizeof(c), cudaMemcpyDeviceToHost);
+                const double rate = c.status == CG_OK && ms > 0.f
+                                        ? (double)g.count * hops_per_trial / (ms * 1e-3)
+                                        : 0.0;
+                if (rate > best) {
+                    best = rate;
+                    best_t = t;
+                    best_M = Ms[mi];
+                }
+                ce = copy_group(false);   // restore: tuning leaves the chains untouched
+            }
+        }
+        cudaFree(snap);
+        if (ce != cudaSuccess) {
+            rc = fail(CG_ECUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+            break;
+        }
+        g.threads = best_t;
+        g.M = best_M;
+        g.tuned = true;
+        found.push_back({key, {best_t, best_M}});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (auto &e : h->graphs) cudaGraphExecDestroy(e.exec);   // shapes changed
+    h->graphs.clear();
+    if (rc == CG_OK && path && !found.empty()) {
+        // rewrite the cache with the old entries plus the new ones
+        std::string body;
+        size_t p = cache.find('{');
+        size_t q = cache.rfind('}');
+        if (p != std::string::npos && q != std::string::npos && q > p) {
+            body = cache.substr(p + 1, q - p - 1);
+            while (!body.empty() && (body.back() == '\n' || body.back() == ' ')) body.pop_back();
+        }
+        if (FILE *f = std::fopen(path, "w")) {
+            std::fprintf(f, "{");
+            bool first = body.find('"') == std::string::npos;
+            if (!first) std::fprintf(f, "%s", body.c_str());
+            for (auto &e : found) {
+                std::fprintf(f, "%s\n  \"%s\": {\"threads\": %d, \"M\": %u}", first ? "" : ",",
+                             e.first.c_str(), e.second.first, e.second.second);
+                first = false;
+            }
+            std::fprintf(f, "\n}\n");
+            std::fclose(f);
+        }
+    }
+    return rc;
+}
+
+int cg_num_groups(const cg_handle *h) { return h ? (int)h->groups.size() : 0; }
+
+int cg_group_shape(const cg_handle *h, int index, int *L, int *threads, unsigned *M,
+                   int *cluster)
+{
+    if (!h || index < 0 || index >= (int)h->groups.size())
+        return fail(CG_EINVAL, "group index out of range");
+    const Group &g = h->groups[index];
+    if (L) *L = g.L;
+    if (threads) *threads = g.threads;
+    if (M) *M = g.M;
+    if (cluster) *cluster = g.cluster;
     return CG_OK;
 }
 

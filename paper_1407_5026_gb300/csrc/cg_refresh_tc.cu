@@ -407,11 +407,13 @@ int refresh_tc_smem_bytes(int R_pad, int H1)
 }
 
 // K split of the contraction: the largest divisor of the K-block count that is
-// at most 8 (partial sums over at most an eighth of the lattice).
+// at most max(8, K-blocks / 32), so each CTA's FP32 partial sum covers at most
+// an eighth of the lattice and at most 32 K-blocks (2048 sites) on large ones.
 int refresh_tc_ksplit(int L)
 {
     const int kblocks = L * L / 64;
-    for (int k = 8; k > 1; --k)
+    const int cap = kblocks / 32 > 8 ? kblocks / 32 : 8;
+    for (int k = cap; k > 1; --k)
         if (kblocks % k == 0) return k;
     return 1;
 }
