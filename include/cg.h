@@ -120,6 +120,14 @@ typedef struct {
     uint64_t cycles_update;   /* SM clock cycles spent in the eps update       */
 } cg_obs;
 
+/* One point of the log-spaced trace (cg_set_trace). */
+typedef struct {
+    uint64_t attempts;   /* serial-equivalent attempts when recorded (time = attempts/Gamma) */
+    uint64_t hops;
+    int64_t P;           /* dipole moment (unwrapped)                                      */
+    double energy;
+} cg_trace_point;
+
 /* One executed hop (diagnostics; see cg_run_logged). */
 typedef struct {
     uint32_t i, j;       /* origin, destination                        */
@@ -252,6 +260,20 @@ int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int *occ,
  *   kind 2: shared-memory read-modify-write bandwidth of 64-bit words, bytes/s
  * summed over all SMs; result written to *result. */
 int cg_microbench(int kind, int device, double *result);
+
+/* Log-spaced trace of the dipole moment P and the energy, from which the
+ * conductivity sigma(t) = (1 / N E) dP/dt of Eq. 3 is estimated (P(t) and
+ * its relaxation are the paper's Fig. 3 observables).  After this call every
+ * replica records a point at the first executed hop whose time reaches
+ * t_k = first_time * 10^(k / points_per_decade) (time in units of tau_0,
+ * t = attempts / Gamma), up to `capacity` points; the first point is the
+ * state at the call.  Allocates per-replica device buffers (cudaMalloc, also
+ * for workspace handles); a later call restarts the trace. */
+int cg_set_trace(cg_handle *h, double first_time, double points_per_decade, int capacity);
+
+/* Copy up to `cap` recorded points of one replica into out_host; returns
+ * the number of points copied (>= 0) or a negative CG_E* code. */
+int cg_read_trace(cg_handle *h, int replica, cg_trace_point *out_host, int cap);
 
 /* Launch-shape autotuner.  The parallel-rejection section recommends M near
  * 1/A but larger than the number of concurrent threads; the best M and CTA

@@ -31,6 +31,7 @@ EXPORTED = [
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_version",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
+    "cg_set_trace", "cg_read_trace",
 ]
 
 
@@ -87,6 +88,14 @@ class cg_hop(ctypes.Structure):
 HOP_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("q", "<u4"), ("p", "<u4"),
                       ("round", "<u8"), ("dx", "<i4"), ("dy", "<i4"), ("dE", "<f8")])
 
+
+class cg_trace_point(ctypes.Structure):
+    _fields_ = [("attempts", ctypes.c_uint64), ("hops", ctypes.c_uint64),
+                ("P", ctypes.c_int64), ("energy", ctypes.c_double)]
+
+
+TRACE_DTYPE = np.dtype([("attempts", "<u8"), ("hops", "<u8"), ("P", "<i8"), ("energy", "<f8")])
+
 _lib = None
 _lock = threading.Lock()
 
@@ -131,6 +140,8 @@ def load(path: str | None = None):
             "cg_refresh_tc_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      vp, vp, vp, vp, vp]),
             "cg_autotune": (ctypes.c_int, [vp, ctypes.c_uint32]),
+            "cg_set_trace": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+            "cg_read_trace": (ctypes.c_int, [vp, ctypes.c_int, P(cg_trace_point), ctypes.c_int]),
             "cg_num_groups": (ctypes.c_int, [vp]),
             "cg_group_shape": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
                                               P(ctypes.c_uint), P(ctypes.c_int)]),
@@ -303,6 +314,29 @@ def cg_refresh_tc_noalloc(L, R, nu, occ_ptr, phi_ptr, eps_ptr, max_err_ptr=None,
         L, R, nu, ctypes.c_void_p(occ_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(eps_ptr),
         ctypes.c_void_p(max_err_ptr) if max_err_ptr else None,
         ctypes.c_void_p(stream) if stream else None))
+
+
+def cg_set_trace(h, first_time, points_per_decade=8.0, capacity=256):
+    return _check(load().cg_set_trace(h, first_time, points_per_decade, capacity))
+
+
+def cg_read_trace(h, replica=0, capacity=256):
+    out = np.zeros(capacity, TRACE_DTYPE)
+    n = load().cg_read_trace(h, replica, out.ctypes.data_as(ctypes.POINTER(cg_trace_point)),
+                             capacity)
+    _check(n if n < 0 else CG_OK)
+    return out[:n]
+
+
+def sigma_windows(trace, N, E, Gamma):
+    """Conductivity of Eq. 3, sigma = (1 / N E) dP/dt, over the windows between
+    consecutive trace points (t = attempts / Gamma); returns (t_mid, sigma)."""
+    t = trace["attempts"].astype(np.float64) / Gamma
+    P = trace["P"].astype(np.float64)
+    dt = np.diff(t)
+    keep = dt > 0
+    t_mid = 0.5 * (t[1:] + t[:-1])[keep]
+    return t_mid, (np.diff(P)[keep] / dt[keep]) / (N * E)
 
 
 def cg_autotune(h, hops_per_trial=0):

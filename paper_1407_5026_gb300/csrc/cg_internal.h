@@ -26,7 +26,10 @@ struct alignas(16) DevCounters {
     unsigned long long max_err_bits;   // max |eps - eps_ref| of the last refresh (binary64 bits)
     int status;                        // CG_OK, CG_ESTUCK or CG_ETIMEOUT
     float m_ema;                       // running mean of attempts per hop (chunk sizing)
-    int pad_[2];
+    int trace_count;                   // points recorded
+    int trace_cap;                     // trace capacity (0: no trace)
+    double trace_next;                 // attempt count of the next trace point
+    double trace_ratio;                // ratio between consecutive trace points
 };
 
 // Guide table of the tower: bucket b = x1 >> (32 - kGuideBits) holds the
@@ -60,7 +63,26 @@ struct alignas(16) DevReplica {
     const double *phi;        // N site energies
     DevCounters *ctr;
     cg_hop *log;              // NULL, or n_hops entries for this replica
+    cg_trace_point *trace;    // NULL, or ctr->trace_cap points
 };
+
+// Thread 0 at commit: record trace points whose attempt threshold the
+// replica's attempt count has reached (several if one hop spans them).
+__device__ __forceinline__ void trace_hop(const DevReplica &Rg, unsigned long long attempts,
+                                          unsigned long long hops, long long P, double energy)
+{
+    DevCounters *c = Rg.ctr;
+    if (!Rg.trace || c->trace_count >= c->trace_cap || (double)attempts < c->trace_next) return;
+    cg_trace_point pt;
+    pt.attempts = attempts;
+    pt.hops = hops;
+    pt.P = P;
+    pt.energy = energy;
+    Rg.trace[c->trace_count++] = pt;
+    double next = c->trace_next;
+    while (next <= (double)attempts) next = next * c->trace_ratio > next + 1.0 ? next * c->trace_ratio : next + 1.0;
+    c->trace_next = next;
+}
 
 struct RunArgs {
     unsigned long long n_hops;     // hops every replica executes in this launch

@@ -229,6 +229,8 @@ struct cg_handle {
     cg_hop *d_log = nullptr;
     bool pending = false;
     cudaEvent_t fork = nullptr;      // fork event for the groups' side streams
+    cg_trace_point *d_trace = nullptr;
+    int trace_cap = 0;
     // captured CUDA graphs of cg_run, keyed by (n_hops, M, hops since refresh)
     struct GraphEntry {
         unsigned long long n_hops, hsr_before, hsr_after;
@@ -868,6 +870,7 @@ void cg_destroy(cg_handle *h)
     if (h->st) cudaStreamSynchronize(h->st);
     for (void *p : h->allocs) cudaFree(p);
     if (h->d_log) cudaFree(h->d_log);
+    if (h->d_trace) cudaFree(h->d_trace);
     for (auto &e : h->graphs) cudaGraphExecDestroy(e.exec);
     for (Group &g : h->groups) {
         if (g.st) cudaStreamDestroy(g.st);
@@ -1172,6 +1175,60 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
         }
     }
     return rc;
+}
+
+int cg_set_trace(cg_handle *h, double first_time, double points_per_decade, int capacity)
+{
+    if (!h) return fail(CG_EINVAL, "null handle");
+    if (!(first_time > 0.0) || !(points_per_decade > 0.0) || capacity < 1)
+        return fail(CG_EINVAL, "need first_time > 0, points_per_decade > 0, capacity >= 1");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    const size_t R = h->reps.size();
+    if (h->d_trace) {
+        cudaFree(h->d_trace);
+        h->d_trace = nullptr;
+    }
+    CG_CUDA(cudaMalloc((void **)&h->d_trace, sizeof(cg_trace_point) * R * (size_t)capacity));
+    const double ratio = std::pow(10.0, 1.0 / points_per_decade);
+    for (size_t k = 0; k < R; ++k) {
+        const Rep &r = h->reps[k];
+        DevCounters c;
+        CG_CUDA(cudaMemcpy(&c, r.d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+        // the first point is the present state; later points at first_time * ratio^n
+        cg_trace_point p0{c.attempts, c.hops, c.P, c.energy};
+        CG_CUDA(cudaMemcpy(h->d_trace + k * capacity, &p0, sizeof(p0), cudaMemcpyHostToDevice));
+        const double Gamma = (double)r.N * r.tab->Z;
+        c.trace_count = 1;
+        c.trace_cap = capacity;
+        c.trace_ratio = ratio;
+        c.trace_next = std::max((double)c.attempts + 1.0, first_time * Gamma);
+        CG_CUDA(cudaMemcpy(r.d_ctr, &c, sizeof(c), cudaMemcpyHostToDevice));
+        h->h_reps[k].trace = h->d_trace + k * capacity;
+    }
+    CG_CUDA(cudaMemcpy(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
+                       cudaMemcpyHostToDevice));
+    for (auto &e : h->graphs) cudaGraphExecDestroy(e.exec);   // descriptors changed
+    h->graphs.clear();
+    h->trace_cap = capacity;
+    return CG_OK;
+}
+
+int cg_read_trace(cg_handle *h, int replica, cg_trace_point *out_host, int cap)
+{
+    int rc = replica_index_ok(h, replica);
+    if (rc) return rc;
+    if (!out_host || cap < 0) return fail(CG_EINVAL, "bad output buffer");
+    if (!h->d_trace) return 0;
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    DevCounters c;
+    CG_CUDA(cudaMemcpy(&c, h->reps[replica].d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    const int n = std::min(cap, c.trace_count);
+    if (n > 0)
+        CG_CUDA(cudaMemcpy(out_host, h->d_trace + (size_t)replica * h->trace_cap,
+                           sizeof(cg_trace_point) * n, cudaMemcpyDeviceToHost));
+    return n;
 }
 
 int cg_num_groups(const cg_handle *h) { return h ? (int)h->groups.size() : 0; }

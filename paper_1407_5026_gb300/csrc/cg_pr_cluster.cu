@@ -272,6 +272,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 s_c.P += cdx;
                 s_c.energy = d_add(s_c.energy, win.dE);
             }
+            if (rank == 0) trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
             if (rank == 0 && Rg.log) {

@@ -227,6 +227,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 s_c.P += cdx;
                 s_c.energy = d_add(s_c.energy, c.dE);
             }
+            trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
             if (Rg.log) {
