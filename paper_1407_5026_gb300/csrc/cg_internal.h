@@ -89,6 +89,7 @@ struct RunArgs {
     unsigned long long max_rounds; // rounds per hop before CG_ESTUCK
     unsigned long long log_offset; // index of this launch's first hop in each log
     unsigned long long hop_timeout_ns; // wall-clock limit of one hop
+    unsigned long long hop_timeout_cyc; // the same in SM cycles at the peak clock
     unsigned int M;                // labels per round
     int toy;                       // constant-acceptance test mode
     double toy_A0;
@@ -97,7 +98,7 @@ struct RunArgs {
 // Shared-memory carve-up of the persistent kernel (bytes, 16-aligned).
 struct SmemLayout {
     int off_eps, off_tinv, off_occ, off_guide, off_thr, off_disp;
-    int off_vr64, off_edx64, off_vr32, off_edx32, total;
+    int off_vr64, off_edx64, off_cv32, total;
 };
 
 __host__ __device__ inline int cg_align16(int x) { return (x + 15) & ~15; }
@@ -115,8 +116,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int H1, int V, int word
     s.off_disp = o;  o = cg_align16(o + V * 4);
     s.off_vr64 = o;  o = cg_align16(o + V * 8);
     s.off_edx64 = o; o = cg_align16(o + V * 8);
-    s.off_vr32 = o;  o = cg_align16(o + V * 4);
-    s.off_edx32 = o; o = cg_align16(o + V * 4);
+    s.off_cv32 = o;  o = cg_align16(o + V * 4);
     s.total = o;
     return s;
 }

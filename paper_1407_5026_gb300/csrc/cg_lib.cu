@@ -207,6 +207,7 @@ size_t tc_img_bytes(int L, int count)
 struct cg_handle {
     cg_opts opts{};
     int device = 0;
+    int clock_khz = 2000000;       // peak SM clock (per-hop limit in cycles)
     cudaStream_t st = nullptr;
     bool own_stream = false;
     std::vector<Rep> reps;
@@ -510,6 +511,11 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         fail(CG_ECUDA, "cudaSetDevice failed");
         return nullptr;
     }
+    {
+        int khz = 0;
+        if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, o.device) == cudaSuccess && khz > 0)
+            h->clock_khz = khz;
+    }
     if (ws) {
         if (((uintptr_t)ws & 255) != 0) { fail(CG_EINVAL, "workspace must be 256-byte aligned"); return nullptr; }
         h->ws_mode = true;
@@ -706,6 +712,10 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.max_rounds = h->opts.max_rounds_per_hop;
     a.log_offset = log_off;
     a.hop_timeout_ns = 1000000ull * (h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u);
+    // the same limit in SM cycles at the peak clock (a lower clock only makes
+    // the limit longer in seconds)
+    a.hop_timeout_cyc = (unsigned long long)(h->opts.hop_timeout_ms ? h->opts.hop_timeout_ms : 10000u) *
+                        (unsigned long long)h->clock_khz;
     a.toy = h->toy;
     a.toy_A0 = h->toy_A0;
     if (g.cluster > 1)

@@ -85,8 +85,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     S.disp = reinterpret_cast<int *>(smem + lay.off_disp);
     S.vr64 = reinterpret_cast<double *>(smem + lay.off_vr64);
     S.edx64 = reinterpret_cast<double *>(smem + lay.off_edx64);
-    S.vr32 = reinterpret_cast<float *>(smem + lay.off_vr32);
-    S.edx32 = reinterpret_cast<float *>(smem + lay.off_edx32);
+    S.cv32 = reinterpret_cast<float *>(smem + lay.off_cv32);
     Real *eps = reinterpret_cast<Real *>(S.eps);
     const Real *tinv = reinterpret_cast<const Real *>(S.tinv);
 
@@ -108,8 +107,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
             S.disp[l] = dxy;
             S.vr64[l] = Rg.tinvd[l];
             S.edx64[l] = d_mul(E, (double)dx);
-            S.vr32[l] = (float)Rg.tinvd[l];
-            S.edx32[l] = (float)E * (float)dx;
+            S.cv32[l] = (float)d_add(Rg.tinvd[l], S.edx64[l]);   // one rounding to binary32
         }
     }
     DevCounters *cnt = Rg.ctr;

@@ -57,8 +57,8 @@ struct Shared {
     unsigned short *guide;
     unsigned *thr;
     int *disp;
-    double *vr64, *edx64;
-    float *vr32, *edx32;
+    double *vr64, *edx64;     // 1/r_v and E dx_v (binary64)
+    float *cv32;              // 1/r_v + E dx_v rounded once to binary32
 };
 
 struct Prop {
@@ -81,13 +81,11 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     uint32_t x[4];
     philox_finish(k, P, key0, key1, x);
     p.x2 = x[2];
-    p.i = __umulhi(x[0], N);
-    p.theta = false;
-    p.j = 0;
-    p.v = 0;
-    p.dxy = 0;
-    const uint32_t x1 = x[1];
-    if (!valid || x1 > thr_last) return p;       // beyond M, or a null proposal
+    p.i = kPow2 ? (x[0] >> (32 - 2 * log2L)) : __umulhi(x[0], N);   // floor(x0 N / 2^32)
+    // a label beyond M or a null proposal (x1 above the last threshold) is
+    // evaluated on a clamped x1 without a branch and can never pass theta
+    const uint32_t x1 = min(x[1], thr_last);
+    const bool live = valid && x[1] <= thr_last;
     const unsigned g = S.guide[x1 >> (32 - kGuideBits)];
     int v = (int)(g & 0x7fffu);
     if (g & 0x8000u)
@@ -111,7 +109,7 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     p.v = v;
     p.dxy = dxy;
     const unsigned wi = S.occ[p.i >> 5], wj = S.occ[p.j >> 5];
-    p.theta = ((wi >> (p.i & 31)) & 1u) && !((wj >> (p.j & 31)) & 1u);
+    p.theta = live && ((wi >> (p.i & 31)) & 1u) && !((wj >> (p.j & 31)) & 1u);
     return p;
 }
 
@@ -153,7 +151,7 @@ __device__ __forceinline__ bool accept_vals<float>(float ei, float ej, const Sha
                                                    const Prop &p, double T, float invTf,
                                                    double &dE_out)
 {
-    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn(ej, ei), S.vr32[p.v]), S.edx32[p.v]);
+    const float dEf = __fsub_rn(__fsub_rn(ej, ei), S.cv32[p.v]);
     if (fabsf(dEf) < 1e-5f) {
         // near tie: decide in binary64 from the widened energies
         double d = d_sub((double)ej, (double)ei);
@@ -166,8 +164,34 @@ __device__ __forceinline__ bool accept_vals<float>(float ei, float ej, const Sha
     }
     dE_out = 0.0;   // widened for the executed hop only
     if (dEf <= 0.0f) return true;
-    const float u = ((float)(p.x2 >> 9) + 0.5f) * 0x1p-23f;
-    return u < __expf(-dEf * invTf);
+    // u = (m + 1/2) 2^-23 with m = x2 >> 9 (exact in binary32); u < e^(-dH/T)
+    // tested as m < e 2^23 - 1/2
+    return (float)(p.x2 >> 9) < __fmaf_rn(__expf(-dEf * invTf), 0x1p23f, -0.5f);
+}
+
+// Step 2 for the two labels of a thread in the binary32 form, without a
+// branch per label: the energies are read for every label (its sites are
+// valid even when theta fails) and theta masks the result, so the two
+// dependency chains interleave.  Near ties (|dH| < 1e-5) are re-decided in
+// binary64 by accept_vals<float>.
+__device__ __forceinline__ void accept2_f32(const Shared &S, const Prop &p0, const Prop &p1,
+                                            double T, float invTf, bool &acc0, bool &acc1,
+                                            double &dE0, double &dE1)
+{
+    const float *eps = reinterpret_cast<const float *>(S.eps);
+    const float d0 = __fsub_rn(__fsub_rn(eps[p0.j], eps[p0.i]), S.cv32[p0.v]);
+    const float d1 = __fsub_rn(__fsub_rn(eps[p1.j], eps[p1.i]), S.cv32[p1.v]);
+    const float t0 = __fmaf_rn(__expf(-d0 * invTf), 0x1p23f, -0.5f);
+    const float t1 = __fmaf_rn(__expf(-d1 * invTf), 0x1p23f, -0.5f);
+    acc0 = p0.theta && (d0 <= 0.0f || (float)(p0.x2 >> 9) < t0);
+    acc1 = p1.theta && (d1 <= 0.0f || (float)(p1.x2 >> 9) < t1);
+    dE0 = 0.0;
+    dE1 = 0.0;
+    const bool tie0 = p0.theta && fabsf(d0) < 1e-5f, tie1 = p1.theta && fabsf(d1) < 1e-5f;
+    if (tie0 || tie1) {
+        if (tie0) acc0 = accept_vals<float>(eps[p0.i], eps[p0.j], S, p0, T, invTf, dE0);
+        if (tie1) acc1 = accept_vals<float>(eps[p1.i], eps[p1.j], S, p1, T, invTf, dE1);
+    }
 }
 
 template <typename Real>
@@ -185,8 +209,7 @@ __device__ __forceinline__ double hop_dE_vals(Real ei, Real ej, const Shared &S,
                                               double dE)
 {
     if (sizeof(Real) == 8 || dE != 0.0) return dE;
-    const float dEf = __fsub_rn(__fsub_rn(__fsub_rn((float)ej, (float)ei), S.vr32[p.v]),
-                                S.edx32[p.v]);
+    const float dEf = __fsub_rn(__fsub_rn((float)ej, (float)ei), S.cv32[p.v]);
     return (double)dEf;
 }
 

@@ -23,7 +23,10 @@
 //   [64, 2 * blockDim]); it changes which labels are evaluated, never the hop.
 //   Commit (step 3a/3c): flip n_i, n_j, P += dx, attempts += (p-1)M + q.
 //   Update (step 3b): eps_l += 1/r_lj - 1/r_li for every l, with the table
-//   holding 0 at the origin so l = i and l = j need no special case.
+//   holding 0 at the origin so l = i and l = j need no special case.  A
+//   thread takes the four sites (x, y), (x + L/2, y), (x, y + L/2),
+//   (x + L/2, y + L/2): on an even ring fold(d + L/2) = L/2 - fold(d), so one
+//   folded offset per axis serves all four.
 //
 // Binary64 form: every operation that feeds the chain is a round-to-nearest
 // intrinsic in the serial chain's order, so the trajectory is bit-identical
@@ -46,7 +49,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     __shared__ Cand s_cand[32];
     // counters only thread 0 advances (registers stay free for the labels)
     __shared__ struct {
-        unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd, wall0;
+        unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd;
         long long P, t0;
         double energy;
         float m_ema;
@@ -70,8 +73,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     S.disp = reinterpret_cast<int *>(smem + lay.off_disp);
     S.vr64 = reinterpret_cast<double *>(smem + lay.off_vr64);
     S.edx64 = reinterpret_cast<double *>(smem + lay.off_edx64);
-    S.vr32 = reinterpret_cast<float *>(smem + lay.off_vr32);
-    S.edx32 = reinterpret_cast<float *>(smem + lay.off_edx32);
+    S.cv32 = reinterpret_cast<float *>(smem + lay.off_cv32);
     Real *eps = reinterpret_cast<Real *>(S.eps);
     const Real *tinv = reinterpret_cast<const Real *>(S.tinv);
 
@@ -93,11 +95,12 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             S.disp[l] = dxy;
             S.vr64[l] = Rg.tinvd[l];
             S.edx64[l] = d_mul(E, (double)dx);          // E * dx, as in the serial chain
-            S.vr32[l] = (float)Rg.tinvd[l];
-            S.edx32[l] = (float)E * (float)dx;
+            S.cv32[l] = (float)d_add(Rg.tinvd[l], S.edx64[l]);   // one rounding to binary32
         }
     }
     DevCounters *cnt = Rg.ctr;
+    cg_hop *const hop_log = Rg.log;
+    const bool tracing = Rg.trace != nullptr;
     unsigned long long rounds = cnt->rounds;
     if (tid == 0) {
         s_c.hops = cnt->hops;
@@ -114,17 +117,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 
     const unsigned M = a.M;
     const unsigned thr_last = S.thr[V - 1];
-    // update mapping: thread -> fixed column ux, rows uy0, uy0 + rows_per_pass, ...
-    const int rows_per_pass = kThreads / L;
-    const int active = rows_per_pass * L;
-    const int ux = tid % L, uy0 = tid / L;
     const int log2L = __ffs(L) - 1;      // used when L is a power of two
+    // update mapping: thread -> base column bx < L/2, base rows by0, by0 + rpp, ...
+    const int Lh = L >> 1;
+    const int rpp = kThreads / Lh;
+    const int active = rpp * Lh;
+    const int bx = tid % Lh, by0 = tid / Lh;
 
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
-        if (tid == 0) {
-            s_c.t0 = clock64();
-            s_c.wall0 = globaltimer_ns();
-        }
+        if (tid == 0) s_c.t0 = clock64();
         // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
         // worth b ~ 64 labels (uniform: m_ema is identical in every thread)
         unsigned C = 64;
@@ -154,6 +155,8 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                     const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
                     acc0 = mine && k0 < M && u0 < a.toy_A0;
                     acc1 = mine && k1 < M && u1 < a.toy_A0;
+                } else if (sizeof(Real) == 4) {
+                    accept2_f32(S, p0, p1, T, invTf, acc0, acc1, dE0, dE1);
                 } else {
                     if (p0.theta) acc0 = accept<Real>(S, p0, T, invTf, dE0);
                     if (p1.theta) acc1 = accept<Real>(S, p1, T, invTf, dE1);
@@ -197,10 +200,11 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             if (!found) {
                 if (tid == 0) s_c.attempts += M;
                 rounds += 1;
-                // bounded hop: thread 0 reads the wall clock, the block-wide OR
-                // makes the decision uniform
+                // bounded hop: thread 0 reads its SM's cycle counter (the limit
+                // is in cycles at the peak clock), the block-wide OR makes the
+                // decision uniform
                 const int late = __syncthreads_or(
-                    tid == 0 && (globaltimer_ns() - s_c.wall0) > a.hop_timeout_ns);
+                    tid == 0 && (unsigned long long)(clock64() - s_c.t0) > a.hop_timeout_cyc);
                 if (late) {
                     status = CG_ETIMEOUT;
                     break;
@@ -227,15 +231,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 s_c.P += cdx;
                 s_c.energy = d_add(s_c.energy, c.dE);
             }
-            trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
+            if (tracing) trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
-            if (Rg.log) {
+            if (hop_log) {
                 cg_hop e;
                 e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
                 e.dx = a.toy ? 0 : cdx; e.dy = a.toy ? 0 : cdy;
                 e.dE = a.toy ? 0.0 : c.dE;
-                Rg.log[a.log_offset + h] = e;
+                hop_log[a.log_offset + h] = e;
             }
             if (!a.toy) {
                 S.occ[ci >> 5] &= ~(1u << (ci & 31));
@@ -248,25 +252,34 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         if (!a.toy && tid < active) {
             const int yi = (int)__umulhi(ci, magic), xi = (int)ci - yi * L;
             const int yj = (int)__umulhi(cj, magic), xj = (int)cj - yj * L;
-            const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
-            const Real *colj = tinv + fxj, *coli = tinv + fxi;
-            if (kPow2) {
-                const int Lm = L - 1;
-#pragma unroll 4
-                for (int y = uy0; y < L; y += rows_per_pass) {
-                    const int dj = (y - yj) & Lm, di = (y - yi) & Lm;
-                    const int fyj = min(dj, L - dj), fyi = min(di, L - di);
-                    const Real ta = colj[fyj * H1], tb = coli[fyi * H1];
-                    Real *e = eps + y * L + ux;
-                    *e = Prec<Real>::add(*e, Prec<Real>::sub(ta, tb));
+            const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);
+            // columns of (x, .) and (x + L/2, .) relative to j and to i
+            const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
+            const Real *ci0 = tinv + fxi, *ci1 = tinv + (Lh - fxi);
+            const int LhH1 = Lh * H1, LhL = Lh * L;
+            Real *e = eps + by0 * L + bx;
+#pragma unroll 2
+            for (int y = by0; y < Lh; y += rpp, e += rpp * L) {
+                int fyj, fyi;
+                if (kPow2) {
+                    const int dj = (y - yj) & (L - 1), di = (y - yi) & (L - 1);
+                    fyj = min(dj, L - dj);
+                    fyi = min(di, L - di);
+                } else {
+                    fyj = fold_axis(y - yj, L);
+                    fyi = fold_axis(y - yi, L);
                 }
-            } else {
-                for (int y = uy0; y < L; y += rows_per_pass) {
-                    const int fyj = fold_axis(y - yj, L), fyi = fold_axis(y - yi, L);
-                    const Real ta = colj[fyj * H1], tb = coli[fyi * H1];
-                    Real *e = eps + y * L + ux;
-                    *e = Prec<Real>::add(*e, Prec<Real>::sub(ta, tb));
-                }
+                // rows fold(y - .) and L/2 - fold(y - .) = fold(y + L/2 - .)
+                const int oj0 = fyj * H1, oj1 = LhH1 - oj0;
+                const int oi0 = fyi * H1, oi1 = LhH1 - oi0;
+                const Real a00 = cj0[oj0], b00 = ci0[oi0];
+                const Real a10 = cj1[oj0], b10 = ci1[oi0];
+                const Real a01 = cj0[oj1], b01 = ci0[oi1];
+                const Real a11 = cj1[oj1], b11 = ci1[oi1];
+                e[0] = Prec<Real>::add(e[0], Prec<Real>::sub(a00, b00));
+                e[Lh] = Prec<Real>::add(e[Lh], Prec<Real>::sub(a10, b10));
+                e[LhL] = Prec<Real>::add(e[LhL], Prec<Real>::sub(a01, b01));
+                e[LhL + Lh] = Prec<Real>::add(e[LhL + Lh], Prec<Real>::sub(a11, b11));
             }
         }
         __syncthreads();
