@@ -81,7 +81,7 @@ typedef struct {
     int32_t precision;          /* CG_FP64 or CG_FP32                           */
     int32_t refresh_kind;       /* CG_REFRESH_*                                 */
     uint32_t refresh_every;     /* FP32: hops between refreshes, 0 = never      */
-    int32_t block_threads;      /* 0 = automatic; else 128..1024, multiple of 32 */
+    int32_t block_threads;      /* 0 = automatic; else 256, 384, 512 or 1024  */
     uint64_t max_rounds_per_hop;/* 0 = 2^32                                     */
     int32_t device;             /* CUDA device ordinal                          */
     int32_t use_graph;          /* 1: cg_run replays a captured CUDA graph      */
@@ -301,6 +301,15 @@ int cg_set_toy_acceptance(cg_handle *h, double A0);
 int cg_debug_philox(const uint32_t *ctr_host, const uint32_t *key_host,
                     uint32_t *out_host, int n);
 int cg_debug_exp(const double *x_host, double *out_host, int n);
+
+/* Test-only: the PR kernels' tower sampler (guide table + thresholds of
+ * replica `replica`, section "Hopping conduction in the Coulomb glass": hop
+ * vector by tower sampling) on the GPU for n 32-bit words x1 (host arrays).
+ * v_host[k] = the smallest vector index v with x1 < C_v, C the integer
+ * cumulative weights in the table's order, or -1 for a null proposal
+ * (x1 >= C_{V-1}).  Returns CG_EINVAL for bad arguments, CG_ECUDA on a CUDA
+ * error; allocates and frees device memory internally. */
+int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *v_host, int n);
 
 /* Library version string. */
 const char *cg_version(void);

@@ -138,6 +138,8 @@ def lib():
         L.orc_set_counters.restype = None
         L.orc_set_toy.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_set_toy.restype = None
+        L.orc_tower_many.argtypes = [ctypes.c_void_p, u32p, i32p, ctypes.c_int]
+        L.orc_tower_many.restype = None
         L.orc_delta_e.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int]
         L.orc_delta_e.restype = ctypes.c_double
@@ -224,6 +226,14 @@ class Chain:
                                   _ptr(Wi, ctypes.c_uint64),
                                   _ptr(w, ctypes.c_double))
         return dx, dy, Wi, w
+
+    def tower(self, x1):
+        """Tower sampling (vector index, -1 for a null proposal) for words x1."""
+        x1 = np.ascontiguousarray(x1, dtype=np.uint32)
+        out = np.zeros(len(x1), np.int32)
+        self._lib.orc_tower_many(self._h, _ptr(x1, ctypes.c_uint32), _ptr(out, ctypes.c_int32),
+                                 len(x1))
+        return out
 
     def tinv_table(self):
         t = np.zeros((self.Ly // 2 + 1, self.Lx // 2 + 1), np.float64)

@@ -472,6 +472,13 @@ static int tower_sample(const orc_chain *c, uint32_t x1)
     return lo;
 }
 
+/* The tower sampler for n words x1 (-1 marks a null proposal). */
+void orc_tower_many(const orc_chain *c, const uint32_t *x1, int32_t *out, int n)
+{
+    int k;
+    for (k = 0; k < n; ++k) out[k] = tower_sample(c, x1[k]);
+}
+
 void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *out)
 {
     uint32_t ctr[4], key[2];

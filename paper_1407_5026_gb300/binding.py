@@ -29,7 +29,7 @@ EXPORTED = [
     "cg_destroy", "cg_last_error", "cg_num_replicas", "cg_num_sites", "cg_run",
     "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
-    "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_version",
+    "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_debug_tower", "cg_version",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
     "cg_set_trace", "cg_read_trace",
 ]
@@ -136,6 +136,8 @@ def load(path: str | None = None):
             "cg_set_toy_acceptance": (ctypes.c_int, [vp, ctypes.c_double]),
             "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
             "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
+            "cg_debug_tower": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u32p,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
             "cg_version": (ctypes.c_char_p, []),
             "cg_refresh_tc_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      vp, vp, vp, vp, vp]),
@@ -372,6 +374,14 @@ def cg_debug_exp(x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = np.zeros_like(x)
     _check(load().cg_debug_exp(_ptr(x, ctypes.c_double), _ptr(out, ctypes.c_double), len(x)))
+    return out
+
+
+def cg_debug_tower(h, replica, x1):
+    x1 = np.ascontiguousarray(x1, dtype=np.uint32)
+    out = np.zeros(len(x1), dtype=np.int32)
+    _check(load().cg_debug_tower(h, replica, _ptr(x1, ctypes.c_uint32),
+                                 _ptr(out, ctypes.c_int32), len(x1)))
     return out
 
 

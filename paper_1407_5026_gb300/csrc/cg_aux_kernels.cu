@@ -12,6 +12,7 @@
 //                 for tests.
 #include "cg_device.cuh"
 #include "cg_internal.h"
+#include "cg_pr_common.cuh"
 
 namespace cg {
 
@@ -149,6 +150,23 @@ __global__ void debug_exp_kernel(const double *x, double *out, int n)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = cg_exp_accept(x[t]);
+}
+
+__global__ void debug_tower_kernel(const unsigned short *guide, const unsigned *thr, int V,
+                                   const uint32_t *x1, int *out, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    // the PR kernels' sampler (on the global copies of the tables); -1 marks a
+    // null proposal
+    out[t] = x1[t] > thr[V - 1] ? -1 : tower_lookup(guide, thr, x1[t]);
+}
+
+cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr, int V,
+                               const uint32_t *x1, int *out, int n, cudaStream_t st)
+{
+    debug_tower_kernel<<<(n + 127) / 128, 128, 0, st>>>(guide, thr, V, x1, out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,

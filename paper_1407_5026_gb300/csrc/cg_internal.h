@@ -138,6 +138,8 @@ cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int word
 cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key,
                                 uint32_t *out, int n, cudaStream_t st);
 cudaError_t launch_debug_exp(const double *x, double *out, int n, cudaStream_t st);
+cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr, int V,
+                               const uint32_t *x1, int *out, int n, cudaStream_t st);
 cudaError_t set_pr_smem_limit(int precision, int bytes);
 int microbench(int kind, int device, double *result);
 cudaError_t launch_reset_refresh_err(const DevReplica *d_reps, const int *d_index, int R,

@@ -148,8 +148,11 @@ int build_tables(Tables &t, int L, double xi, int r_max)
         run += Wk;
         t.thr.push_back((unsigned)(run - 1));
     }
-    // guide table: smallest vector whose threshold reaches each bucket, flag
-    // set when a threshold lies inside the bucket
+    // guide table: smallest vector whose threshold reaches each bucket (14
+    // bits); bit 15 set when a threshold lies inside the bucket (one compare
+    // decides between it and the next vector), bit 14 when two or more do
+    // (the sampler then keeps scanning)
+    if (t.V > 0x3fff) return fail(CG_EINVAL, "more than 16383 hop vectors (r_max too large)");
     t.guide.assign(kGuide, 0);
     const int shift = 32 - kGuideBits;
     int v = 0;
@@ -158,7 +161,8 @@ int build_tables(Tables &t, int L, double xi, int r_max)
         const unsigned long long hi = lo + (1ull << shift) - 1;
         while (v < t.V - 1 && t.thr[v] < lo) ++v;
         const bool scan = t.thr[v] >= lo && t.thr[v] < hi;
-        t.guide[b] = (unsigned short)(v | (scan ? 0x8000 : 0));
+        const bool multi = scan && v + 1 < t.V && t.thr[v + 1] < hi;
+        t.guide[b] = (unsigned short)(v | (scan ? 0x8000 : 0) | (multi ? 0x4000 : 0));
     }
     return CG_OK;
 }
@@ -303,11 +307,13 @@ int choose_cluster(const cg_opts &o, const Rep &r, int optin)
     return 0;
 }
 
+// CTA size of a single-CTA group: the update needs at least L/2 threads (one
+// per base column); 384 is accepted as given.
 int choose_threads(const cg_opts &o, int L, int smem)
 {
     int t = o.block_threads;
     if (t == 0) t = (o.precision == CG_FP64 || smem > 110 * 1024) ? 1024 : 512;
-    while (t < L && t < 1024) t *= 2;
+    while (t < L / 2 && t < 1024) t = (t == 384) ? 512 : 2 * t;
     return t;
 }
 
@@ -495,9 +501,9 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         fail(CG_EINVAL, "precision must be CG_FP64 or CG_FP32");
         return nullptr;
     }
-    if (o.block_threads && (o.block_threads != 256 && o.block_threads != 512 &&
-                            o.block_threads != 1024)) {
-        fail(CG_EINVAL, "block_threads must be 0, 256, 512 or 1024");
+    if (o.block_threads && (o.block_threads != 256 && o.block_threads != 384 &&
+                            o.block_threads != 512 && o.block_threads != 1024)) {
+        fail(CG_EINVAL, "block_threads must be 0, 256, 384, 512 or 1024");
         return nullptr;
     }
     if (o.max_rounds_per_hop == 0) o.max_rounds_per_hop = 1ull << 32;
@@ -605,7 +611,11 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         g.smem = smem;
         g.cluster = cluster;
         g.threads = choose_threads(o, g.L, smem);
-        if (cluster > 1 && g.threads < 512) g.threads = 512;
+        if (cluster > 1) {
+            // the cluster kernel maps a thread to a column: at least L threads
+            if (g.threads < 512) g.threads = 512;
+            while (g.threads < g.L && g.threads < 1024) g.threads *= 2;
+        }
         g.tc = group_uses_tc(o, g.L, g.count);
         if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.count)) ||
                      dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
@@ -1120,11 +1130,11 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
         double best = -1.0;
         int best_t = g.threads;
         unsigned best_M = g.M;
-        const int shapes[3] = {256, 512, 1024};
+        const int shapes[4] = {256, 384, 512, 1024};
         const unsigned Ms[3] = {1024, 4096, 16384};
-        for (int ti = 0; ti < 3 && ce == cudaSuccess; ++ti) {
+        for (int ti = 0; ti < 4 && ce == cudaSuccess; ++ti) {
             const int t = shapes[ti];
-            if (t < g.L || (g.cluster > 1 && t < 512)) continue;
+            if (t < g.L / 2 || (g.cluster > 1 && (t < 512 || t < g.L))) continue;
             for (int mi = 0; mi < 3 && ce == cudaSuccess; ++mi) {
                 Group trial = g;
                 trial.threads = t;
@@ -1308,6 +1318,24 @@ int cg_debug_exp(const double *x_host, double *out_host, int n)
     cudaMemcpy(d, x_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
     cudaError_t e = launch_debug_exp(d, d + n, n, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out_host, d + n, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
+    return CG_OK;
+}
+
+int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *v_host, int n)
+{
+    if (!h || n <= 0 || !x1_host || !v_host) return fail(CG_EINVAL, "bad arguments");
+    if (replica < 0 || replica >= (int)h->reps.size()) return fail(CG_EINVAL, "replica out of range");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    const Tables &t = *h->reps[replica].tab;
+    char *d = nullptr;
+    CG_CUDA(cudaMalloc((void **)&d, 8 * (size_t)n));
+    uint32_t *dx = (uint32_t *)d;
+    int *dv = (int *)(d + 4 * (size_t)n);
+    cudaError_t e = cudaMemcpy(dx, x1_host, 4 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_tower(t.d_guide, t.d_thr, t.V, dx, dv, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(v_host, dv, 4 * (size_t)n, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
     return CG_OK;

@@ -61,6 +61,22 @@ struct Shared {
     float *cv32;              // 1/r_v + E dx_v rounded once to binary32
 };
 
+// Tower sampling: the smallest vector index v with x1 <= thr[v] (thr[v] =
+// C_v - 1, C the integer cumulative weights), for x1 <= thr[V-1].  The guide
+// bucket of x1's top bits holds the first candidate; one threshold inside
+// the bucket costs a predicated compare, several (rare) a scan.
+__device__ __forceinline__ int tower_lookup(const unsigned short *guide, const unsigned *thr,
+                                            uint32_t x1)
+{
+    const unsigned g = guide[x1 >> (32 - kGuideBits)];
+    int v = (int)(g & 0x3fffu);
+    const unsigned t0 = thr[v];
+    v += (int)(((g >> 15) & 1u) & (unsigned)(x1 > t0));
+    if (g & 0x4000u)
+        while (x1 > thr[v]) ++v;
+    return v;
+}
+
 struct Prop {
     unsigned i, j;
     int v, dxy;
@@ -86,10 +102,7 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     // evaluated on a clamped x1 without a branch and can never pass theta
     const uint32_t x1 = min(x[1], thr_last);
     const bool live = valid && x[1] <= thr_last;
-    const unsigned g = S.guide[x1 >> (32 - kGuideBits)];
-    int v = (int)(g & 0x7fffu);
-    if (g & 0x8000u)
-        while (x1 > S.thr[v]) ++v;               // the bucket holds a threshold
+    const int v = tower_lookup(S.guide, S.thr, x1);
     const int dxy = S.disp[v];
     const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
     if (kPow2) {

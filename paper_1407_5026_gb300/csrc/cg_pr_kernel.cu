@@ -40,27 +40,37 @@
 
 namespace cg {
 
-template <typename Real, int kThreads, bool kPow2>
+// kLog2L > 0: L = 2^kLog2L fixed at compile time (the lattice constants
+// fold into immediates and free registers for the labels); kLog2L = 0: L a
+// power of two known at run time; kLog2L < 0: any even L.
+template <typename Real, int kThreads, int kLog2L>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
+    constexpr bool kPow2 = kLog2L >= 0;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
-    // counters only thread 0 advances (registers stay free for the labels)
+    // counters and pointers only thread 0 uses (registers stay free for the
+    // labels)
     __shared__ struct {
         unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd;
         long long P, t0;
         double energy;
+        cg_hop *log;
+        int tracing;
         float m_ema;
     } s_c;
 
     const DevReplica &Rg = reps[index[blockIdx.x]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int L = Rg.L, N = Rg.N, H1 = Rg.H1, V = Rg.V, words = Rg.words;
-    const unsigned magic = Rg.magicL;
+    const int L = kLog2L > 0 ? (1 << kLog2L) : Rg.L;
+    const int N = L * L, H1 = L / 2 + 1, words = (N + 31) / 32;
+    const int V = Rg.V;
+    const unsigned magic = kPow2 ? 0u : Rg.magicL;
+    const int log2L = kLog2L > 0 ? kLog2L : __ffs(L) - 1;   // used when L is a power of two
     const uint32_t key0 = Rg.key0, key1 = Rg.key1, rep = Rg.replica;
-    const double T = Rg.T, E = Rg.E;
+    const double T = Rg.T;
     const float invTf = (float)(1.0 / T);
 
     const SmemLayout lay = smem_layout(N, H1, V, words, (int)sizeof(Real));
@@ -94,15 +104,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             S.thr[l] = Rg.thr[l];
             S.disp[l] = dxy;
             S.vr64[l] = Rg.tinvd[l];
-            S.edx64[l] = d_mul(E, (double)dx);          // E * dx, as in the serial chain
+            S.edx64[l] = d_mul(Rg.E, (double)dx);       // E * dx, as in the serial chain
             S.cv32[l] = (float)d_add(Rg.tinvd[l], S.edx64[l]);   // one rounding to binary32
         }
     }
-    DevCounters *cnt = Rg.ctr;
-    cg_hop *const hop_log = Rg.log;
-    const bool tracing = Rg.trace != nullptr;
-    unsigned long long rounds = cnt->rounds;
+    unsigned long long rounds = Rg.ctr->rounds;
     if (tid == 0) {
+        const DevCounters *cnt = Rg.ctr;
+        s_c.log = Rg.log;
+        s_c.tracing = Rg.trace != nullptr;
         s_c.hops = cnt->hops;
         s_c.attempts = cnt->attempts;
         s_c.evaluated = cnt->evaluated;
@@ -117,23 +127,25 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 
     const unsigned M = a.M;
     const unsigned thr_last = S.thr[V - 1];
-    const int log2L = __ffs(L) - 1;      // used when L is a power of two
-    // update mapping: thread -> base column bx < L/2, base rows by0, by0 + rpp, ...
-    const int Lh = L >> 1;
-    const int rpp = kThreads / Lh;
-    const int active = rpp * Lh;
-    const int bx = tid % Lh, by0 = tid / Lh;
 
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
         if (tid == 0) s_c.t0 = clock64();
         // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
-        // worth b ~ 64 labels (uniform: m_ema is identical in every thread)
-        unsigned C = 64;
-        {
-            const float want = sqrtf(128.0f * s_c.m_ema);
-            while (C < (unsigned)(2 * kThreads) && (float)C < want) C <<= 1;
+        // worth b ~ 64 labels: two per thread (C = 2 blockDim) when that
+        // exceeds blockDim, else one per thread for the first C threads (C a
+        // power of two >= 64); m_ema is identical in every thread, so the
+        // choice is uniform and idle warps skip the labels whole
+        const float want = sqrtf(128.0f * s_c.m_ema);
+        unsigned C;
+        if (want > (float)kThreads) {
+            C = 2u * kThreads;
+        } else {
+            C = 64;
+            while (C < (unsigned)kThreads && (float)C < want) C <<= 1;
+            if (C > (unsigned)kThreads) C = kThreads;
         }
-        const unsigned half = C >> 1;
+        const bool two = C > (unsigned)kThreads;
+        const bool act = (unsigned)tid < C;
         unsigned long long p = 0;
         unsigned q = 0, win = 0;
         bool found = false;
@@ -142,24 +154,28 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             const PhiloxPrefix PP =
                 philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
             for (unsigned kb = 0; kb < M; kb += C) {
-                const bool mine = (unsigned)tid < half;
-                const unsigned k0 = kb + (unsigned)tid, k1 = k0 + half;
-                const Prop p0 = propose<kPow2>(S, k0, PP, key0, key1, L, log2L, (unsigned)N,
-                                               magic, thr_last, mine && k0 < M);
-                const Prop p1 = propose<kPow2>(S, k1, PP, key0, key1, L, log2L, (unsigned)N,
-                                               magic, thr_last, mine && k1 < M);
+                const unsigned k0 = kb + (unsigned)tid, k1 = k0 + (unsigned)kThreads;
+                const bool v0 = k0 < M, v1 = two && k1 < M;
+                Prop p0{}, p1{};
                 double dE0 = 0.0, dE1 = 0.0;
                 bool acc0 = false, acc1 = false;
-                if (a.toy) {
-                    const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
-                    const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
-                    acc0 = mine && k0 < M && u0 < a.toy_A0;
-                    acc1 = mine && k1 < M && u1 < a.toy_A0;
-                } else if (sizeof(Real) == 4) {
-                    accept2_f32(S, p0, p1, T, invTf, acc0, acc1, dE0, dE1);
-                } else {
-                    if (p0.theta) acc0 = accept<Real>(S, p0, T, invTf, dE0);
-                    if (p1.theta) acc1 = accept<Real>(S, p1, T, invTf, dE1);
+                if (act) {
+                    p0 = propose<kPow2>(S, k0, PP, key0, key1, L, log2L, (unsigned)N, magic,
+                                        thr_last, v0);
+                    if (two)
+                        p1 = propose<kPow2>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
+                                            thr_last, v1);
+                    if (a.toy) {
+                        const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
+                        const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
+                        acc0 = v0 && u0 < a.toy_A0;
+                        acc1 = v1 && u1 < a.toy_A0;
+                    } else if (sizeof(Real) == 4 && two) {
+                        accept2_f32(S, p0, p1, T, invTf, acc0, acc1, dE0, dE1);
+                    } else {
+                        if (p0.theta) acc0 = accept<Real>(S, p0, T, invTf, dE0);
+                        if (p1.theta) acc1 = accept<Real>(S, p1, T, invTf, dE1);
+                    }
                 }
                 const int any = __syncthreads_or(acc0 || acc1);
                 if (tid == 0) s_c.evaluated += (M - kb < C) ? (M - kb) : C;
@@ -178,7 +194,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                         }
                     } else if (b1) {
                         const int first = __ffs(b1) - 1;
-                        off = half + (unsigned)(warp * 32 + first);
+                        off = (unsigned)(kThreads + warp * 32 + first);
                         if (lane == first) {
                             s_cand[warp].i = p1.i;
                             s_cand[warp].j = p1.j;
@@ -192,7 +208,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 #pragma unroll
                     for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
                     q = kb + wl + 1;                 // 1-based label in the round
-                    win = (wl >= half ? wl - half : wl) >> 5;
+                    win = (wl >= (unsigned)kThreads ? wl - (unsigned)kThreads : wl) >> 5;
                     found = true;
                     break;
                 }
@@ -231,15 +247,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 s_c.P += cdx;
                 s_c.energy = d_add(s_c.energy, c.dE);
             }
-            if (tracing) trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
+            if (s_c.tracing) trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
-            if (hop_log) {
+            if (s_c.log) {
                 cg_hop e;
                 e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
                 e.dx = a.toy ? 0 : cdx; e.dy = a.toy ? 0 : cdy;
                 e.dE = a.toy ? 0.0 : c.dE;
-                hop_log[a.log_offset + h] = e;
+                s_c.log[a.log_offset + h] = e;
             }
             if (!a.toy) {
                 S.occ[ci >> 5] &= ~(1u << (ci & 31));
@@ -249,9 +265,14 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         rounds += 1;
 
         // ---- local-energy update (step 3b) ----
-        if (!a.toy && tid < active) {
-            const int yi = (int)__umulhi(ci, magic), xi = (int)ci - yi * L;
-            const int yj = (int)__umulhi(cj, magic), xj = (int)cj - yj * L;
+        // thread -> base column bx < L/2, base rows by0, by0 + rpp, ...
+        const int Lh = L >> 1;
+        const int rpp = kThreads / Lh;
+        if (!a.toy && tid < rpp * Lh) {
+            const int bx = tid % Lh, by0 = tid / Lh;
+            const int yi = kPow2 ? (int)(ci >> log2L) : (int)__umulhi(ci, magic);
+            const int yj = kPow2 ? (int)(cj >> log2L) : (int)__umulhi(cj, magic);
+            const int xi = (int)ci - yi * L, xj = (int)cj - yj * L;
             const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);
             // columns of (x, .) and (x + L/2, .) relative to j and to i
             const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
@@ -293,6 +314,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         for (int l = tid; l < words; l += kThreads) Rg.occ[l] = S.occ[l];
     }
     if (tid == 0) {
+        DevCounters *cnt = Rg.ctr;
         cnt->rounds = rounds;
         cnt->hops = s_c.hops;
         cnt->attempts = s_c.attempts;
@@ -308,24 +330,38 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 
 template <typename Real, int kThreads>
 static cudaError_t launch_t(const DevReplica *d_reps, const int *d_index, int n_ctas,
-                            int smem_bytes, const RunArgs &args, cudaStream_t st, bool pow2)
+                            int smem_bytes, const RunArgs &args, cudaStream_t st, int L)
 {
-    if (pow2)
-        pr_persistent<Real, kThreads, true>
-            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
-    else
-        pr_persistent<Real, kThreads, false>
-            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+    switch (L) {
+    case 64:
+        pr_persistent<Real, kThreads, 6><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    case 128:
+        pr_persistent<Real, kThreads, 7><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    default:
+        if ((L & (L - 1)) == 0)
+            pr_persistent<Real, kThreads, 0><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        else
+            pr_persistent<Real, kThreads, -1><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+    }
     return cudaGetLastError();
 }
 
 template <typename Real, int kThreads>
 static cudaError_t set_smem_one(int bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e) return e;
-    return cudaFuncSetAttribute(pr_persistent<Real, kThreads, false>,
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 6>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 7>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 0>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    return cudaFuncSetAttribute(pr_persistent<Real, kThreads, -1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -335,6 +371,7 @@ static cudaError_t set_smem_t(int bytes)
     cudaError_t e;
     if ((e = set_smem_one<Real, 1024>(bytes))) return e;
     if ((e = set_smem_one<Real, 512>(bytes))) return e;
+    if ((e = set_smem_one<Real, 384>(bytes))) return e;
     return set_smem_one<Real, 256>(bytes);
 }
 
@@ -347,18 +384,20 @@ cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const 
                                  int n_ctas, int threads, int smem_bytes, const RunArgs &args,
                                  cudaStream_t st, int L)
 {
-    const bool pow2 = (L & (L - 1)) == 0;
+    if (threads < L / 2) return cudaErrorInvalidValue;     // the update needs L/2 columns
     if (precision == CG_FP64) {
         switch (threads) {
-        case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
-        case 512: return launch_t<double, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
-        case 256: return launch_t<double, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 512: return launch_t<double, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 384: return launch_t<double, 384>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 256: return launch_t<double, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
         }
     } else {
         switch (threads) {
-        case 1024: return launch_t<float, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
-        case 512: return launch_t<float, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
-        case 256: return launch_t<float, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, pow2);
+        case 1024: return launch_t<float, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 512: return launch_t<float, 512>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 384: return launch_t<float, 384>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+        case 256: return launch_t<float, 256>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
         }
     }
     return cudaErrorInvalidValue;
