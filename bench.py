@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # workload (304 replicas x 1024 hops), from the ncu capture summarised in
 # profiles/pr_persistent_fp32_L128_R304_relaxed.md; valid only while the
 # kernel sources hash to the captured version.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "1cc8713741233dd3", "bytes_per_launch": 30.7e6,
+TRAFFIC_CAPTURE = {"sources_sha256_16": "e2fa40e5e8cd9aeb", "bytes_per_launch": 20.72e6,
                    "replicas": 304, "hops_per_replica": 1024}
 
 
@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--fp64-hops", type=int, default=3000)
     ap.add_argument("--relax-steps", type=int, default=40,
                     help="untimed steps from the random start before warm-up")
+    ap.add_argument("--obs-samples", type=int, default=64,
+                    help="disorder samples of the binary32-vs-binary64 observable check (0: skip)")
+    ap.add_argument("--obs-hops", type=int, default=32768)
+    ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -414,6 +418,16 @@ def run_ours(args):
         result["fp64_form"]["dadd_peak_per_s"] = dadd_peak
         result["fp32_batched_over_fp64_form"] = result["value"] / result["fp64_form"]["hops_per_s"]
 
+    # binary32 form (with its binary64 refresh) against the binary64 form on
+    # the same disorder samples: paired differences of the observables
+    if args.obs_samples > 0 and rank == 0:
+        result["fp32_vs_fp64_observables"] = observable_check(args, B, local)
+
+    # the mixed-L batch and the cluster-sized lattice (not the headline
+    # workload): throughput of their own launch paths
+    if not args.no_other_configs and rank == 0:
+        result["other_configs"] = other_configs(args, B, local)
+
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, run one step, read the state back
     if not args.no_e2e:
@@ -425,6 +439,88 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def observable_check(args, B, local):
+    """Runs the same obs_samples disorder replicas of the workload in binary32
+    (refresh every 1024 hops) and in binary64 from their common random start
+    for obs_hops hops; returns per observable the mean paired difference, its
+    standard error and z = mean / SE, and the largest eps error any binary32
+    replica saw at its refreshes."""
+    import math
+    import numpy as np
+    reps = replicas_for(0, args.obs_samples)
+    out = {}
+    vals = {}
+    for key, prec in (("fp32", B.CG_FP32), ("fp64", B.CG_FP64)):
+        s = B.System(reps, precision=prec, device=local,
+                     refresh_every=HOPS_PER_STEP if prec == B.CG_FP32 else 0)
+        s.run(args.obs_hops, args.M)
+        obs = [s.observables(k) for k in range(len(reps))]
+        vals[key] = np.array([[o["energy_per_site"], o["P"], o["acceptance"]] for o in obs])
+        if prec == B.CG_FP32:
+            out["max_eps_err"] = max(o["max_eps_err_last_refresh"] for o in obs)
+        s.close()
+    d = vals["fp32"] - vals["fp64"]
+    n = len(reps)
+    for col, name in enumerate(("E_per_site", "P", "acceptance")):
+        mean = float(d[:, col].mean())
+        se = float(d[:, col].std(ddof=1) / math.sqrt(n))
+        out[name] = {"fp64_mean": float(vals["fp64"][:, col].mean()),
+                     "mean_diff": mean, "se": se, "z": (mean / se) if se > 0 else 0.0}
+    out["samples"] = n
+    out["hops"] = args.obs_hops
+    out["start"] = "the random initial configuration of each replica, identical in both forms"
+    return out
+
+
+def shape_of(B, h, g, tuned):
+    sh = B.cg_group_shape(h, g)
+    if not tuned:
+        sh.pop("M")        # the group's own M applies only to runs with M = 0
+    return sh
+
+
+def other_configs(args, B, local):
+    """Throughput of the two other batch configurations: 256 replicas with L
+    drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
+    replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
+    tensor-core refresh per same-L group every 1024 hops), and 16 replicas of
+    L=256 whose eps is split over a thread-block cluster (refresh every 4096
+    hops).  Each is timed with CUDA events over hops that follow a relaxation
+    from the random start."""
+    import torch
+    from paper_1407_5026_gb300 import workloads as W
+    out = {}
+    for name, wl, relax, hops, graph, tune in (
+            ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
+            ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, False)):
+        reps = [r.as_dict() for r in wl.replicas]
+        s = B.System(reps, precision=B.CG_FP32, refresh_every=wl.refresh_every,
+                     use_graph=graph, device=local)
+        s.run(relax, wl.M)
+        if tune:
+            B.cg_autotune(s.h, 256)
+        M = 0 if tune else wl.M
+        o0 = [B.cg_observables(s.h, k) for k in range(len(reps))]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(s.stream):
+            ev[0].record(s.stream)
+            B.cg_run_async(s.h, hops, M)
+            ev[1].record(s.stream)
+            B.cg_sync(s.h)
+        o1 = [B.cg_observables(s.h, k) for k in range(len(reps))]
+        dt = ev[0].elapsed_time(ev[1]) * 1e-3
+        dh = sum(b["hops"] - a["hops"] for a, b in zip(o0, o1))
+        da = sum(b["attempts"] - a["attempts"] for a, b in zip(o0, o1))
+        out[name] = {"hops_per_s": dh / dt, "attempts_per_s": da / dt, "acceptance": dh / max(1, da),
+                     "replicas": len(reps), "hops_per_replica": hops, "relaxed_hops": relax,
+                     "M": "autotuned per L" if tune else wl.M,
+                     "groups": [shape_of(B, s.h, g, tune) for g in range(B.cg_num_groups(s.h))],
+                     "max_eps_err": max(o["max_eps_err_last_refresh"] for o in o1),
+                     "graph": bool(graph)}
+        s.close()
+    return out
 
 
 def e2e(args, B, reps, local):
