@@ -363,6 +363,10 @@ def run_ours(args):
                      "bytes_per_hop": bytes_per_hop,
                      "peak_source": "measured: shared-memory 32-bit read-modify-write "
                                     "microbenchmark over all SMs (cg_microbench kind 0)"},
+        # the refresh as a whole (error reset, S image, contraction,
+        # reduction) against the measured sustained BF16 tensor peak: the
+        # contraction is 2 (hi, lo) x 2 N^2 flop per replica
+        "refresh_roofline": refresh_roofline(N, R, statistics.mean(ref_ms)),
         "phase_split": {"refresh_ms_per_step": statistics.mean(ref_ms),
                         "run_ms_per_step": statistics.mean(run_ms),
                         "update_cycles_frac": cyc_upd / max(1, cyc_upd + cyc_rej),
@@ -472,6 +476,23 @@ def observable_check(args, B, local):
     out["hops"] = args.obs_hops
     out["start"] = "the random initial configuration of each replica, identical in both forms"
     return out
+
+
+def refresh_roofline(N, R, ms):
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    if "bf16_tflops_sustained" in peaks:
+        peak, src = float(peaks["bf16_tflops_sustained"]), "of measured (MEASURED_PEAKS.json, sustained BF16)"
+    else:
+        peak, src = 1700.0, "of fallback (1.7 PFLOP/s sustained BF16)"
+    achieved = 4.0 * N * N * R / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src, "kernel": "refresh_tc_kernel (+ pack, reduce)",
+            "flop_per_refresh": 4.0 * N * N * R}
 
 
 def shape_of(B, h, g, tuned):
