@@ -147,7 +147,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         const bool two = C > (unsigned)kThreads;
         const bool act = (unsigned)tid < C;
         unsigned long long p = 0;
-        unsigned q = 0, win = 0;
+        unsigned q = 0, win = 0, kb_hit = 0;
         bool found = false;
         while (!found) {
             ++p;
@@ -178,7 +178,6 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                     }
                 }
                 const int any = __syncthreads_or(acc0 || acc1);
-                if (tid == 0) s_c.evaluated += (M - kb < C) ? (M - kb) : C;
                 if (any) {
                     const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
                     const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
@@ -208,13 +207,17 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 #pragma unroll
                     for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
                     q = kb + wl + 1;                 // 1-based label in the round
+                    kb_hit = kb;
                     win = (wl >= (unsigned)kThreads ? wl - (unsigned)kThreads : wl) >> 5;
                     found = true;
                     break;
                 }
             }
             if (!found) {
-                if (tid == 0) s_c.attempts += M;
+                if (tid == 0) {
+                    s_c.attempts += M;
+                    s_c.evaluated += M;
+                }
                 rounds += 1;
                 // bounded hop: thread 0 reads its SM's cycle counter (the limit
                 // is in cycles at the peak clock), the block-wide OR makes the
@@ -242,6 +245,8 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
             s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
             s_c.attempts += q;
+            // the chunks of the hop's round up to the accepting one
+            s_c.evaluated += (kb_hit + C < M) ? (kb_hit + C) : M;
             s_c.hops += 1;
             if (!a.toy) {
                 s_c.P += cdx;
