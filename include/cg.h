@@ -291,6 +291,34 @@ int cg_num_groups(const cg_handle *h);
 int cg_group_shape(const cg_handle *h, int index, int *L, int *threads,
                    unsigned int *M, int *cluster);
 
+/* Replica indices of group `group`, in the group's order (count = the
+ * number of replicas with that L; ascending replica index).  The paper has
+ * no counterpart: this and the next two calls are the batch form of the
+ * state I/O (checkpoint/resume of a whole batch).  CG_EINVAL for a bad
+ * group or a NULL output. */
+int cg_group_replicas(const cg_handle *h, int group, int *replicas_out);
+
+/* Read the state of every replica of one group in one copy per array
+ * (device order = cg_group_replicas order; NULL pointers are skipped):
+ *   occ_words_host  count * ceil(N/32) words, bit s of word s/32 = n_s;
+ *   eps_host        count * N values in the handle's precision (double for
+ *                   CG_FP64, float for CG_FP32), not widened;
+ *   c_host          count counter records.
+ * Pinned host buffers make the copies asynchronous DMA; the call blocks
+ * until they are done.  CG_EINVAL for a bad group, CG_ECUDA on a CUDA error. */
+int cg_read_group_state(cg_handle *h, int group, uint32_t *occ_words_host,
+                        void *eps_host, cg_counters *c_host);
+
+/* Write the same arrays back (NULL pointers are skipped).  Occupations and
+ * eps are stored as given: eps is not recomputed (cg_refresh rebuilds it
+ * from the occupation); every replica must keep nu*N electrons and no bit
+ * beyond site N-1, else CG_ESTATE and nothing is written.  The counter
+ * records replace the public counters; the library's own per-replica fields
+ * (chunk statistics, refresh record, trace state, phase clocks) are kept.
+ * Blocks until the copies are done. */
+int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host,
+                         const void *eps_host, const cg_counters *c_host);
+
 /* Test-only constant-acceptance mode: every label accepts iff u < A0, the
  * configuration is never changed, the counters advance.  A0 < 0 turns the
  * mode off. */

@@ -30,6 +30,7 @@ EXPORTED = [
     "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_debug_tower", "cg_version",
+    "cg_group_replicas", "cg_read_group_state", "cg_write_group_state",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
     "cg_set_trace", "cg_read_trace",
 ]
@@ -136,6 +137,9 @@ def load(path: str | None = None):
             "cg_set_toy_acceptance": (ctypes.c_int, [vp, ctypes.c_double]),
             "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
             "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
+            "cg_group_replicas": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int)]),
+            "cg_read_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, P(cg_counters)]),
+            "cg_write_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, P(cg_counters)]),
             "cg_debug_tower": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u32p,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
             "cg_version": (ctypes.c_char_p, []),
@@ -377,6 +381,54 @@ def cg_debug_exp(x):
     return out
 
 
+def cg_group_replicas(h, group):
+    """Replica indices of a group (the replicas with its L, ascending)."""
+    N = cg_group_shape(h, group)["L"] ** 2
+    count = sum(1 for k in range(cg_num_replicas(h)) if cg_num_sites(h, k) == N)
+    out = np.zeros(max(count, 1), np.int32)
+    _check(load().cg_group_replicas(h, group, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return out[:count].copy()
+
+
+def _group_arrays(h, group):
+    sh = cg_group_shape(h, group)
+    reps = cg_group_replicas(h, group)
+    N = sh["L"] ** 2
+    return len(reps), N, (N + 31) // 32
+
+
+def cg_read_group_state(h, group, occ=True, eps=True, counters=True, precision=None):
+    """Whole-group state: occ (count, words) uint32, eps (count, N) in the
+    handle's precision (pass `precision`, or float64 is assumed), counters
+    as a list of dicts.  Caller arrays (e.g. pinned) are filled in place."""
+    cnt, N, words = _group_arrays(h, group)
+    dt = np.float32 if precision == CG_FP32 else np.float64
+    o = occ if isinstance(occ, np.ndarray) else (np.zeros((cnt, words), np.uint32) if occ else None)
+    e = eps if isinstance(eps, np.ndarray) else (np.zeros((cnt, N), dt) if eps else None)
+    c = (cg_counters * cnt)() if counters else None
+    _check(load().cg_read_group_state(h, group, _ptr(o, ctypes.c_uint32),
+                                      e.ctypes.data_as(ctypes.c_void_p) if e is not None else None,
+                                      c))
+    return o, e, ([x.as_dict() for x in c] if c is not None else None)
+
+
+def cg_write_group_state(h, group, occ=None, eps=None, counters=None):
+    cnt, N, words = _group_arrays(h, group)
+    c = None
+    if counters is not None:
+        c = (cg_counters * cnt)()
+        for k, d in enumerate(counters):
+            for f, _ in cg_counters._fields_:
+                setattr(c[k], f, d[f])
+    if occ is not None:
+        assert occ.dtype == np.uint32 and occ.size == cnt * words and occ.flags.c_contiguous
+    if eps is not None:
+        assert eps.size == cnt * N and eps.flags.c_contiguous
+    return _check(load().cg_write_group_state(
+        h, group, _ptr(occ, ctypes.c_uint32) if occ is not None else None,
+        eps.ctypes.data_as(ctypes.c_void_p) if eps is not None else None, c))
+
+
 def cg_debug_tower(h, replica, x1):
     x1 = np.ascontiguousarray(x1, dtype=np.uint32)
     out = np.zeros(len(x1), dtype=np.int32)
@@ -436,3 +488,10 @@ class System:
 
     def observables(self, replica=0):
         return cg_observables(self.h, replica)
+
+    def read_group(self, group, occ=True, eps=True, counters=True):
+        return cg_read_group_state(self.h, group, occ, eps, counters,
+                                   precision=self.opts.precision)
+
+    def write_group(self, group, occ=None, eps=None, counters=None):
+        return cg_write_group_state(self.h, group, occ, eps, counters)

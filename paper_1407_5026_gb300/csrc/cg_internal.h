@@ -33,9 +33,10 @@ struct alignas(16) DevCounters {
 };
 
 // Guide table of the tower: bucket b = x1 >> (32 - kGuideBits) holds the
-// smallest vector index whose threshold is >= the bucket's first value, with
-// bit 15 set when a threshold falls inside the bucket (then a short scan
-// finds the exact vector).
+// smallest vector index whose threshold is >= the bucket's first value (14
+// bits), bit 15 set when a threshold falls strictly inside the bucket (one
+// compare decides between that vector and the next) and bit 14 when two or
+// more do (a scan finds the exact vector); see tower_lookup.
 constexpr int kGuideBits = 12;
 constexpr int kGuide = 1 << kGuideBits;
 

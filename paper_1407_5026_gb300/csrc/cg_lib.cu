@@ -585,17 +585,36 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         cudaMemcpyAsync(t->d_guide, t->guide.data(), t->guide.size() * 2, cudaMemcpyHostToDevice, h->st);
     }
     const int rb = o.precision == CG_FP64 ? 8 : 4;
-    for (auto &r : h->reps) {
-        if (dalloc(h.get(), &r.d_eps, (size_t)r.N * rb) ||
-            dalloc(h.get(), (void **)&r.d_occ, (size_t)r.words * 4) ||
-            dalloc(h.get(), (void **)&r.d_phi, (size_t)r.N * 8) ||
-            dalloc(h.get(), (void **)&r.d_ctr, sizeof(DevCounters))) { destroy_partial(); return nullptr; }
-    }
     // groups of equal L (one launch each), replica order kept inside a group
     std::vector<int> order(R);
     for (int k = 0; k < R; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return h->reps[a].d.L < h->reps[b].d.L; });
+    // each group's eps, bitmasks, phi and counters are one block per array in
+    // group order, so a group's state moves between host and device in one
+    // copy per array (cg_read_group_state / cg_write_group_state)
+    for (int k = 0; k < R;) {
+        int e = k;
+        while (e < R && h->reps[order[e]].d.L == h->reps[order[k]].d.L) ++e;
+        const Rep &r0 = h->reps[order[k]];
+        const size_t cnt = (size_t)(e - k);
+        char *eb = nullptr, *pb = nullptr;
+        unsigned *ob = nullptr;
+        DevCounters *cb = nullptr;
+        if (dalloc(h.get(), (void **)&eb, cnt * r0.N * rb) ||
+            dalloc(h.get(), (void **)&ob, cnt * r0.words * 4) ||
+            dalloc(h.get(), (void **)&pb, cnt * r0.N * 8) ||
+            dalloc(h.get(), (void **)&cb, cnt * sizeof(DevCounters))) { destroy_partial(); return nullptr; }
+        for (int m = k; m < e; ++m) {
+            Rep &r = h->reps[order[m]];
+            const size_t i = (size_t)(m - k);
+            r.d_eps = eb + i * r0.N * rb;
+            r.d_occ = ob + i * r0.words;
+            r.d_phi = reinterpret_cast<double *>(pb) + i * r0.N;
+            r.d_ctr = cb + i;
+        }
+        k = e;
+    }
     for (int k = 0; k < R;) {
         Group g;
         g.L = h->reps[order[k]].d.L;
@@ -997,6 +1016,94 @@ int cg_write_state(cg_handle *h, int replica, const uint8_t *n_host, const doubl
     if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
     if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
     return load_state(h, replica, n_host, eps_host, phi_host, c_host);
+}
+
+int cg_group_replicas(const cg_handle *h, int group, int *replicas_out)
+{
+    if (!h || group < 0 || group >= (int)h->groups.size() || !replicas_out)
+        return fail(CG_EINVAL, "bad group or null output");
+    const Group &g = h->groups[group];
+    for (int k = 0; k < g.count; ++k) replicas_out[k] = h->order[g.first + k];
+    return CG_OK;
+}
+
+int cg_read_group_state(cg_handle *h, int group, uint32_t *occ_words_host, void *eps_host,
+                        cg_counters *c_host)
+{
+    if (!h || group < 0 || group >= (int)h->groups.size()) return fail(CG_EINVAL, "bad group");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
+    const Group &g = h->groups[group];
+    const Rep &r0 = h->reps[h->order[g.first]];
+    const size_t cnt = (size_t)g.count;
+    const size_t rb = h->opts.precision == CG_FP64 ? 8 : 4;
+    if (occ_words_host)
+        CG_CUDA(cudaMemcpyAsync(occ_words_host, r0.d_occ, cnt * r0.words * 4,
+                                cudaMemcpyDeviceToHost, h->st));
+    if (eps_host)
+        CG_CUDA(cudaMemcpyAsync(eps_host, r0.d_eps, cnt * r0.N * rb, cudaMemcpyDeviceToHost,
+                                h->st));
+    std::vector<DevCounters> dc;
+    if (c_host) {
+        dc.resize(cnt);
+        CG_CUDA(cudaMemcpyAsync(dc.data(), r0.d_ctr, cnt * sizeof(DevCounters),
+                                cudaMemcpyDeviceToHost, h->st));
+    }
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    for (size_t k = 0; k < dc.size(); ++k) {
+        c_host[k].rounds = dc[k].rounds; c_host[k].hops = dc[k].hops;
+        c_host[k].attempts = dc[k].attempts; c_host[k].evaluated = dc[k].evaluated;
+        c_host[k].P = dc[k].P; c_host[k].energy = dc[k].energy;
+    }
+    return CG_OK;
+}
+
+int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host,
+                         const void *eps_host, const cg_counters *c_host)
+{
+    if (!h || group < 0 || group >= (int)h->groups.size()) return fail(CG_EINVAL, "bad group");
+    const Group &g = h->groups[group];
+    const Rep &r0 = h->reps[h->order[g.first]];
+    const size_t cnt = (size_t)g.count;
+    const size_t rb = h->opts.precision == CG_FP64 ? 8 : 4;
+    if (occ_words_host) {
+        // every replica keeps nu N electrons and no bit beyond site N - 1
+        for (size_t k = 0; k < cnt; ++k) {
+            const Rep &r = h->reps[h->order[g.first + (int)k]];
+            const uint32_t *w = occ_words_host + k * r0.words;
+            long long n = 0;
+            for (int q = 0; q < r0.words; ++q) n += __builtin_popcount(w[q]);
+            if ((r0.N & 31) && (w[r0.words - 1] >> (r0.N & 31)))
+                return fail(CG_ESTATE, "occupation bits beyond the last site");
+            if (n != (long long)std::floor(r.d.nu * r.N + 0.5))
+                return fail(CG_ESTATE, "occupation count differs from nu * N");
+        }
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->pending) CG_CUDA(cudaStreamSynchronize(h->st));
+    if (occ_words_host)
+        CG_CUDA(cudaMemcpyAsync(r0.d_occ, occ_words_host, cnt * r0.words * 4,
+                                cudaMemcpyHostToDevice, h->st));
+    if (eps_host)
+        CG_CUDA(cudaMemcpyAsync(r0.d_eps, eps_host, cnt * r0.N * rb, cudaMemcpyHostToDevice,
+                                h->st));
+    if (c_host) {
+        // the public counters are replaced; the library's own fields (chunk
+        // statistics, refresh record, trace state, phase clocks) are kept
+        std::vector<DevCounters> dc(cnt);
+        CG_CUDA(cudaMemcpyAsync(dc.data(), r0.d_ctr, cnt * sizeof(DevCounters),
+                                cudaMemcpyDeviceToHost, h->st));
+        CG_CUDA(cudaStreamSynchronize(h->st));
+        for (size_t k = 0; k < cnt; ++k) {
+            dc[k].rounds = c_host[k].rounds; dc[k].hops = c_host[k].hops;
+            dc[k].attempts = c_host[k].attempts; dc[k].evaluated = c_host[k].evaluated;
+            dc[k].P = c_host[k].P; dc[k].energy = c_host[k].energy;
+        }
+        CG_CUDA(cudaMemcpyAsync(r0.d_ctr, dc.data(), cnt * sizeof(DevCounters),
+                                cudaMemcpyHostToDevice, h->st));
+    }
+    CG_CUDA(cudaStreamSynchronize(h->st));
+    return CG_OK;
 }
 
 int cg_observables(cg_handle *h, int replica, cg_obs *out)
