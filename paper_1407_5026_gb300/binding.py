@@ -96,6 +96,9 @@ class cg_trace_point(ctypes.Structure):
 
 
 TRACE_DTYPE = np.dtype([("attempts", "<u8"), ("hops", "<u8"), ("P", "<i8"), ("energy", "<f8")])
+# layout of cg_counters, for arrays of counter records
+COUNTERS_DTYPE = np.dtype([("rounds", "<u8"), ("hops", "<u8"), ("attempts", "<u8"),
+                           ("evaluated", "<u8"), ("P", "<i8"), ("energy", "<f8")])
 
 _lib = None
 _lock = threading.Lock()
@@ -138,8 +141,8 @@ def load(path: str | None = None):
             "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
             "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
             "cg_group_replicas": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int)]),
-            "cg_read_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, P(cg_counters)]),
-            "cg_write_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, P(cg_counters)]),
+            "cg_read_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, vp]),
+            "cg_write_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, vp]),
             "cg_debug_tower": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u32p,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
             "cg_version": (ctypes.c_char_p, []),
@@ -390,43 +393,48 @@ def cg_group_replicas(h, group):
     return out[:count].copy()
 
 
-def _group_arrays(h, group):
-    sh = cg_group_shape(h, group)
+def group_dims(h, group):
+    """(replica indices, N, bitmask words per replica) of one group."""
     reps = cg_group_replicas(h, group)
-    N = sh["L"] ** 2
-    return len(reps), N, (N + 31) // 32
+    N = cg_group_shape(h, group)["L"] ** 2
+    return reps, N, (N + 31) // 32
 
 
-def cg_read_group_state(h, group, occ=True, eps=True, counters=True, precision=None):
+def _vp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cg_read_group_state(h, group, occ=True, eps=True, counters=True, precision=None, dims=None):
     """Whole-group state: occ (count, words) uint32, eps (count, N) in the
-    handle's precision (pass `precision`, or float64 is assumed), counters
-    as a list of dicts.  Caller arrays (e.g. pinned) are filled in place."""
-    cnt, N, words = _group_arrays(h, group)
+    handle's precision (pass `precision`; float64 is assumed otherwise) and
+    the counters as a COUNTERS_DTYPE array.  Caller arrays (e.g. pinned) are
+    filled in place; False skips an array; `dims` is group_dims(h, group)."""
+    idx, N, words = dims if dims is not None else group_dims(h, group)
+    cnt = len(idx)
     dt = np.float32 if precision == CG_FP32 else np.float64
-    o = occ if isinstance(occ, np.ndarray) else (np.zeros((cnt, words), np.uint32) if occ else None)
-    e = eps if isinstance(eps, np.ndarray) else (np.zeros((cnt, N), dt) if eps else None)
-    c = (cg_counters * cnt)() if counters else None
-    _check(load().cg_read_group_state(h, group, _ptr(o, ctypes.c_uint32),
-                                      e.ctypes.data_as(ctypes.c_void_p) if e is not None else None,
-                                      c))
-    return o, e, ([x.as_dict() for x in c] if c is not None else None)
+    pick = lambda a, shape, d: a if isinstance(a, np.ndarray) else (np.zeros(shape, d) if a else None)
+    o = pick(occ, (cnt, words), np.uint32)
+    e = pick(eps, (cnt, N), dt)
+    c = pick(counters, cnt, COUNTERS_DTYPE)
+    for a, size in ((o, cnt * words), (e, cnt * N), (c, cnt)):
+        assert a is None or (a.size == size and a.flags.c_contiguous)
+    assert c is None or c.dtype == COUNTERS_DTYPE
+    _check(load().cg_read_group_state(h, group, _ptr(o, ctypes.c_uint32), _vp(e), _vp(c)))
+    return o, e, c
 
 
-def cg_write_group_state(h, group, occ=None, eps=None, counters=None):
-    cnt, N, words = _group_arrays(h, group)
-    c = None
-    if counters is not None:
-        c = (cg_counters * cnt)()
-        for k, d in enumerate(counters):
-            for f, _ in cg_counters._fields_:
-                setattr(c[k], f, d[f])
+def cg_write_group_state(h, group, occ=None, eps=None, counters=None, dims=None):
+    idx, N, words = dims if dims is not None else group_dims(h, group)
+    cnt = len(idx)
     if occ is not None:
         assert occ.dtype == np.uint32 and occ.size == cnt * words and occ.flags.c_contiguous
     if eps is not None:
         assert eps.size == cnt * N and eps.flags.c_contiguous
-    return _check(load().cg_write_group_state(
-        h, group, _ptr(occ, ctypes.c_uint32) if occ is not None else None,
-        eps.ctypes.data_as(ctypes.c_void_p) if eps is not None else None, c))
+    if counters is not None:
+        counters = np.ascontiguousarray(counters, dtype=COUNTERS_DTYPE)
+        assert counters.size == cnt
+    return _check(load().cg_write_group_state(h, group, _ptr(occ, ctypes.c_uint32), _vp(eps),
+                                              _vp(counters)))
 
 
 def cg_debug_tower(h, replica, x1):
@@ -489,9 +497,17 @@ class System:
     def observables(self, replica=0):
         return cg_observables(self.h, replica)
 
+    def group_dims(self, group):
+        if not hasattr(self, "_dims"):
+            self._dims = {}
+        if group not in self._dims:
+            self._dims[group] = group_dims(self.h, group)
+        return self._dims[group]
+
     def read_group(self, group, occ=True, eps=True, counters=True):
         return cg_read_group_state(self.h, group, occ, eps, counters,
-                                   precision=self.opts.precision)
+                                   precision=self.opts.precision, dims=self.group_dims(group))
 
     def write_group(self, group, occ=None, eps=None, counters=None):
-        return cg_write_group_state(self.h, group, occ, eps, counters)
+        return cg_write_group_state(self.h, group, occ, eps, counters,
+                                    dims=self.group_dims(group))

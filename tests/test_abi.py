@@ -61,6 +61,11 @@ def test_binding_structs_match_the_c_layout(libcg, tmp_path):
         py = structs[cname]
         want = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
         assert int(val) == want, (cname, field)
+    # the numpy record of cg_counters (batch state I/O) has the same layout
+    dt = B.COUNTERS_DTYPE
+    assert dt.itemsize == ctypes.sizeof(B.cg_counters)
+    assert [(f, dt.fields[f][1]) for f in dt.names] == \
+        [(f, getattr(B.cg_counters, f).offset) for f, _ in B.cg_counters._fields_]
 
 
 @pytest.mark.parametrize("bad,msg", [

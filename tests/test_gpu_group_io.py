@@ -56,7 +56,7 @@ def test_group_read_equals_per_replica_reads(B):
                 n, e, _, c = s.state(int(k))
                 np.testing.assert_array_equal(_unpack(occ[m], L * L), n)
                 np.testing.assert_array_equal(_bits(eps[m]), _bits(e))
-                assert cnt[m] == c
+                assert {f: cnt[m][f] for f in cnt.dtype.names} == c
         assert sorted(seen) == list(range(len(reps)))
     finally:
         s.close()
