@@ -421,6 +421,32 @@ def run_ours(args):
                     "frac": bw / per_sm, "update_time_frac": cyc / max(
                         1, cyc + o1["cycles_reject"] - o0["cycles_reject"])}
             s1.close()
+        # the binary64 form batched (one replica per SM) and one binary64
+        # replica over an 8-CTA cluster (its update spread over 8 SMs' FP64
+        # units); both bit-exact with the serial chain
+        for key, R64, csize in (("fp64_batched", sms, 0), ("fp64_cluster8", 1, 8)):
+            s1 = B.System(replicas_for(rank, R64), precision=B.CG_FP64, device=local,
+                          cluster_size=csize)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            hops = args.fp64_hops if R64 > 1 else 4 * args.fp64_hops
+            with torch.cuda.stream(s1.stream):
+                B.cg_run_async(s1.h, relax, args.M)
+                B.cg_sync(s1.h)
+                o0 = [B.cg_observables(s1.h, k) for k in range(R64)]
+                ev[0].record(s1.stream)
+                B.cg_run_async(s1.h, hops, args.M)
+                ev[1].record(s1.stream)
+                B.cg_sync(s1.h)
+            o1 = [B.cg_observables(s1.h, k) for k in range(R64)]
+            dt = ev[0].elapsed_time(ev[1]) * 1e-3
+            dh = sum(b["hops"] - a["hops"] for a, b in zip(o0, o1))
+            da = sum(b["attempts"] - a["attempts"] for a, b in zip(o0, o1))
+            sh = B.cg_group_shape(s1.h, 0)
+            result[key] = {"hops_per_s": dh / dt, "attempts_per_s": da / dt, "replicas": R64,
+                           "hops_per_replica": hops, "acceptance": dh / max(1, da),
+                           "threads": sh["threads"], "cluster": sh["cluster"],
+                           "state": f"after {relax} hops from the random start"}
+            s1.close()
         result["fp64_form"]["update_bound_dadd_per_hop"] = 2 * N
         result["fp64_form"]["dadd_peak_per_s"] = dadd_peak
         result["fp32_batched_over_fp64_form"] = result["value"] / result["fp64_form"]["hops_per_s"]
