@@ -23,6 +23,12 @@ Parity status of each oracle function (what pins it, in ``tests/``):
                         Boltzmann weights; the constant-acceptance closed
                         forms <p> = 1/[1-(1-A)^M], <m> = 1/A; the T -> infinity
                         acceptance p_theta computed by brute force.
+* stochastic time       pinned: ``log`` and ``cos2pi`` against libm,
+  (``log``, ``cos2pi``,  ``gauss`` against the standard normal law (moments,
+  ``gauss``,             tail mass, Kolmogorov-Smirnov distance, lag-1
+  ``time_increment``)    correlation), ``time_increment`` against its closed
+                        forms, a chain's time against the increments
+                        recomputed from its hop log (tests/test_oracle_time.py).
 """
 from __future__ import annotations
 
@@ -63,7 +69,8 @@ def build(force: bool = False) -> str:
 class Counters(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint64), ("hops", ctypes.c_uint64),
                 ("attempts", ctypes.c_uint64), ("evaluated", ctypes.c_uint64),
-                ("P", ctypes.c_int64), ("energy", ctypes.c_double)]
+                ("P", ctypes.c_int64), ("energy", ctypes.c_double),
+                ("time", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -138,6 +145,16 @@ def lib():
         L.orc_set_counters.restype = None
         L.orc_set_toy.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_set_toy.restype = None
+        L.orc_log.argtypes = [ctypes.c_double]
+        L.orc_log.restype = ctypes.c_double
+        L.orc_cos2pi.argtypes = [ctypes.c_double]
+        L.orc_cos2pi.restype = ctypes.c_double
+        L.orc_gauss.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64]
+        L.orc_gauss.restype = ctypes.c_double
+        L.orc_time_increment.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_double]
+        L.orc_time_increment.restype = ctypes.c_double
+        L.orc_set_time_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_time_mode.restype = None
         L.orc_tower_many.argtypes = [ctypes.c_void_p, u32p, i32p, ctypes.c_int]
         L.orc_tower_many.restype = None
         L.orc_delta_e.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -177,6 +194,26 @@ def cg_exp(x: float) -> float:
 def exp_core(x: float) -> float:
     """Cody-Waite + Taylor exp for -745 < x <= 0."""
     return lib().orc_exp_core(float(x))
+
+
+def log(x: float) -> float:
+    """Project natural logarithm (atanh series) of a normal x > 0."""
+    return lib().orc_log(float(x))
+
+
+def cos2pi(u: float) -> float:
+    """cos(2 pi u) for u in [0, 1) (exact quarter reduction + Taylor)."""
+    return lib().orc_cos2pi(float(u))
+
+
+def gauss(seed: int, replica: int, hop: int) -> float:
+    """Standard normal deviate of executed hop ``hop`` (reading R13)."""
+    return lib().orc_gauss(int(seed), int(replica), int(hop))
+
+
+def time_increment(Gamma: float, m: int, z: float) -> float:
+    """max(0, (m + sqrt(m) z) / Gamma) (reading R13)."""
+    return lib().orc_time_increment(float(Gamma), int(m), float(z))
 
 
 class Chain:
@@ -284,6 +321,10 @@ class Chain:
     def set_counters(self, d):
         c = Counters(**d)
         self._lib.orc_set_counters(self._h, ctypes.byref(c))
+
+    def set_time_mode(self, mode):
+        """0: t = attempts / Gamma (R4, default); 1: Gaussian dt per hop (R13)."""
+        self._lib.orc_set_time_mode(self._h, int(mode))
 
     def set_toy(self, A0=None):
         self._lib.orc_set_toy(self._h, 0 if A0 is None else 1,

@@ -64,6 +64,13 @@
  *   R9  dH = ((eps_j - eps_i) - 1/r_ij) - E * dx evaluated in that order.
  *   R10 Incremental energy: E_tot += dH of each executed hop; the dipole P
  *       accumulates the hop's minimum-image dx (unwrapped).
+ *   R13 Stochastic time (step 3c, optional; R4 stays the default): each
+ *       executed hop adds dt = max(0, (m + sqrt(m) z) / Gamma), m = (p-1)M + q,
+ *       z standard normal by Box-Muller from the Philox block of counter
+ *       (h lo, h hi, 0xFFFFFFFE, c), h the number of hops executed before
+ *       this one: z = sqrt(-2 ln u1) cos(2 pi u2), u1 = (x0 + 1/2) 2^-32,
+ *       u2 = x1 2^-32.  The paper's Gaussian can go negative for small m and
+ *       it is silent on that case; it is clamped at zero.
  *
  * Geometry is a general Lx x Ly torus (Ly = 1 gives a ring) so that tiny
  * systems can be enumerated exactly; the library itself only builds L x L.
@@ -144,6 +151,110 @@ double orc_cg_exp(double x)
     return orc_exp_core(x);
 }
 
+/* ---- stochastic time increment (reading R13) ---- */
+
+/* Natural logarithm of a normal x > 0: x = 2^k m with m in [sqrt(1/2),
+ * sqrt(2)); ln m = 2 atanh(f), f = (m - 1)/(m + 1) (|f| <= 0.1716), by the
+ * odd series f + f^3/3 + ... + f^23/23 (the next term is below 3e-21);
+ * ln x = k LN2_HI + (k LN2_LO + ln m).  The coefficients 1/(2n+1) are
+ * rounded to binary64. */
+double orc_log(double x)
+{
+    uint64_t b;
+    int k;
+    double m, f, s, p, lm;
+    memcpy(&b, &x, 8);
+    k = (int)((b >> 52) & 0x7ff) - 1023;
+    b = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;   /* m in [1, 2) */
+    memcpy(&m, &b, 8);
+    if (m > 0x1.6a09e667f3bcdp+0) {                            /* sqrt(2) */
+        m = m * 0.5;
+        k += 1;
+    }
+    f = (m - 1.0) / (m + 1.0);
+    s = f * f;
+    p = 0x1.642c8590b2164p-5;               /* 1/23 */
+    p = p * s + 0x1.8618618618618p-5;       /* 1/21 */
+    p = p * s + 0x1.af286bca1af28p-5;       /* 1/19 */
+    p = p * s + 0x1.e1e1e1e1e1e1ep-5;       /* 1/17 */
+    p = p * s + 0x1.1111111111111p-4;       /* 1/15 */
+    p = p * s + 0x1.3b13b13b13b14p-4;       /* 1/13 */
+    p = p * s + 0x1.745d1745d1746p-4;       /* 1/11 */
+    p = p * s + 0x1.c71c71c71c71cp-4;       /* 1/9 */
+    p = p * s + 0x1.2492492492492p-3;       /* 1/7 */
+    p = p * s + 0x1.999999999999ap-3;       /* 1/5 */
+    p = p * s + 0x1.5555555555555p-2;       /* 1/3 */
+    p = p * s + 1.0;
+    lm = (2.0 * f) * p;
+    return (double)k * ORC_LN2_HI + ((double)k * ORC_LN2_LO + lm);
+}
+
+/* cos(2 pi u) for u in [0, 1): v = u - rint(u), q = rint(4 v) and
+ * w = v - q/4 in [-1/8, 1/8] are exact; theta = 2 pi w; cos(2 pi u) is
+ * cos(theta), -sin(theta), -cos(theta) or sin(theta) for q = 0, 1, 2, 3
+ * (mod 4), from the Taylor series of cos to theta^16 and of sin to theta^17
+ * on |theta| <= pi/4 (remainders below 3e-18). */
+double orc_cos2pi(double u)
+{
+    double v = u - rint(u);
+    double q = rint(4.0 * v);
+    double w = v - 0.25 * q;
+    double t = 0x1.921fb54442d18p+2 * w;    /* 2 pi */
+    double s = t * t, p, r;
+    int qi = ((int)q) & 3;
+    if (qi == 0 || qi == 2) {
+        p = 0x1.ae7f3e733b81fp-45;              /*  1/16! */
+        p = p * s + -0x1.93974a8c07c9dp-37;     /* -1/14! */
+        p = p * s + 0x1.1eed8eff8d898p-29;      /*  1/12! */
+        p = p * s + -0x1.27e4fb7789f5cp-22;     /* -1/10! */
+        p = p * s + 0x1.a01a01a01a01ap-16;      /*  1/8! */
+        p = p * s + -0x1.6c16c16c16c17p-10;     /* -1/6! */
+        p = p * s + 0x1.5555555555555p-5;       /*  1/4! */
+        p = p * s + -0x1.0p-1;                  /* -1/2! */
+        p = p * s + 1.0;
+        r = p;
+    } else {
+        p = 0x1.952c77030ad4ap-49;              /*  1/17! */
+        p = p * s + -0x1.ae7f3e733b81fp-41;     /* -1/15! */
+        p = p * s + 0x1.6124613a86d09p-33;      /*  1/13! */
+        p = p * s + -0x1.ae64567f544e4p-26;     /* -1/11! */
+        p = p * s + 0x1.71de3a556c734p-19;      /*  1/9! */
+        p = p * s + -0x1.a01a01a01a01ap-13;     /* -1/7! */
+        p = p * s + 0x1.1111111111111p-7;       /*  1/5! */
+        p = p * s + -0x1.5555555555555p-3;      /* -1/3! */
+        p = p * s + 1.0;
+        r = t * p;
+    }
+    return (qi == 1 || qi == 2) ? -r : r;
+}
+
+/* Standard normal deviate of executed hop h of a replica (Box-Muller on the
+ * Philox block of counter (h lo, h hi, 0xFFFFFFFE, replica)). */
+double orc_gauss(uint64_t seed, uint32_t replica, uint64_t h)
+{
+    uint32_t ctr[4], key[2], x[4];
+    double u1, u2;
+    ctr[0] = (uint32_t)h;
+    ctr[1] = (uint32_t)(h >> 32);
+    ctr[2] = 0xFFFFFFFEu;
+    ctr[3] = replica;
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    orc_philox(ctr, key, x);
+    u1 = ((double)x[0] + 0.5) * 0x1p-32;
+    u2 = (double)x[1] * 0x1p-32;
+    return sqrt(-2.0 * orc_log(u1)) * orc_cos2pi(u2);
+}
+
+/* Time increment of one executed hop that took m attempts (reading R13). */
+double orc_time_increment(double Gamma, uint64_t m, double z)
+{
+    double dm = (double)m;
+    double d = dm + sqrt(dm) * z;
+    if (d < 0.0) d = 0.0;
+    return d / Gamma;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Chain state                                                               */
 /* ------------------------------------------------------------------------ */
@@ -155,6 +266,7 @@ typedef struct {
     uint64_t evaluated;   /* labels evaluated (== attempts for the serial chain) */
     int64_t P;            /* dipole moment, unwrapped (sum of hop dx) */
     double energy;        /* H_0 + sum of executed dH */
+    double time;          /* stochastic time (reading R13); 0 in the default mode */
 } orc_counters;
 
 typedef struct {
@@ -187,6 +299,7 @@ typedef struct orc_chain {
     orc_counters cnt;
     int toy;                  /* test-only constant acceptance mode */
     double toy_A0;
+    int time_mode;            /* 0: t = attempts / Gamma (R4); 1: Gaussian dt (R13) */
 } orc_chain;
 
 static int fold(int d, int L)
@@ -430,6 +543,8 @@ void orc_set_eps(orc_chain *c, const double *eps)
 void orc_get_counters(const orc_chain *c, orc_counters *out) { *out = c->cnt; }
 void orc_set_counters(orc_chain *c, const orc_counters *in) { c->cnt = *in; }
 
+void orc_set_time_mode(orc_chain *c, int mode) { c->time_mode = mode; }
+
 void orc_set_toy(orc_chain *c, int on, double A0)
 {
     c->toy = on;
@@ -562,6 +677,12 @@ int orc_run(orc_chain *c, uint64_t n_hops, uint32_t M, uint64_t max_rounds,
                     e->i = lab.i; e->j = lab.j; e->q = q; e->p = p;
                     e->round = c->cnt.rounds;
                     e->dx = lab.dx; e->dy = lab.dy; e->dE = lab.dE;
+                }
+                if (c->time_mode) {
+                    uint64_t m = (uint64_t)(p - 1) * M + q;
+                    double z = orc_gauss(c->seed, c->replica, c->cnt.hops);
+                    c->cnt.time = c->cnt.time +
+                                  orc_time_increment((double)c->N * c->Z, m, z);
                 }
                 c->cnt.attempts += q;
                 c->cnt.rounds += 1;

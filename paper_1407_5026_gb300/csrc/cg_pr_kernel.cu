@@ -284,7 +284,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             const Real *ci0 = tinv + fxi, *ci1 = tinv + (Lh - fxi);
             const int LhH1 = Lh * H1, LhL = Lh * L;
             Real *e = eps + by0 * L + bx;
-#pragma unroll 2
+#pragma unroll 4
             for (int y = by0; y < Lh; y += rpp, e += rpp * L) {
                 int fyj, fyi;
                 if (kPow2) {
