@@ -48,6 +48,10 @@ extern "C" {
 #define CG_FP64 0        /* eps in binary64: bit-exact with the serial chain  */
 #define CG_FP32 1        /* eps in binary32 with a periodic binary64 refresh  */
 
+/* cg_opts.time_mode */
+#define CG_TIME_DETERMINISTIC 0
+#define CG_TIME_GAUSSIAN 1
+
 #define CG_REFRESH_AUTO 0
 #define CG_REFRESH_FP64 1  /* direct G (n - nu) in binary64                   */
 #define CG_REFRESH_BF16X2 2 /* split-BF16 hi+lo tensor-core contraction over
@@ -94,6 +98,11 @@ typedef struct {
                                    smallest of 2, 4, 8 that fits); 2, 4 or 8
                                    force a thread-block cluster that splits
                                    eps by rows                                 */
+    int32_t time_mode;          /* CG_TIME_DETERMINISTIC (0): t = attempts/Gamma;
+                                   CG_TIME_GAUSSIAN: each executed hop adds a
+                                   Gaussian dt of mean m/Gamma and standard
+                                   deviation sqrt(m)/Gamma, m = (p-1)M + q
+                                   (mixed PR algorithm, step 3c), clamped at 0 */
 } cg_opts;
 
 /* Counters of one replica (step 3 of the mixed PR algorithm). */
@@ -104,12 +113,15 @@ typedef struct {
     uint64_t evaluated;  /* labels actually evaluated on the GPU                  */
     int64_t P;           /* dipole moment sum_i n_i x_i, unwrapped by hop dx      */
     double energy;       /* H of Eq. 1 (field term with the unwrapped P)          */
+    double time;         /* CG_TIME_GAUSSIAN: the accumulated stochastic time;
+                            CG_TIME_DETERMINISTIC: 0 (time is attempts/Gamma)     */
 } cg_counters;
 
 /* Observables of one replica. */
 typedef struct {
     cg_counters c;
-    double time;              /* attempts / Gamma (deterministic time rule)   */
+    double time;              /* attempts / Gamma, or the stochastic time of
+                                 CG_TIME_GAUSSIAN                             */
     double Gamma;             /* N * sum_d exp(-2|d|/xi) over the hop disk     */
     double acceptance;        /* hops / attempts                              */
     double energy_per_site;   /* energy / N                                   */
@@ -122,10 +134,11 @@ typedef struct {
 
 /* One point of the log-spaced trace (cg_set_trace). */
 typedef struct {
-    uint64_t attempts;   /* serial-equivalent attempts when recorded (time = attempts/Gamma) */
+    uint64_t attempts;   /* serial-equivalent attempts when recorded                       */
     uint64_t hops;
     int64_t P;           /* dipole moment (unwrapped)                                      */
     double energy;
+    double time;         /* attempts/Gamma, or the stochastic time of CG_TIME_GAUSSIAN     */
 } cg_trace_point;
 
 /* One executed hop (diagnostics; see cg_run_logged). */
@@ -329,6 +342,13 @@ int cg_set_toy_acceptance(cg_handle *h, double A0);
 int cg_debug_philox(const uint32_t *ctr_host, const uint32_t *key_host,
                     uint32_t *out_host, int n);
 int cg_debug_exp(const double *x_host, double *out_host, int n);
+
+/* Test-only: the standard normal deviate of executed hop hops_host[k] of
+ * replica replica_host[k] under seed seed_host[k] (Box-Muller on the Philox
+ * block of counter (hop lo, hop hi, 0xFFFFFFFE, replica), as the kernels draw
+ * it for CG_TIME_GAUSSIAN), on the GPU for n inputs (host arrays). */
+int cg_debug_gauss(const uint64_t *seed_host, const uint32_t *replica_host,
+                   const uint64_t *hops_host, double *z_host, int n);
 
 /* Test-only: the PR kernels' tower sampler (guide table + thresholds of
  * replica `replica`, section "Hopping conduction in the Coulomb glass": hop

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcg.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_ESTUCK, CG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 CG_FP64, CG_FP32 = 0, 1
+CG_TIME_DETERMINISTIC, CG_TIME_GAUSSIAN = 0, 1
 CG_REFRESH_AUTO, CG_REFRESH_FP64, CG_REFRESH_BF16X2 = 0, 1, 2
 
 EXPORTED = [
@@ -30,7 +31,7 @@ EXPORTED = [
     "cg_run_async", "cg_sync", "cg_run_logged", "cg_read_state", "cg_write_state",
     "cg_observables", "cg_refresh", "cg_refresh_async", "cg_microbench",
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_debug_tower", "cg_version",
-    "cg_group_replicas", "cg_read_group_state", "cg_write_group_state",
+    "cg_group_replicas", "cg_read_group_state", "cg_write_group_state", "cg_debug_gauss",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
     "cg_set_trace", "cg_read_trace",
 ]
@@ -55,13 +56,14 @@ class cg_opts(ctypes.Structure):
                 ("refresh_every", ctypes.c_uint32), ("block_threads", ctypes.c_int32),
                 ("max_rounds_per_hop", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("hop_timeout_ms", ctypes.c_uint32), ("cluster_size", ctypes.c_int32)]
+                ("hop_timeout_ms", ctypes.c_uint32), ("cluster_size", ctypes.c_int32),
+                ("time_mode", ctypes.c_int32)]
 
 
 class cg_counters(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint64), ("hops", ctypes.c_uint64),
                 ("attempts", ctypes.c_uint64), ("evaluated", ctypes.c_uint64),
-                ("P", ctypes.c_int64), ("energy", ctypes.c_double)]
+                ("P", ctypes.c_int64), ("energy", ctypes.c_double), ("time", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -75,8 +77,10 @@ class cg_obs(ctypes.Structure):
                 ("cycles_update", ctypes.c_uint64)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "c"}
-        d.update(self.c.as_dict())
+        # the counters first, then the observables: "time" is the observable
+        # (attempts / Gamma, or the stochastic clock)
+        d = self.c.as_dict()
+        d.update({f: getattr(self, f) for f, _ in self._fields_ if f != "c"})
         return d
 
 
@@ -92,13 +96,15 @@ HOP_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("q", "<u4"), ("p", "<u4"),
 
 class cg_trace_point(ctypes.Structure):
     _fields_ = [("attempts", ctypes.c_uint64), ("hops", ctypes.c_uint64),
-                ("P", ctypes.c_int64), ("energy", ctypes.c_double)]
+                ("P", ctypes.c_int64), ("energy", ctypes.c_double), ("time", ctypes.c_double)]
 
 
-TRACE_DTYPE = np.dtype([("attempts", "<u8"), ("hops", "<u8"), ("P", "<i8"), ("energy", "<f8")])
+TRACE_DTYPE = np.dtype([("attempts", "<u8"), ("hops", "<u8"), ("P", "<i8"), ("energy", "<f8"),
+                        ("time", "<f8")])
 # layout of cg_counters, for arrays of counter records
 COUNTERS_DTYPE = np.dtype([("rounds", "<u8"), ("hops", "<u8"), ("attempts", "<u8"),
-                           ("evaluated", "<u8"), ("P", "<i8"), ("energy", "<f8")])
+                           ("evaluated", "<u8"), ("P", "<i8"), ("energy", "<f8"),
+                           ("time", "<f8")])
 
 _lib = None
 _lock = threading.Lock()
@@ -141,6 +147,8 @@ def load(path: str | None = None):
             "cg_debug_philox": (ctypes.c_int, [u32p, u32p, u32p, ctypes.c_int]),
             "cg_debug_exp": (ctypes.c_int, [dp, dp, ctypes.c_int]),
             "cg_group_replicas": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int)]),
+            "cg_debug_gauss": (ctypes.c_int, [P(ctypes.c_uint64), u32p, P(ctypes.c_uint64), dp,
+                                              ctypes.c_int]),
             "cg_read_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, vp]),
             "cg_write_group_state": (ctypes.c_int, [vp, ctypes.c_int, u32p, vp, vp]),
             "cg_debug_tower": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u32p,
@@ -180,11 +188,12 @@ def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0):
 
 def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,
          max_rounds_per_hop=0, device=0, use_graph=0, stream=None, hop_timeout_ms=0,
-         cluster_size=0):
+         cluster_size=0, time_mode=CG_TIME_DETERMINISTIC):
     return cg_opts(precision=precision, refresh_kind=refresh_kind, refresh_every=refresh_every,
                    block_threads=block_threads, max_rounds_per_hop=max_rounds_per_hop,
                    device=device, use_graph=use_graph, stream=stream,
-                   hop_timeout_ms=hop_timeout_ms, cluster_size=cluster_size)
+                   hop_timeout_ms=hop_timeout_ms, cluster_size=cluster_size,
+                   time_mode=time_mode)
 
 
 # ---- the C entry points, one to one ----
@@ -291,7 +300,8 @@ def cg_write_state(h, replica, n, eps=None, phi=None, counters=None):
     n = np.ascontiguousarray(n, dtype=np.uint8)
     eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
     phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
-    c = None if counters is None else cg_counters(**counters)
+    c = None if counters is None else cg_counters(
+        **{f: counters.get(f, 0) for f, _ in cg_counters._fields_})
     return _check(load().cg_write_state(h, replica, _ptr(n, ctypes.c_uint8),
                                         _ptr(eps, ctypes.c_double), _ptr(phi, ctypes.c_double),
                                         ctypes.byref(c) if c is not None else None))
@@ -337,10 +347,11 @@ def cg_read_trace(h, replica=0, capacity=256):
     return out[:n]
 
 
-def sigma_windows(trace, N, E, Gamma):
+def sigma_windows(trace, N, E, Gamma=None):
     """Conductivity of Eq. 3, sigma = (1 / N E) dP/dt, over the windows between
-    consecutive trace points (t = attempts / Gamma); returns (t_mid, sigma)."""
-    t = trace["attempts"].astype(np.float64) / Gamma
+    consecutive trace points, on the time each point recorded (attempts /
+    Gamma, or the stochastic time of CG_TIME_GAUSSIAN); returns (t_mid, sigma)."""
+    t = trace["time"].astype(np.float64)
     P = trace["P"].astype(np.float64)
     dt = np.diff(t)
     keep = dt > 0
@@ -374,6 +385,16 @@ def cg_debug_philox(ctr, key):
     out = np.zeros_like(ctr)
     _check(load().cg_debug_philox(_ptr(ctr, ctypes.c_uint32), _ptr(key, ctypes.c_uint32),
                                   _ptr(out, ctypes.c_uint32), len(ctr)))
+    return out
+
+
+def cg_debug_gauss(seed, replica, hops):
+    seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    replica = np.ascontiguousarray(replica, dtype=np.uint32)
+    hops = np.ascontiguousarray(hops, dtype=np.uint64)
+    out = np.zeros(len(hops), np.float64)
+    _check(load().cg_debug_gauss(_ptr(seed, ctypes.c_uint64), _ptr(replica, ctypes.c_uint32),
+                                 _ptr(hops, ctypes.c_uint64), _ptr(out, ctypes.c_double), len(hops)))
     return out
 
 
@@ -451,7 +472,7 @@ class System:
 
     def __init__(self, reps, precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO,
                  block_threads=0, max_rounds_per_hop=0, device=0, torch_memory=True,
-                 hop_timeout_ms=0, cluster_size=0, use_graph=0):
+                 hop_timeout_ms=0, cluster_size=0, use_graph=0, time_mode=0):
         import torch
         self.reps = [r if isinstance(r, dict) else r for r in reps]
         torch.cuda.set_device(device)
@@ -462,7 +483,7 @@ class System:
                          refresh_kind=refresh_kind, block_threads=block_threads,
                          max_rounds_per_hop=max_rounds_per_hop, device=device,
                          stream=self.stream.cuda_stream, hop_timeout_ms=hop_timeout_ms,
-                         cluster_size=cluster_size, use_graph=use_graph)
+                         cluster_size=cluster_size, use_graph=use_graph, time_mode=time_mode)
         self.workspace = None
         if torch_memory:
             nbytes = cg_workspace_bytes(self.reps, self.opts)

@@ -169,6 +169,21 @@ cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr,
     return cudaGetLastError();
 }
 
+__global__ void debug_gauss_kernel(const uint64_t *seed, const uint32_t *rep, const uint64_t *hop,
+                                   double *z, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n)
+        z[t] = cg_gauss((uint32_t)seed[t], (uint32_t)(seed[t] >> 32), rep[t], hop[t]);
+}
+
+cudaError_t launch_debug_gauss(const uint64_t *seed, const uint32_t *rep, const uint64_t *hop,
+                               double *z, int n, cudaStream_t st)
+{
+    debug_gauss_kernel<<<(n + 127) / 128, 128, 0, st>>>(seed, rep, hop, z, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
                                 cudaStream_t st)
 {

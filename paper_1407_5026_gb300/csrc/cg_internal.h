@@ -30,6 +30,7 @@ struct alignas(16) DevCounters {
     int trace_cap;                     // trace capacity (0: no trace)
     double trace_next;                 // attempt count of the next trace point
     double trace_ratio;                // ratio between consecutive trace points
+    double time;                       // stochastic time (CG_TIME_GAUSSIAN), else 0
 };
 
 // Guide table of the tower: bucket b = x1 >> (32 - kGuideBits) holds the
@@ -51,6 +52,7 @@ struct alignas(16) DevReplica {
     double nu, T, E;
     double negC0nu;           // -nu * sum_{t != s} 1/r_st (same for every s)
     double C0;                // sum_{t != s} 1/r_st
+    double Gamma;             // N * Z, the total proposal rate
     // tables (device)
     const double *tinv64;     // H1*H1, [fy*H1 + fx] = 1/sqrt(fx^2+fy^2), 0 at origin
     const float *tinv32;      // the same rounded to binary32
@@ -70,7 +72,8 @@ struct alignas(16) DevReplica {
 // Thread 0 at commit: record trace points whose attempt threshold the
 // replica's attempt count has reached (several if one hop spans them).
 __device__ __forceinline__ void trace_hop(const DevReplica &Rg, unsigned long long attempts,
-                                          unsigned long long hops, long long P, double energy)
+                                          unsigned long long hops, long long P, double energy,
+                                          int time_mode, double time)
 {
     DevCounters *c = Rg.ctr;
     if (!Rg.trace || c->trace_count >= c->trace_cap || (double)attempts < c->trace_next) return;
@@ -79,6 +82,7 @@ __device__ __forceinline__ void trace_hop(const DevReplica &Rg, unsigned long lo
     pt.hops = hops;
     pt.P = P;
     pt.energy = energy;
+    pt.time = time_mode ? time : __ddiv_rn((double)attempts, Rg.Gamma);
     Rg.trace[c->trace_count++] = pt;
     double next = c->trace_next;
     while (next <= (double)attempts) next = next * c->trace_ratio > next + 1.0 ? next * c->trace_ratio : next + 1.0;
@@ -93,6 +97,7 @@ struct RunArgs {
     unsigned long long hop_timeout_cyc; // the same in SM cycles at the peak clock
     unsigned int M;                // labels per round
     int toy;                       // constant-acceptance test mode
+    int time_mode;                 // CG_TIME_DETERMINISTIC or CG_TIME_GAUSSIAN
     double toy_A0;
 };
 
@@ -139,6 +144,8 @@ cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int word
 cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key,
                                 uint32_t *out, int n, cudaStream_t st);
 cudaError_t launch_debug_exp(const double *x, double *out, int n, cudaStream_t st);
+cudaError_t launch_debug_gauss(const uint64_t *seed, const uint32_t *rep, const uint64_t *hop,
+                               double *z, int n, cudaStream_t st);
 cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr, int V,
                                const uint32_t *x1, int *out, int n, cudaStream_t st);
 cudaError_t set_pr_smem_limit(int precision, int bytes);

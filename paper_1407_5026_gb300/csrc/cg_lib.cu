@@ -330,6 +330,7 @@ void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
     dr.replica = r.d.replica;
     dr.nu = r.d.nu; dr.T = r.d.T; dr.E = r.d.E;
     dr.negC0nu = -r.d.nu * t.C0;
+    dr.Gamma = (double)r.N * t.Z;
     dr.tinv64 = t.d_t64; dr.tinv32 = t.d_t32; dr.thr = t.d_thr; dr.disp = t.d_disp;
     dr.tinvd = t.d_tinvd;
     dr.guide = t.d_guide;
@@ -435,6 +436,7 @@ int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
     if (c) {
         dc.rounds = c->rounds; dc.hops = c->hops; dc.attempts = c->attempts;
         dc.evaluated = c->evaluated; dc.P = c->P; dc.energy = c->energy;
+        dc.time = c->time;
     } else {
         std::vector<double> e(r.N), ph(r.N);
         int rc = read_eps_host(h, r, e.data());
@@ -504,6 +506,10 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     if (o.block_threads && (o.block_threads != 256 && o.block_threads != 384 &&
                             o.block_threads != 512 && o.block_threads != 1024)) {
         fail(CG_EINVAL, "block_threads must be 0, 256, 384, 512 or 1024");
+        return nullptr;
+    }
+    if (o.time_mode != CG_TIME_DETERMINISTIC && o.time_mode != CG_TIME_GAUSSIAN) {
+        fail(CG_EINVAL, "time_mode must be CG_TIME_DETERMINISTIC or CG_TIME_GAUSSIAN");
         return nullptr;
     }
     if (o.max_rounds_per_hop == 0) o.max_rounds_per_hop = 1ull << 32;
@@ -747,6 +753,7 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
                         (unsigned long long)h->clock_khz;
     a.toy = h->toy;
     a.toy_A0 = h->toy_A0;
+    a.time_mode = h->opts.time_mode;
     if (g.cluster > 1)
         CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
                                   g.cluster, g.threads, g.smem, a, st, g.L));
@@ -995,6 +1002,7 @@ int cg_read_state(cg_handle *h, int replica, uint8_t *n_host, double *eps_host,
         CG_CUDA(cudaStreamSynchronize(h->st));
         c_host->rounds = dc.rounds; c_host->hops = dc.hops; c_host->attempts = dc.attempts;
         c_host->evaluated = dc.evaluated; c_host->P = dc.P; c_host->energy = dc.energy;
+        c_host->time = dc.time;
     }
     return CG_OK;
 }
@@ -1054,6 +1062,7 @@ int cg_read_group_state(cg_handle *h, int group, uint32_t *occ_words_host, void 
         c_host[k].rounds = dc[k].rounds; c_host[k].hops = dc[k].hops;
         c_host[k].attempts = dc[k].attempts; c_host[k].evaluated = dc[k].evaluated;
         c_host[k].P = dc[k].P; c_host[k].energy = dc[k].energy;
+        c_host[k].time = dc[k].time;
     }
     return CG_OK;
 }
@@ -1098,6 +1107,7 @@ int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host
             dc[k].rounds = c_host[k].rounds; dc[k].hops = c_host[k].hops;
             dc[k].attempts = c_host[k].attempts; dc[k].evaluated = c_host[k].evaluated;
             dc[k].P = c_host[k].P; dc[k].energy = c_host[k].energy;
+            dc[k].time = c_host[k].time;
         }
         CG_CUDA(cudaMemcpyAsync(r0.d_ctr, dc.data(), cnt * sizeof(DevCounters),
                                 cudaMemcpyHostToDevice, h->st));
@@ -1120,8 +1130,10 @@ int cg_observables(cg_handle *h, int replica, cg_obs *out)
     std::memset(out, 0, sizeof(*out));
     out->c.rounds = dc.rounds; out->c.hops = dc.hops; out->c.attempts = dc.attempts;
     out->c.evaluated = dc.evaluated; out->c.P = dc.P; out->c.energy = dc.energy;
+    out->c.time = dc.time;
     out->Gamma = (double)r.N * r.tab->Z;
-    out->time = (double)dc.attempts / out->Gamma;
+    out->time = h->opts.time_mode == CG_TIME_GAUSSIAN ? dc.time
+                                                      : (double)dc.attempts / out->Gamma;
     out->acceptance = dc.attempts ? (double)dc.hops / (double)dc.attempts : 0.0;
     out->energy_per_site = dc.energy / (double)r.N;
     std::memcpy(&out->max_eps_err_last_refresh, &dc.max_err_bits, 8);
@@ -1425,6 +1437,26 @@ int cg_debug_exp(const double *x_host, double *out_host, int n)
     cudaMemcpy(d, x_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
     cudaError_t e = launch_debug_exp(d, d + n, n, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out_host, d + n, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
+    return CG_OK;
+}
+
+int cg_debug_gauss(const uint64_t *seed_host, const uint32_t *replica_host,
+                   const uint64_t *hops_host, double *z_host, int n)
+{
+    if (n <= 0 || !seed_host || !replica_host || !hops_host || !z_host)
+        return fail(CG_EINVAL, "bad arguments");
+    char *d = nullptr;
+    CG_CUDA(cudaMalloc((void **)&d, 28 * (size_t)n));
+    uint64_t *ds = (uint64_t *)d, *dh = (uint64_t *)(d + 8 * (size_t)n);
+    double *dz = (double *)(d + 16 * (size_t)n);
+    uint32_t *dr = (uint32_t *)(d + 24 * (size_t)n);
+    cudaError_t e = cudaMemcpy(ds, seed_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dh, hops_host, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dr, replica_host, 4 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_gauss(ds, dr, dh, dz, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(z_host, dz, 8 * (size_t)n, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return fail(CG_ECUDA, cudaGetErrorString(e));
     return CG_OK;

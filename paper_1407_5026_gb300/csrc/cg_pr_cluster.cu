@@ -58,7 +58,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     __shared__ struct {
         unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd, wall0;
         long long P, t0;
-        double energy;
+        double energy, time;
         float m_ema;
     } s_c;
 
@@ -118,6 +118,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         s_c.evaluated = cnt->evaluated;
         s_c.P = cnt->P;
         s_c.energy = cnt->energy;
+        s_c.time = cnt->time;
         s_c.m_ema = cnt->m_ema > 0.f ? cnt->m_ema : 64.0f;
         s_c.cyc_rej = 0;
         s_c.cyc_upd = 0;
@@ -263,6 +264,9 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
+            if (a.time_mode)     // step 3c: Gaussian dt of hop number s_c.hops
+                s_c.time = d_add(s_c.time, cg_time_increment(Rg.Gamma, m_hop,
+                                                            cg_gauss(key0, key1, rep, s_c.hops)));
             s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
             s_c.attempts += q;
             s_c.hops += 1;
@@ -270,7 +274,8 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 s_c.P += cdx;
                 s_c.energy = d_add(s_c.energy, win.dE);
             }
-            if (rank == 0) trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy);
+            if (rank == 0)
+                trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy, a.time_mode, s_c.time);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
             if (rank == 0 && Rg.log) {
@@ -325,6 +330,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         cnt->evaluated = s_c.evaluated;
         cnt->P = s_c.P;
         cnt->energy = s_c.energy;
+        cnt->time = s_c.time;
         cnt->cycles_reject += s_c.cyc_rej;
         cnt->cycles_update += s_c.cyc_upd;
         cnt->m_ema = s_c.m_ema;

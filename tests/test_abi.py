@@ -82,6 +82,16 @@ def test_create_rejects_bad_parameters_on_host(libcg, bad, msg):
     assert msg in str(ei.value)
 
 
+@pytest.mark.parametrize("bad,msg", [(dict(time_mode=2), "time_mode"),
+                                     (dict(block_threads=300), "block_threads"),
+                                     (dict(precision=7), "precision")])
+def test_create_batch_rejects_bad_options_on_host(libcg, bad, msg):
+    from paper_1407_5026_gb300 import binding as B
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create_batch([B.desc(L=16)], B.opts(**bad))
+    assert msg in str(ei.value)
+
+
 def test_workspace_plan_counts_every_buffer(libcg):
     from paper_1407_5026_gb300 import binding as B
     reps = [B.desc(L=16), B.desc(L=16, seed=1), B.desc(L=32, r_max=6)]
