@@ -676,7 +676,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         destroy_partial();
         return nullptr;
     }
-    if (set_pr_smem_limit(o.precision, optin - 1024) != cudaSuccess) {
+    if (set_pr_smem_limit(o.precision, optin - 2048) != cudaSuccess) {
         fail(CG_ECUDA, "cudaFuncSetAttribute(max dynamic shared memory) failed");
         destroy_partial();
         return nullptr;

@@ -54,6 +54,11 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
+    // step-3c deviates of the next hops (CG_TIME_GAUSSIAN): warp 0 draws 32
+    // at a time, one per lane, so the binary64 Box-Muller chain runs once
+    // per 32 hops instead of on thread 0's path at every commit
+    __shared__ double s_z[32];
+    __shared__ unsigned long long s_zbase;
     __shared__ Slot s_slot[2][8];
     __shared__ struct {
         unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd, wall0;
@@ -133,7 +138,19 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int active = rows_per_pass * L;
     const int ux = tid % L, uy0 = tid / L;
 
+    if (tid == 0) s_zbase = ~0ull;
+    __syncthreads();
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
+        if (a.time_mode && warp == 0) {
+            // s_c.hops was last written before the previous hop's final barrier
+            const unsigned long long hcur = s_c.hops;
+            if (hcur < s_zbase || hcur - s_zbase >= 32ull) {
+                s_z[lane] = cg_gauss(key0, key1, rep, hcur + (unsigned long long)lane);
+                __syncwarp();
+                if (lane == 0) s_zbase = hcur;
+                __syncwarp();
+            }
+        }
         if (tid == 0) {
             s_c.t0 = clock64();
             s_c.wall0 = globaltimer_ns();
@@ -266,7 +283,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
             if (a.time_mode)     // step 3c: Gaussian dt of hop number s_c.hops
                 s_c.time = d_add(s_c.time, cg_time_increment(Rg.Gamma, m_hop,
-                                                            cg_gauss(key0, key1, rep, s_c.hops)));
+                                                            s_z[s_c.hops - s_zbase]));
             s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
             s_c.attempts += q;
             s_c.hops += 1;

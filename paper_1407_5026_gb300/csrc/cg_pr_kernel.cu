@@ -43,7 +43,9 @@ namespace cg {
 // kLog2L > 0: L = 2^kLog2L fixed at compile time (the lattice constants
 // fold into immediates and free registers for the labels); kLog2L = 0: L a
 // power of two known at run time; kLog2L < 0: any even L.
-template <typename Real, int kThreads, int kLog2L>
+// kTime: CG_TIME_GAUSSIAN runs (the step-3c deviates are drawn in the
+// kernel); the default deterministic clock compiles without that code.
+template <typename Real, int kThreads, int kLog2L, bool kTime>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
@@ -51,6 +53,11 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
+    // step-3c deviates of the next hops (CG_TIME_GAUSSIAN): warp 0 draws 32
+    // at a time, one per lane, so the binary64 Box-Muller chain runs once
+    // per 32 hops instead of on thread 0's path at every commit
+    __shared__ double s_z[32];
+    __shared__ unsigned long long s_zbase;
     // counters and pointers only thread 0 uses (registers stay free for the
     // labels)
     __shared__ struct {
@@ -129,7 +136,21 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     const unsigned M = a.M;
     const unsigned thr_last = S.thr[V - 1];
 
+    if (kTime) {
+        if (tid == 0) s_zbase = ~0ull;
+        __syncthreads();
+    }
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
+        if (kTime && warp == 0) {
+            // s_c.hops was last written before the previous hop's final barrier
+            const unsigned long long hcur = s_c.hops;
+            if (hcur < s_zbase || hcur - s_zbase >= 32ull) {
+                s_z[lane] = cg_gauss(key0, key1, rep, hcur + (unsigned long long)lane);
+                __syncwarp();
+                if (lane == 0) s_zbase = hcur;
+                __syncwarp();
+            }
+        }
         if (tid == 0) s_c.t0 = clock64();
         // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
         // worth b ~ 64 labels: two per thread (C = 2 blockDim) when that
@@ -244,9 +265,9 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
-            if (a.time_mode)     // step 3c: Gaussian dt of hop number s_c.hops
+            if (kTime)           // step 3c: Gaussian dt of hop number s_c.hops
                 s_c.time = d_add(s_c.time, cg_time_increment(Rg.Gamma, m_hop,
-                                                            cg_gauss(key0, key1, rep, s_c.hops)));
+                                                            s_z[s_c.hops - s_zbase]));
             s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
             s_c.attempts += q;
             // the chunks of the hop's round up to the accepting one
@@ -257,7 +278,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 s_c.energy = d_add(s_c.energy, c.dE);
             }
             if (s_c.tracing)
-                trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy, a.time_mode, s_c.time);
+                trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy, kTime ? 1 : 0, s_c.time);
             t1 = clock64();
             s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
             if (s_c.log) {
@@ -339,41 +360,62 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     }
 }
 
+template <typename Real, int kThreads, bool kTime>
+static void launch_tt(const DevReplica *d_reps, const int *d_index, int n_ctas, int smem_bytes,
+                      const RunArgs &args, cudaStream_t st, int L)
+{
+    switch (L) {
+    case 64:
+        pr_persistent<Real, kThreads, 6, kTime>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    case 128:
+        pr_persistent<Real, kThreads, 7, kTime>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    default:
+        if ((L & (L - 1)) == 0)
+            pr_persistent<Real, kThreads, 0, kTime>
+                <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        else
+            pr_persistent<Real, kThreads, -1, kTime>
+                <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+    }
+}
+
 template <typename Real, int kThreads>
 static cudaError_t launch_t(const DevReplica *d_reps, const int *d_index, int n_ctas,
                             int smem_bytes, const RunArgs &args, cudaStream_t st, int L)
 {
-    switch (L) {
-    case 64:
-        pr_persistent<Real, kThreads, 6><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
-        break;
-    case 128:
-        pr_persistent<Real, kThreads, 7><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
-        break;
-    default:
-        if ((L & (L - 1)) == 0)
-            pr_persistent<Real, kThreads, 0><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
-        else
-            pr_persistent<Real, kThreads, -1><<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
-    }
+    if (args.time_mode)
+        launch_tt<Real, kThreads, true>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
+    else
+        launch_tt<Real, kThreads, false>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);
     return cudaGetLastError();
+}
+
+template <typename Real, int kThreads, bool kTime>
+static cudaError_t set_smem_tt(int bytes)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 6, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 7, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 0, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
+    return cudaFuncSetAttribute(pr_persistent<Real, kThreads, -1, kTime>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <typename Real, int kThreads>
 static cudaError_t set_smem_one(int bytes)
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 6>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 7>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 0>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    return cudaFuncSetAttribute(pr_persistent<Real, kThreads, -1>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = set_smem_tt<Real, kThreads, false>(bytes);
+    return e ? e : set_smem_tt<Real, kThreads, true>(bytes);
 }
 
 template <typename Real>
