@@ -362,7 +362,18 @@ def run_ours(args):
                      "kernel": "pr_persistent<float>",
                      "bytes_per_hop": bytes_per_hop,
                      "peak_source": "measured: shared-memory 32-bit read-modify-write "
-                                    "microbenchmark over all SMs (cg_microbench kind 0)"},
+                                    "microbenchmark over all SMs (cg_microbench kind 0)",
+                     # the eps-update phase alone (the bandwidth-bound step):
+                     # algorithmic bytes over each CTA's update-phase clock
+                     # cycles (clock64 of thread 0) against one SM's share of
+                     # the measured peak; the one-replica figure is filled in
+                     # below (fp32_single.update_phase.frac)
+                     "update_phase_frac_batched": (
+                         (hops * bytes_per_hop / (cyc_upd / (clk["sm_mhz"] * 1e6)))
+                         / (smem_peak / sms) if clk and cyc_upd else None),
+                     "update_phase_frac_one_replica": None,
+                     "end_to_end_note": "frac covers the whole kernel, whose time is "
+                                        "mostly the rejection phase at T=0.01"},
         # the refresh as a whole (error reset, S image, contraction,
         # reduction) against the measured sustained BF16 tensor peak: the
         # contraction is 2 (hi, lo) x 2 N^2 flop per replica
@@ -420,6 +431,7 @@ def run_ours(args):
                     "achieved_GBps": bw / 1e9, "peak_per_sm_GBps": per_sm / 1e9,
                     "frac": bw / per_sm, "update_time_frac": cyc / max(
                         1, cyc + o1["cycles_reject"] - o0["cycles_reject"])}
+                result["roofline"]["update_phase_frac_one_replica"] = bw / per_sm
             s1.close()
         # the binary64 form batched (one replica per SM) and one binary64
         # replica over an 8-CTA cluster (its update spread over 8 SMs' FP64

@@ -23,6 +23,12 @@ Parity status of each oracle function (what pins it, in ``tests/``):
                         Boltzmann weights; the constant-acceptance closed
                         forms <p> = 1/[1-(1-A)^M], <m> = 1/A; the T -> infinity
                         acceptance p_theta computed by brute force.
+* cubic lattice         pinned: the hop ball against a brute-force count and
+  (``Chain(L, dim=3)``)  order, the 1/r table against closed forms, eps and
+                        dH against numpy evaluations of Eq. 1 on the 3D
+                        torus, incremental eps against scratch, detailed
+                        balance over every state of two electrons on a 4^3
+                        torus (tests/test_oracle_3d.py).
 * stochastic time       pinned: ``log`` and ``cos2pi`` against libm,
   (``log``, ``cos2pi``,  ``gauss`` against the standard normal law (moments,
   ``gauss``,             tail mass, Kolmogorov-Smirnov distance, lag-1
@@ -92,7 +98,7 @@ assert HOP_DTYPE.itemsize == ctypes.sizeof(Hop)
 class Label(ctypes.Structure):
     _fields_ = [("accepted", ctypes.c_int32), ("vec", ctypes.c_int32),
                 ("i", ctypes.c_uint32), ("j", ctypes.c_uint32),
-                ("dx", ctypes.c_int32), ("dy", ctypes.c_int32),
+                ("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
                 ("theta", ctypes.c_int32), ("dE", ctypes.c_double),
                 ("u", ctypes.c_double), ("x", ctypes.c_uint32 * 4)]
 
@@ -118,6 +124,15 @@ def lib():
                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
                               ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                               ctypes.c_uint32]
+        L.orc_new3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                               ctypes.c_uint32]
+        L.orc_new3.restype = ctypes.c_void_p
+        L.orc_get_vectors_z.argtypes = [ctypes.c_void_p, i32p]
+        L.orc_get_vectors_z.restype = None
+        L.orc_tinv_of3.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_tinv_of3.restype = ctypes.c_double
         L.orc_new.restype = ctypes.c_void_p
         L.orc_free.argtypes = [ctypes.c_void_p]
         L.orc_free.restype = None
@@ -220,16 +235,19 @@ class Chain:
     """One replica of the serial mixed-rejection chain on an Lx x Ly torus."""
 
     def __init__(self, Lx, Ly=None, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05,
-                 E=0.0, seed=0, replica=0):
+                 E=0.0, seed=0, replica=0, Lz=1, dim=None):
+        """Lx x Ly x Lz torus; dim=3 makes the cubic lattice Lx = Ly = Lz."""
         Ly = Lx if Ly is None else Ly
+        if dim == 3:
+            Ly = Lz = Lx
         self._lib = lib()
-        self._h = self._lib.orc_new(int(Lx), int(Ly), float(nu), float(W),
-                                    float(xi), int(r_max), float(T), float(E),
-                                    int(seed), int(replica))
+        self._h = self._lib.orc_new3(int(Lx), int(Ly), int(Lz), float(nu), float(W),
+                                     float(xi), int(r_max), float(T), float(E),
+                                     int(seed), int(replica))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
-        self.Lx, self.Ly = int(Lx), int(Ly)
-        self.N = self.Lx * self.Ly
+        self.Lx, self.Ly, self.Lz = int(Lx), int(Ly), int(Lz)
+        self.N = self.Lx * self.Ly * self.Lz
         self.nu, self.W, self.xi, self.r_max = nu, W, xi, r_max
         self.T, self.E, self.seed, self.replica = T, E, seed, replica
 
@@ -273,12 +291,21 @@ class Chain:
         return out
 
     def tinv_table(self):
-        t = np.zeros((self.Ly // 2 + 1, self.Lx // 2 + 1), np.float64)
+        """Folded 1/r table: (Ly/2+1, Lx/2+1), or (Lz/2+1, Ly/2+1, Lx/2+1) in 3D."""
+        shape = (self.Ly // 2 + 1, self.Lx // 2 + 1)
+        if self.Lz > 1:
+            shape = (self.Lz // 2 + 1,) + shape
+        t = np.zeros(shape, np.float64)
         self._lib.orc_get_tinv(self._h, _ptr(t, ctypes.c_double))
         return t
 
-    def tinv(self, dx, dy):
-        return self._lib.orc_tinv_of(self._h, int(dx), int(dy))
+    def tinv(self, dx, dy, dz=0):
+        return self._lib.orc_tinv_of3(self._h, int(dx), int(dy), int(dz))
+
+    def vectors_z(self):
+        dz = np.zeros(self.V, np.int32)
+        self._lib.orc_get_vectors_z(self._h, _ptr(dz, ctypes.c_int32))
+        return dz
 
     # ---- state ----
     def state(self):

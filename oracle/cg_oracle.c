@@ -42,7 +42,9 @@
  *       label k (0-based) of replica c = (k, r lo 32, r hi 32, c); three of
  *       the four output words are used (site, displacement, acceptance).
  *   R2  Displacements: all (dx,dy) with 0 < dx^2+dy^2 <= r_max^2 (r_max
- *       strictly below L/2), ordered dy outer ascending, dx inner ascending.
+ *       strictly below L/2), ordered dy outer ascending, dx inner ascending;
+ *       on the cubic lattice all (dx,dy,dz) with 0 < dx^2+dy^2+dz^2 <=
+ *       r_max^2, dz outermost (the plane dz = 0 is the square lattice's).
  *       Tower sampling over integer weights W_k = floor(2^32 w_k / Z),
  *       w_k = exp(-2 r_k / xi), Z = sum_k w_k; the sampled vector is the
  *       smallest k with x1 < C_k (C_k the running sum); x1 >= C_{V-1} is a
@@ -72,7 +74,9 @@
  *       u2 = x1 2^-32.  The paper's Gaussian can go negative for small m and
  *       it is silent on that case; it is clamped at zero.
  *
- * Geometry is a general Lx x Ly torus (Ly = 1 gives a ring) so that tiny
+ * Geometry is a general Lx x Ly x Lz torus (Ly = Lz = 1 gives a ring, Lz = 1
+ * the square lattice, Lx = Ly = Lz the cubic lattice of the 3D extension) so
+ * that tiny
  * systems can be enumerated exactly; the library itself only builds L x L.
  */
 #include <math.h>
@@ -279,15 +283,15 @@ typedef struct {
 } orc_hop;
 
 typedef struct orc_chain {
-    int Lx, Ly, N, Hx, Hy;    /* Hx = Lx/2 + 1 folded extents */
+    int Lx, Ly, Lz, N, Hx, Hy, Hz;  /* Hx = Lx/2 + 1 folded extents */
     double nu, W, xi, T, E;
     int r_max;
     uint64_t seed;
     uint32_t replica;
     /* tables */
-    double *tinv;             /* Hy x Hx, tinv[fy*Hx + fx] = 1/r, 0 at (0,0) */
+    double *tinv;             /* Hz x Hy x Hx, tinv[(fz*Hy + fy)*Hx + fx] = 1/r, 0 at 0 */
     int V;
-    int32_t *vdx, *vdy;
+    int32_t *vdx, *vdy, *vdz;
     double *w;                /* real tunnelling weights */
     uint64_t *Wint;           /* integer weights */
     uint64_t *C;              /* running sums */
@@ -310,22 +314,29 @@ static int fold(int d, int L)
     return (m < L - m) ? m : L - m;
 }
 
-double orc_tinv_of(const orc_chain *c, int dx, int dy)
+double orc_tinv_of3(const orc_chain *c, int dx, int dy, int dz)
 {
-    int fx = fold(dx, c->Lx), fy = fold(dy, c->Ly);
-    return c->tinv[fy * c->Hx + fx];
+    int fx = fold(dx, c->Lx), fy = fold(dy, c->Ly), fz = fold(dz, c->Lz);
+    return c->tinv[(fz * c->Hy + fy) * c->Hx + fx];
 }
 
+double orc_tinv_of(const orc_chain *c, int dx, int dy)
+{
+    return orc_tinv_of3(c, dx, dy, 0);
+}
+
+/* site s = (z Ly + y) Lx + x */
 static double tinv_sites(const orc_chain *c, int a, int b)
 {
-    int xa = a % c->Lx, ya = a / c->Lx, xb = b % c->Lx, yb = b / c->Lx;
-    return orc_tinv_of(c, xa - xb, ya - yb);
+    int xa = a % c->Lx, ya = (a / c->Lx) % c->Ly, za = a / (c->Lx * c->Ly);
+    int xb = b % c->Lx, yb = (b / c->Lx) % c->Ly, zb = b / (c->Lx * c->Ly);
+    return orc_tinv_of3(c, xa - xb, ya - yb, za - zb);
 }
 
 void orc_free(orc_chain *c)
 {
     if (!c) return;
-    free(c->tinv); free(c->vdx); free(c->vdy); free(c->w); free(c->Wint);
+    free(c->tinv); free(c->vdx); free(c->vdy); free(c->vdz); free(c->w); free(c->Wint);
     free(c->C); free(c->n); free(c->phi); free(c->eps);
     free(c);
 }
@@ -386,58 +397,66 @@ static void philox_setup_word(const orc_chain *c, uint32_t s, uint32_t domain,
     orc_philox(ctr, key, out);
 }
 
-orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
-                   double T, double E, uint64_t seed, uint32_t replica)
+orc_chain *orc_new3(int Lx, int Ly, int Lz, double nu, double W, double xi, int r_max,
+                    double T, double E, uint64_t seed, uint32_t replica)
 {
     orc_chain *c;
-    int fx, fy, dx, dy, k, s, nocc, Ry;
+    int fx, fy, fz, dx, dy, dz, k, s, nocc, Ry, Rz;
     double nuN;
     orc_sortkey *sk;
 
-    if (Lx < 2 || Ly < 1 || (Lx % 2) || (Ly > 1 && (Ly % 2))) return NULL;
+    if (Lx < 2 || Ly < 1 || Lz < 1 || (Lx % 2) || (Ly > 1 && (Ly % 2)) ||
+        (Lz > 1 && (Lz % 2)) || (Lz > 1 && Ly == 1)) return NULL;
     if (!(nu > 0.0 && nu < 1.0) || !(xi > 0.0) || !(T > 0.0) || !(W >= 0.0)) return NULL;
-    if (r_max < 1 || 2 * r_max >= Lx || (Ly > 1 && 2 * r_max >= Ly)) return NULL;
-    nuN = nu * (double)(Lx * Ly);
+    if (r_max < 1 || 2 * r_max >= Lx || (Ly > 1 && 2 * r_max >= Ly) ||
+        (Lz > 1 && 2 * r_max >= Lz)) return NULL;
+    nuN = nu * (double)(Lx * Ly * Lz);
     if (fabs(nuN - floor(nuN + 0.5)) > 1e-9) return NULL;
 
     c = (orc_chain *)calloc(1, sizeof(*c));
     if (!c) return NULL;
-    c->Lx = Lx; c->Ly = Ly; c->N = Lx * Ly;
-    c->Hx = Lx / 2 + 1; c->Hy = Ly / 2 + 1;
+    c->Lx = Lx; c->Ly = Ly; c->Lz = Lz; c->N = Lx * Ly * Lz;
+    c->Hx = Lx / 2 + 1; c->Hy = Ly / 2 + 1; c->Hz = Lz / 2 + 1;
     c->nu = nu; c->W = W; c->xi = xi; c->T = T; c->E = E; c->r_max = r_max;
     c->seed = seed; c->replica = replica;
 
     /* folded minimum-image 1/r table (reading R8: zero at the origin) */
-    c->tinv = (double *)calloc((size_t)c->Hx * c->Hy, sizeof(double));
-    for (fy = 0; fy < c->Hy; ++fy)
-        for (fx = 0; fx < c->Hx; ++fx)
-            c->tinv[fy * c->Hx + fx] =
-                (fx == 0 && fy == 0) ? 0.0
-                                     : 1.0 / sqrt((double)(fx * fx + fy * fy));
+    c->tinv = (double *)calloc((size_t)c->Hx * c->Hy * c->Hz, sizeof(double));
+    for (fz = 0; fz < c->Hz; ++fz)
+        for (fy = 0; fy < c->Hy; ++fy)
+            for (fx = 0; fx < c->Hx; ++fx)
+                c->tinv[(fz * c->Hy + fy) * c->Hx + fx] =
+                    (fx == 0 && fy == 0 && fz == 0)
+                        ? 0.0
+                        : 1.0 / sqrt((double)(fx * fx + fy * fy + fz * fz));
 
     /* displacement list and tower (reading R2) */
     Ry = (Ly > 1) ? r_max : 0;
+    Rz = (Lz > 1) ? r_max : 0;
     c->V = 0;
-    for (dy = -Ry; dy <= Ry; ++dy)
-        for (dx = -r_max; dx <= r_max; ++dx) {
-            int r2 = dx * dx + dy * dy;
-            if (r2 > 0 && r2 <= r_max * r_max) c->V++;
-        }
+    for (dz = -Rz; dz <= Rz; ++dz)
+        for (dy = -Ry; dy <= Ry; ++dy)
+            for (dx = -r_max; dx <= r_max; ++dx) {
+                int r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 > 0 && r2 <= r_max * r_max) c->V++;
+            }
     c->vdx = (int32_t *)malloc(sizeof(int32_t) * c->V);
     c->vdy = (int32_t *)malloc(sizeof(int32_t) * c->V);
+    c->vdz = (int32_t *)malloc(sizeof(int32_t) * c->V);
     c->w = (double *)malloc(sizeof(double) * c->V);
     c->Wint = (uint64_t *)malloc(sizeof(uint64_t) * c->V);
     c->C = (uint64_t *)malloc(sizeof(uint64_t) * c->V);
     k = 0;
-    for (dy = -Ry; dy <= Ry; ++dy)
-        for (dx = -r_max; dx <= r_max; ++dx) {
-            int r2 = dx * dx + dy * dy;
-            if (r2 > 0 && r2 <= r_max * r_max) {
-                c->vdx[k] = dx; c->vdy[k] = dy;
-                c->w[k] = orc_exp_core(-2.0 * sqrt((double)r2) / xi);
-                ++k;
+    for (dz = -Rz; dz <= Rz; ++dz)
+        for (dy = -Ry; dy <= Ry; ++dy)
+            for (dx = -r_max; dx <= r_max; ++dx) {
+                int r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 > 0 && r2 <= r_max * r_max) {
+                    c->vdx[k] = dx; c->vdy[k] = dy; c->vdz[k] = dz;
+                    c->w[k] = orc_exp_core(-2.0 * sqrt((double)r2) / xi);
+                    ++k;
+                }
             }
-        }
     c->Z = 0.0;
     for (k = 0; k < c->V; ++k) c->Z = c->Z + c->w[k];
     {
@@ -485,6 +504,12 @@ orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
     return c;
 }
 
+orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
+                   double T, double E, uint64_t seed, uint32_t replica)
+{
+    return orc_new3(Lx, Ly, 1, nu, W, xi, r_max, T, E, seed, replica);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Accessors                                                                 */
 /* ------------------------------------------------------------------------ */
@@ -508,7 +533,13 @@ void orc_get_vectors(const orc_chain *c, int32_t *dx, int32_t *dy,
 
 void orc_get_tinv(const orc_chain *c, double *out)
 {
-    memcpy(out, c->tinv, sizeof(double) * (size_t)c->Hx * c->Hy);
+    memcpy(out, c->tinv, sizeof(double) * (size_t)c->Hx * c->Hy * c->Hz);
+}
+
+void orc_get_vectors_z(const orc_chain *c, int32_t *dz)
+{
+    int k;
+    for (k = 0; k < c->V; ++k) dz[k] = c->vdz[k];
 }
 
 void orc_get_state(const orc_chain *c, uint8_t *n, double *eps, double *phi)
@@ -568,7 +599,7 @@ typedef struct {
     int32_t accepted;
     int32_t vec;          /* displacement index, -1 for a null proposal */
     uint32_t i, j;
-    int32_t dx, dy;
+    int32_t dx, dy, dz;
     int32_t theta;        /* n_i = 1 and n_j = 0 */
     double dE;
     double u;
@@ -597,7 +628,7 @@ void orc_tower_many(const orc_chain *c, const uint32_t *x1, int32_t *out, int n)
 void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *out)
 {
     uint32_t ctr[4], key[2];
-    int v, xi, yi, xj, yj;
+    int v, xi, yi, zi, xj, yj, zj;
     memset(out, 0, sizeof(*out));
     ctr[0] = k;
     ctr[1] = (uint32_t)round;
@@ -618,11 +649,14 @@ void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *o
     if (v < 0) { out->accepted = 0; return; }
     out->dx = c->vdx[v];
     out->dy = c->vdy[v];
+    out->dz = c->vdz[v];
     xi = (int)(out->i % (uint32_t)c->Lx);
-    yi = (int)(out->i / (uint32_t)c->Lx);
+    yi = (int)((out->i / (uint32_t)c->Lx) % (uint32_t)c->Ly);
+    zi = (int)(out->i / (uint32_t)(c->Lx * c->Ly));
     xj = (xi + out->dx + c->Lx) % c->Lx;
     yj = (yi + out->dy + c->Ly) % c->Ly;
-    out->j = (uint32_t)(yj * c->Lx + xj);
+    zj = (zi + out->dz + c->Lz) % c->Lz;
+    out->j = (uint32_t)((zj * c->Ly + yj) * c->Lx + xj);
     out->theta = (c->n[out->i] == 1) && (c->n[out->j] == 0);
     if (!out->theta) { out->accepted = 0; return; }
     out->dE = orc_delta_e(c, (int)out->i, (int)out->j, out->dx);

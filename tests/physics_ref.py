@@ -60,3 +60,23 @@ def site_energies_fft(n, phi, nu, L):
     s = (n.astype(np.float64) - nu).reshape(L, L)
     conv = np.fft.irfft2(np.fft.rfft2(g) * np.fft.rfft2(s), s=(L, L))
     return phi + conv.reshape(-1)
+
+
+def min_image_distance_matrix3(Lx, Ly, Lz):
+    """Euclidean minimum-image distance between every pair of sites of an
+    Lx x Ly x Lz torus, site s = (z Ly + y) Lx + x."""
+    N = Lx * Ly * Lz
+    s = np.arange(N)
+    x, y, z = s % Lx, (s // Lx) % Ly, s // (Lx * Ly)
+    d = []
+    for c, L in ((x, Lx), (y, Ly), (z, Lz)):
+        a = np.abs(c[:, None] - c[None, :])
+        d.append(np.minimum(a, L - a))
+    return np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+
+
+def coupling_matrix3(Lx, Ly, Lz):
+    """G[s, t] = 1 / r_st on the three-dimensional torus, 0 on the diagonal."""
+    D = min_image_distance_matrix3(Lx, Ly, Lz)
+    with np.errstate(divide="ignore"):
+        return np.where(D > 0, 1.0 / np.where(D > 0, D, 1.0), 0.0)
