@@ -46,7 +46,7 @@ TRAFFIC_CAPTURE = {"sources_sha256_16": "bb72bd921f7ac59b", "bytes_per_launch": 
 def kernel_sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("cg_pr_kernel.cu", "cg_pr_common.cuh", "cg_device.cuh"):
+    for f in ("cg_pr_kernel.cu", "cg_pr_persistent.cuh", "cg_pr_common.cuh", "cg_device.cuh"):
         with open(os.path.join(ROOT, "paper_1407_5026_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

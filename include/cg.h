@@ -68,14 +68,18 @@ typedef struct cg_handle cg_handle;
  *   T      temperature (> 0)
  *   E      field along x; dH of a hop contains -E*dx
  *   seed   Philox key (64 bits)
- *   replica  Philox counter word 3 of every draw of this replica          */
+ *   replica  Philox counter word 3 of every draw of this replica
+ *   dim    0 or 2: the L x L square lattice of the paper; 3: the L x L x L
+ *          cubic lattice (the three-dimensional extension named in the
+ *          paper's conclusions; L <= 64, hop ball dx^2+dy^2+dz^2 <= r_max^2,
+ *          one CTA per replica, binary32 refreshed in binary64)        */
 typedef struct {
     int32_t L;
     int32_t r_max;
     double nu, W, xi, T, E;
     uint64_t seed;
     uint32_t replica;
-    uint32_t pad_;
+    int32_t dim;
 } cg_replica_desc;
 
 /* Options of a handle.  Zero-initialised means: FP64, no refresh, automatic
@@ -304,11 +308,12 @@ int cg_num_groups(const cg_handle *h);
 int cg_group_shape(const cg_handle *h, int index, int *L, int *threads,
                    unsigned int *M, int *cluster);
 
-/* Replica indices of group `group`, in the group's order (count = the
- * number of replicas with that L; ascending replica index).  The paper has
- * no counterpart: this and the next two calls are the batch form of the
- * state I/O (checkpoint/resume of a whole batch).  CG_EINVAL for a bad
- * group or a NULL output. */
+/* Replica indices of group `group` (the replicas with its L and
+ * dimension, ascending) written to replicas_out, which must hold
+ * cg_num_replicas entries; returns their count (>= 1), or CG_EINVAL for a
+ * bad group or a NULL output.  The paper has no counterpart: this and the
+ * next two calls are the batch form of the state I/O (checkpoint/resume of
+ * a whole batch). */
 int cg_group_replicas(const cg_handle *h, int group, int *replicas_out);
 
 /* Read the state of every replica of one group in one copy per array

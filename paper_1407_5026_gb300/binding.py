@@ -48,7 +48,7 @@ class cg_replica_desc(ctypes.Structure):
                 ("nu", ctypes.c_double), ("W", ctypes.c_double),
                 ("xi", ctypes.c_double), ("T", ctypes.c_double),
                 ("E", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("replica", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
+                ("replica", ctypes.c_uint32), ("dim", ctypes.c_int32)]
 
 
 class cg_opts(ctypes.Structure):
@@ -181,9 +181,9 @@ def _ptr(a, ctype):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0):
+def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0, dim=0):
     return cg_replica_desc(L=L, r_max=r_max, nu=nu, W=W, xi=xi, T=T, E=E, seed=seed,
-                           replica=replica)
+                           replica=replica, dim=dim)
 
 
 def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,
@@ -406,18 +406,18 @@ def cg_debug_exp(x):
 
 
 def cg_group_replicas(h, group):
-    """Replica indices of a group (the replicas with its L, ascending)."""
-    N = cg_group_shape(h, group)["L"] ** 2
-    count = sum(1 for k in range(cg_num_replicas(h)) if cg_num_sites(h, k) == N)
-    out = np.zeros(max(count, 1), np.int32)
-    _check(load().cg_group_replicas(h, group, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
-    return out[:count].copy()
+    """Replica indices of a group (the replicas with its L and dimension)."""
+    out = np.zeros(max(cg_num_replicas(h), 1), np.int32)
+    n = load().cg_group_replicas(h, group, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if n < 0:
+        raise CgError(n, cg_last_error())
+    return out[:n].copy()
 
 
 def group_dims(h, group):
-    """(replica indices, N, bitmask words per replica) of one group."""
+    """(replica indices, sites N, bitmask words per replica) of one group."""
     reps = cg_group_replicas(h, group)
-    N = cg_group_shape(h, group)["L"] ** 2
+    N = cg_num_sites(h, int(reps[0]))
     return reps, N, (N + 31) // 32
 
 

@@ -16,30 +16,52 @@
 
 namespace cg {
 
+// Site s = (z L + y) L + x of a square (z = 0) or cubic lattice: x, y, z
+// from two exact multiply-high divisions by L.
+__device__ __forceinline__ void site_xyz(unsigned s, const DevReplica &R, int &x, int &y, int &z)
+{
+    const unsigned q = __umulhi(s, R.magicL);           // s / L
+    x = (int)(s - q * (unsigned)R.L);
+    z = (int)__umulhi(q, R.magicL);                     // s / L^2
+    y = (int)q - z * R.L;
+}
+
+// (L/2+1)^dim entries of the folded 1/r table
+__device__ __forceinline__ int tab_entries(const DevReplica &R)
+{
+    return R.dim == 3 ? R.H1 * R.H1 * R.H1 : R.H1 * R.H1;
+}
+
 __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restrict__ rp,
                                                        int precision)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const DevReplica &R = *rp;
-    const int L = R.L, N = R.N, H1 = R.H1, words = R.words;
+    const int L = R.L, N = R.N, H1 = R.H1, words = R.words, ntab = tab_entries(R);
+    const int Lz = R.dim == 3 ? L : 1;
     double *tab = reinterpret_cast<double *>(sm);
-    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(H1 * H1 * 8));
-    for (int l = threadIdx.x; l < H1 * H1; l += blockDim.x) tab[l] = R.tinv64[l];
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(ntab * 8));
+    for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab[l] = R.tinv64[l];
     for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
-    const int ys = (int)__umulhi((unsigned)s, R.magicL), xs = s - ys * L;
+    int xs, ys, zs;
+    site_xyz((unsigned)s, R, xs, ys, zs);
     const double c_occ = d_sub(1.0, R.nu), c_emp = d_sub(0.0, R.nu);
+    // t = 0 .. N-1 in increasing order, as the serial chain sums
     double acc = 0.0;
-    for (int yt = 0; yt < L; ++yt) {
-        const double *row = tab + fold_axis(ys - yt, L) * H1;
-        const int base = yt * L;
-        for (int xt = 0; xt < L; ++xt) {
-            const int t = base + xt;
-            if (t == s) continue;
-            const double c = ((occ[t >> 5] >> (t & 31)) & 1u) ? c_occ : c_emp;
-            acc = d_add(acc, d_mul(c, row[fold_axis(xs - xt, L)]));
+    for (int zt = 0; zt < Lz; ++zt) {
+        const double *plane = tab + fold_axis(zs - zt, Lz) * H1 * H1;
+        for (int yt = 0; yt < L; ++yt) {
+            const double *row = plane + fold_axis(ys - yt, L) * H1;
+            const int base = (zt * L + yt) * L;
+            for (int xt = 0; xt < L; ++xt) {
+                const int t = base + xt;
+                if (t == s) continue;
+                const double c = ((occ[t >> 5] >> (t & 31)) & 1u) ? c_occ : c_emp;
+                acc = d_add(acc, d_mul(c, row[fold_axis(xs - xt, L)]));
+            }
         }
     }
     const double e = d_add(R.phi[s], acc);
@@ -49,10 +71,10 @@ __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restr
         reinterpret_cast<float *>(R.eps)[s] = __double2float_rn(e);
 }
 
-cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int H1, int words, int precision,
+cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int ntab, int words, int precision,
                             cudaStream_t st)
 {
-    const int smem = cg_align16(H1 * H1 * 8) + words * 4;
+    const int smem = cg_align16(ntab * 8) + words * 4;
     cudaError_t e = cudaFuncSetAttribute(eps_init_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e) return e;
@@ -65,17 +87,19 @@ __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__r
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ unsigned long long s_max;
     const DevReplica &R = *rp;
-    const int L = R.L, N = R.N, H1 = R.H1, words = R.words;
+    const int L = R.L, N = R.N, H1 = R.H1, words = R.words, ntab = tab_entries(R);
+    const int Lz = R.dim == 3 ? L : 1;
     double *tab = reinterpret_cast<double *>(sm);
-    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(H1 * H1 * 8));
-    for (int l = threadIdx.x; l < H1 * H1; l += blockDim.x) tab[l] = R.tinv64[l];
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(ntab * 8));
+    for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab[l] = R.tinv64[l];
     for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
     if (threadIdx.x == 0) s_max = 0ull;
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double err = 0.0;
     if (s < N) {
-        const int ys = (int)__umulhi((unsigned)s, R.magicL), xs = s - ys * L;
+        int xs, ys, zs;
+        site_xyz((unsigned)s, R, xs, ys, zs);
         double acc = 0.0;
         for (int w = 0; w < words; ++w) {
             unsigned bits = occ[w];
@@ -83,8 +107,10 @@ __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__r
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int t = w * 32 + b;
-                const int yt = (int)__umulhi((unsigned)t, R.magicL), xt = t - yt * L;
-                acc += tab[fold_axis(ys - yt, L) * H1 + fold_axis(xs - xt, L)];
+                int xt, yt, zt;
+                site_xyz((unsigned)t, R, xt, yt, zt);
+                acc += tab[(fold_axis(zs - zt, Lz) * H1 + fold_axis(ys - yt, L)) * H1 +
+                           fold_axis(xs - xt, L)];
             }
         }
         const double e = R.phi[s] + (acc + R.negC0nu);
@@ -107,10 +133,10 @@ __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__r
     }
 }
 
-cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int words,
+cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int ntab, int words,
                                 cudaStream_t st)
 {
-    const int smem = cg_align16(H1 * H1 * 8) + words * 4;
+    const int smem = cg_align16(ntab * 8) + words * 4;
     cudaError_t e = cudaFuncSetAttribute(refresh_fp64_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e) return e;

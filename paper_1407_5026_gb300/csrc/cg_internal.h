@@ -48,7 +48,7 @@ struct alignas(16) DevReplica {
     unsigned int magicL;      // y = umulhi(s, magicL) == s / L for s < N
     unsigned int key0, key1;  // Philox key (seed lo, seed hi)
     unsigned int replica;     // Philox counter word 3
-    int pad0_;
+    int dim;                  // 2 (square lattice) or 3 (cubic lattice)
     double nu, T, E;
     double negC0nu;           // -nu * sum_{t != s} 1/r_st (same for every s)
     double C0;                // sum_{t != s} 1/r_st
@@ -109,13 +109,14 @@ struct SmemLayout {
 
 __host__ __device__ inline int cg_align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int N, int H1, int V, int words,
+// tab_entries: (L/2+1)^dim entries of the folded 1/r table
+__host__ __device__ inline SmemLayout smem_layout(int N, int tab_entries, int V, int words,
                                                   int real_bytes)
 {
     SmemLayout s;
     int o = 0;
     s.off_eps = o;   o = cg_align16(o + N * real_bytes);
-    s.off_tinv = o;  o = cg_align16(o + H1 * H1 * real_bytes);
+    s.off_tinv = o;  o = cg_align16(o + tab_entries * real_bytes);
     s.off_occ = o;   o = cg_align16(o + words * 4);
     s.off_guide = o; o = cg_align16(o + kGuide * 2);
     s.off_thr = o;   o = cg_align16(o + V * 4);
@@ -131,15 +132,20 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int H1, int V, int word
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps,
                                  const int *d_index, int n_ctas, int threads,
                                  int smem_bytes, const RunArgs &args,
-                                 cudaStream_t st, int L);
+                                 cudaStream_t st, int L, int dim);
+// The cubic-lattice instances (cg_pr_kernel3d.cu).
+cudaError_t launch_pr_persistent3(int precision, const DevReplica *d_reps, const int *d_index,
+                                  int n_ctas, int threads, int smem_bytes, const RunArgs &args,
+                                  cudaStream_t st, int L);
+cudaError_t set_pr3_smem_limit(int precision, int bytes);
 // The same chain over a thread-block cluster of `cluster` CTAs per replica
 // (eps split by rows); grid = n_reps * cluster CTAs.
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
                               int n_reps, int cluster, int threads, int smem_bytes,
                               const RunArgs &args, cudaStream_t st, int L);
-cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int H1, int words,
+cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int tab_entries, int words,
                             int precision, cudaStream_t st);
-cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int H1, int words,
+cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int tab_entries, int words,
                                 cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t *ctr, const uint32_t *key,
                                 uint32_t *out, int n, cudaStream_t st);

@@ -84,6 +84,7 @@ float bf16_to_float(uint32_t h)
 struct Tables {
     int L = 0, r_max = 0, H1 = 0, V = 0;
     double xi = 0, Z = 0, C0 = 0;
+    int dim = 2;                      // 2: square lattice, 3: cubic lattice
     std::vector<double> t64;
     std::vector<float> t32;
     std::vector<unsigned> thr;
@@ -100,14 +101,18 @@ struct Tables {
     double *d_tinvd = nullptr;
 };
 
-int build_tables(Tables &t, int L, double xi, int r_max)
+int build_tables(Tables &t, int L, double xi, int r_max, int dim)
 {
-    t.L = L; t.xi = xi; t.r_max = r_max; t.H1 = L / 2 + 1;
-    t.t64.assign((size_t)t.H1 * t.H1, 0.0);
-    for (int fy = 0; fy < t.H1; ++fy)
-        for (int fx = 0; fx < t.H1; ++fx)
-            t.t64[(size_t)fy * t.H1 + fx] =
-                (fx == 0 && fy == 0) ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy));
+    t.L = L; t.xi = xi; t.r_max = r_max; t.H1 = L / 2 + 1; t.dim = dim;
+    const int H1 = t.H1, Hz = dim == 3 ? H1 : 1;
+    // folded 1/r table, [(fz H1 + fy) H1 + fx], 0 at the origin
+    t.t64.assign((size_t)Hz * H1 * H1, 0.0);
+    for (int fz = 0; fz < Hz; ++fz)
+        for (int fy = 0; fy < H1; ++fy)
+            for (int fx = 0; fx < H1; ++fx)
+                t.t64[((size_t)fz * H1 + fy) * H1 + fx] =
+                    (fx == 0 && fy == 0 && fz == 0)
+                        ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy + fz * fz));
     t.t32.resize(t.t64.size());
     for (size_t k = 0; k < t.t64.size(); ++k) t.t32[k] = (float)t.t64[k];
     // two-term BF16 split of 1/r for the tensor-core refresh: hi = bf16(T),
@@ -121,19 +126,30 @@ int build_tables(Tables &t, int L, double xi, int r_max)
     }
     // sum_{t != s} 1/r_st is the same for every s: every displacement once
     double C0 = 0.0;
-    for (int dy = 0; dy < L; ++dy)
-        for (int dx = 0; dx < L; ++dx)
-            C0 += t.t64[(size_t)fold_axis(dy, L) * t.H1 + fold_axis(dx, L)];
+    const int Lz = dim == 3 ? L : 1;
+    for (int dz = 0; dz < Lz; ++dz)
+        for (int dy = 0; dy < L; ++dy)
+            for (int dx = 0; dx < L; ++dx)
+                C0 += t.t64[((size_t)fold_axis(dz, Lz) * H1 + fold_axis(dy, L)) * H1 +
+                            fold_axis(dx, L)];
     t.C0 = C0;
+    // hop vectors, dz outermost (the square lattice: dz = 0 only), packed as
+    // dx | dy << 16 on the square lattice and as 10-bit fields
+    // dx | dy << 10 | dz << 20 on the cubic lattice
     std::vector<double> w;
-    for (int dy = -r_max; dy <= r_max; ++dy)
-        for (int dx = -r_max; dx <= r_max; ++dx) {
-            const int r2 = dx * dx + dy * dy;
-            if (r2 == 0 || r2 > r_max * r_max) continue;
-            t.disp.push_back((dx & 0xffff) | (dy * 65536));
-            w.push_back(host_exp(-2.0 * std::sqrt((double)r2) / xi));
-            t.tinvd.push_back(t.t64[(size_t)std::abs(dy) * t.H1 + std::abs(dx)]);
-        }
+    const int Rz = dim == 3 ? r_max : 0;
+    for (int dz = -Rz; dz <= Rz; ++dz)
+        for (int dy = -r_max; dy <= r_max; ++dy)
+            for (int dx = -r_max; dx <= r_max; ++dx) {
+                const int r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 == 0 || r2 > r_max * r_max) continue;
+                t.disp.push_back(dim == 3 ? (int)((unsigned)(dx & 0x3ff) | ((unsigned)(dy & 0x3ff) << 10) |
+                                                  ((unsigned)dz << 20))
+                                          : (dx & 0xffff) | (dy * 65536));
+                w.push_back(host_exp(-2.0 * std::sqrt((double)r2) / xi));
+                t.tinvd.push_back(
+                    t.t64[((size_t)std::abs(dz) * H1 + std::abs(dy)) * H1 + std::abs(dx)]);
+            }
     t.V = (int)w.size();
     double Z = 0.0;
     for (double v : w) Z = Z + v;
@@ -179,6 +195,7 @@ struct Rep {
 
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
+    int dim = 2;                     // 2: square lattice, 3: cubic lattice
     int cluster = 1;                 // CTAs per replica
     unsigned M = 4096;               // labels per round when cg_run is given M = 0
     bool tuned = false;
@@ -193,9 +210,9 @@ constexpr int kTcMaxReplicas = 512;  // TMEM columns of one accumulator
 
 // Whether a group of `count` binary32 replicas of side L refreshes on the
 // tensor cores (it needs L*L to be a multiple of 128).
-bool group_uses_tc(const cg_opts &o, int L, int count)
+bool group_uses_tc(const cg_opts &o, int L, int count, int dim)
 {
-    if (o.precision != CG_FP32 || (L * L) % 128 != 0) return false;
+    if (o.precision != CG_FP32 || dim == 3 || (L * L) % 128 != 0) return false;
     if (o.refresh_kind == CG_REFRESH_BF16X2) return true;
     if (o.refresh_kind == CG_REFRESH_AUTO) return count >= 8;
     return false;
@@ -266,11 +283,22 @@ int dalloc(cg_handle *h, void **p, size_t bytes)
     return CG_OK;
 }
 
+// 2 for the square lattice (dim 0 or 2), 3 for the cubic lattice
+int dim_of(const cg_replica_desc &d) { return d.dim == 3 ? 3 : 2; }
+
+// sites of a replica: L^2 or L^3
+int sites_of(const cg_replica_desc &d)
+{
+    return dim_of(d) == 3 ? d.L * d.L * d.L : d.L * d.L;
+}
+
 int check_desc(const cg_replica_desc &d)
 {
+    if (d.dim != 0 && d.dim != 2 && d.dim != 3) return fail(CG_EINVAL, "dim must be 0, 2 or 3");
     if (d.L < 4 || d.L > 1024 || (d.L & 1))
         return fail(CG_EINVAL, "L must be even and in [4, 1024]");
-    const double N = (double)d.L * d.L;
+    if (d.dim == 3 && d.L > 64) return fail(CG_EINVAL, "a cubic lattice needs L <= 64");
+    const double N = (double)sites_of(d);
     if (!(d.nu > 0.0 && d.nu < 1.0)) return fail(CG_EINVAL, "nu must be in (0, 1)");
     if (std::fabs(d.nu * N - std::floor(d.nu * N + 0.5)) > 1e-9)
         return fail(CG_EINVAL, "nu * N must be an integer");
@@ -285,7 +313,7 @@ int check_desc(const cg_replica_desc &d)
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
     const int rb = precision == CG_FP64 ? 8 : 4;
-    return smem_layout(r.N / cluster, r.tab->H1, r.tab->V, r.words, rb).total;
+    return smem_layout(r.N / cluster, (int)r.tab->t64.size(), r.tab->V, r.words, rb).total;
 }
 
 // CTAs per replica: 1 when the replica fits one CTA's shared memory, else the
@@ -294,6 +322,8 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
 int choose_cluster(const cg_opts &o, const Rep &r, int optin)
 {
     const int budget = optin - 2048;     // room for the kernels' static shared memory
+    if (dim_of(r.d) == 3)                // the cubic lattice runs on one CTA
+        return persistent_smem(r, o.precision, 1) <= budget ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
         if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
@@ -324,6 +354,7 @@ void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
     std::memset(&dr, 0, sizeof(dr));
     const Tables &t = *r.tab;
     dr.L = r.d.L; dr.N = r.N; dr.H1 = t.H1; dr.V = t.V; dr.words = r.words;
+    dr.dim = t.dim;
     dr.magicL = magic_for(r.d.L);
     dr.key0 = (unsigned)r.d.seed;
     dr.key1 = (unsigned)(r.d.seed >> 32);
@@ -343,7 +374,7 @@ void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
 void host_setup_state(const cg_replica_desc &d, std::vector<double> &phi,
                       std::vector<unsigned char> &n)
 {
-    const int N = d.L * d.L;
+    const int N = sites_of(d);
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     phi.resize(N);
     n.assign(N, 0);
@@ -381,7 +412,7 @@ int replica_index_ok(const cg_handle *h, int r)
 double energy_from_eps(const cg_replica_desc &d, const unsigned char *n, const double *eps,
                        const double *phi, long long *P_out)
 {
-    const int N = d.L * d.L;
+    const int N = sites_of(d);
     double h1 = 0.0, h2 = 0.0;
     long long P = 0;
     for (int s = 0; s < N; ++s) {
@@ -429,7 +460,8 @@ int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
             CG_CUDA(cudaStreamSynchronize(h->st));
         }
     } else {
-        CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, r.tab->H1, r.words, h->opts.precision, h->st));
+        CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, (int)r.tab->t64.size(), r.words,
+                                h->opts.precision, h->st));
     }
     DevCounters dc;
     std::memset(&dc, 0, sizeof(dc));
@@ -458,36 +490,42 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
     // mirrors the allocations of create_impl (each rounded up to 256 bytes)
     const int precision = o.precision;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    std::vector<std::pair<int, int>> groups;   // (L, count)
+    std::vector<std::tuple<int, int, int>> groups;   // (L, dim, count)
     for (int k = 0; k < R; ++k) {
         bool found = false;
         for (auto &g : groups)
-            if (g.first == reps[k].L) { ++g.second; found = true; }
-        if (!found) groups.push_back({reps[k].L, 1});
+            if (std::get<0>(g) == reps[k].L && std::get<1>(g) == dim_of(reps[k])) {
+                ++std::get<2>(g);
+                found = true;
+            }
+        if (!found) groups.push_back({reps[k].L, dim_of(reps[k]), 1});
     }
     size_t tc_total = 0;
     for (auto &g : groups)
-        if (group_uses_tc(o, g.first, g.second))
-            tc_total += up(tc_img_bytes(g.first, g.second)) + up(sizeof(int));
+        if (group_uses_tc(o, std::get<0>(g), std::get<2>(g), std::get<1>(g)))
+            tc_total += up(tc_img_bytes(std::get<0>(g), std::get<2>(g))) + up(sizeof(int));
     size_t total = up(sizeof(DevReplica) * (size_t)R) + up(sizeof(int) * (size_t)R);
-    std::vector<std::tuple<int, int, double>> seen;
+    std::vector<std::tuple<int, int, double, int>> seen;
     for (int k = 0; k < R; ++k) {
         const cg_replica_desc &d = reps[k];
-        const size_t N = (size_t)d.L * d.L, words = (N + 31) / 32;
+        const size_t N = (size_t)sites_of(d), words = (N + 31) / 32;
         total += up(N * (precision == CG_FP64 ? 8 : 4)) + up(words * 4) + up(N * 8) +
                  up(sizeof(DevCounters));
-        auto key = std::make_tuple(d.L, d.r_max, d.xi);
+        auto key = std::make_tuple(d.L, d.r_max, d.xi, dim_of(d));
         if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
             seen.push_back(key);
             const size_t H1 = d.L / 2 + 1;
+            const size_t tab = dim_of(d) == 3 ? H1 * H1 * H1 : H1 * H1;
+            const int Rz = dim_of(d) == 3 ? d.r_max : 0;
             size_t V = 0;
-            for (int dy = -d.r_max; dy <= d.r_max; ++dy)
-                for (int dx = -d.r_max; dx <= d.r_max; ++dx) {
-                    const int r2 = dx * dx + dy * dy;
-                    if (r2 > 0 && r2 <= d.r_max * d.r_max) ++V;
-                }
-            total += up(H1 * H1 * 8) + up(H1 * H1 * 4) + up(V * 4) + up(V * 4) + up(V * 8) +
-                     up((size_t)kGuide * 2) + up(H1 * H1 * 4);
+            for (int dz = -Rz; dz <= Rz; ++dz)
+                for (int dy = -d.r_max; dy <= d.r_max; ++dy)
+                    for (int dx = -d.r_max; dx <= d.r_max; ++dx) {
+                        const int r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > 0 && r2 <= d.r_max * d.r_max) ++V;
+                    }
+            total += up(tab * 8) + up(tab * 4) + up(V * 4) + up(V * 4) + up(V * 8) +
+                     up((size_t)kGuide * 2) + up(tab * 4);
         }
     }
     return total + tc_total;
@@ -553,13 +591,17 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     for (int k = 0; k < R; ++k) {
         Rep &r = h->reps[k];
         r.d = reps[k];
-        r.N = r.d.L * r.d.L;
+        r.N = sites_of(r.d);
         r.words = (r.N + 31) / 32;
         for (auto &t : h->tables)
-            if (t->L == r.d.L && t->r_max == r.d.r_max && t->xi == r.d.xi) r.tab = t.get();
+            if (t->L == r.d.L && t->r_max == r.d.r_max && t->xi == r.d.xi && t->dim == dim_of(r.d))
+                r.tab = t.get();
         if (!r.tab) {
             std::unique_ptr<Tables> t(new Tables());
-            if (build_tables(*t, r.d.L, r.d.xi, r.d.r_max) != CG_OK) { destroy_partial(); return nullptr; }
+            if (build_tables(*t, r.d.L, r.d.xi, r.d.r_max, dim_of(r.d)) != CG_OK) {
+                destroy_partial();
+                return nullptr;
+            }
             r.tab = t.get();
             h->tables.push_back(std::move(t));
         }
@@ -591,17 +633,18 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         cudaMemcpyAsync(t->d_guide, t->guide.data(), t->guide.size() * 2, cudaMemcpyHostToDevice, h->st);
     }
     const int rb = o.precision == CG_FP64 ? 8 : 4;
-    // groups of equal L (one launch each), replica order kept inside a group
+    // groups of equal (dimension, L) (one launch each), replica order kept
+    // inside a group
+    auto gkey = [&](int k) { return dim_of(h->reps[k].d) * 4096 + h->reps[k].d.L; };
     std::vector<int> order(R);
     for (int k = 0; k < R; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return h->reps[a].d.L < h->reps[b].d.L; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gkey(a) < gkey(b); });
     // each group's eps, bitmasks, phi and counters are one block per array in
     // group order, so a group's state moves between host and device in one
     // copy per array (cg_read_group_state / cg_write_group_state)
     for (int k = 0; k < R;) {
         int e = k;
-        while (e < R && h->reps[order[e]].d.L == h->reps[order[k]].d.L) ++e;
+        while (e < R && gkey(order[e]) == gkey(order[k])) ++e;
         const Rep &r0 = h->reps[order[k]];
         const size_t cnt = (size_t)(e - k);
         char *eb = nullptr, *pb = nullptr;
@@ -624,11 +667,13 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     for (int k = 0; k < R;) {
         Group g;
         g.L = h->reps[order[k]].d.L;
+        g.dim = dim_of(h->reps[order[k]].d);
         g.first = k;
+        const int key = gkey(order[k]);
         int smem = 0, cluster = 1;
-        for (int m = k; m < R && h->reps[order[m]].d.L == g.L; ++m)
+        for (int m = k; m < R && gkey(order[m]) == key; ++m)
             cluster = std::max(cluster, choose_cluster(o, h->reps[order[m]], optin));
-        while (k < R && h->reps[order[k]].d.L == g.L) {
+        while (k < R && gkey(order[k]) == key) {
             smem = std::max(smem, persistent_smem(h->reps[order[k]], o.precision, cluster));
             ++k;
         }
@@ -641,7 +686,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             if (g.threads < 512) g.threads = 512;
             while (g.threads < g.L && g.threads < 1024) g.threads *= 2;
         }
-        g.tc = group_uses_tc(o, g.L, g.count);
+        g.tc = group_uses_tc(o, g.L, g.count, g.dim);
         if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.count)) ||
                      dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
             destroy_partial();
@@ -707,7 +752,8 @@ int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
         for (int k = g.first; k < g.first + g.count; ++k) {
             const int ri = h->order[k];
             const Rep &r = h->reps[ri];
-            CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, r.tab->H1, r.words, CG_FP64, st));
+            CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, (int)r.tab->t64.size(), r.words, CG_FP64,
+                                    st));
         }
         return CG_OK;
     }
@@ -723,7 +769,7 @@ int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
         for (int k = g.first; k < g.first + g.count; ++k) {
             const int ri = h->order[k];
             const Rep &r = h->reps[ri];
-            CG_CUDA(launch_refresh_fp64(h->d_reps + ri, r.N, r.tab->H1, r.words, st));
+            CG_CUDA(launch_refresh_fp64(h->d_reps + ri, r.N, (int)r.tab->t64.size(), r.words, st));
         }
     }
     return CG_OK;
@@ -759,7 +805,7 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
                                   g.cluster, g.threads, g.smem, a, st, g.L));
     else
         CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first,
-                                     g.count, g.threads, g.smem, a, st, g.L));
+                                     g.count, g.threads, g.smem, a, st, g.L, g.dim));
     return CG_OK;
 }
 
@@ -1032,7 +1078,7 @@ int cg_group_replicas(const cg_handle *h, int group, int *replicas_out)
         return fail(CG_EINVAL, "bad group or null output");
     const Group &g = h->groups[group];
     for (int k = 0; k < g.count; ++k) replicas_out[k] = h->order[g.first + k];
-    return CG_OK;
+    return g.count;
 }
 
 int cg_read_group_state(cg_handle *h, int group, uint32_t *occ_words_host, void *eps_host,

@@ -80,7 +80,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int row0 = (int)rank * rows_local;
     const int log2L = __ffs(L) - 1;
 
-    const SmemLayout lay = smem_layout(N_local, H1, V, words, (int)sizeof(Real));
+    const SmemLayout lay = smem_layout(N_local, H1 * H1, V, words, (int)sizeof(Real));
     Shared S;
     S.eps = smem + lay.off_eps;
     S.tinv = smem + lay.off_tinv;

@@ -87,7 +87,7 @@ struct Prop {
 // Step 1 of one label (Philox, site, tower, destination) and theta.  P is the
 // Philox prefix of the label's round (counter words 1-3); kPow2 selects shift
 // and mask site arithmetic when L is a power of two (log2L its exponent).
-template <bool kPow2>
+template <bool kPow2, int kDim = 2>
 __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const PhiloxPrefix &P,
                                         uint32_t key0, uint32_t key1, int L, int log2L,
                                         unsigned N, unsigned magic, unsigned thr_last,
@@ -97,27 +97,55 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     uint32_t x[4];
     philox_finish(k, P, key0, key1, x);
     p.x2 = x[2];
-    p.i = kPow2 ? (x[0] >> (32 - 2 * log2L)) : __umulhi(x[0], N);   // floor(x0 N / 2^32)
+    p.i = kPow2 ? (x[0] >> (32 - kDim * log2L)) : __umulhi(x[0], N);   // floor(x0 N / 2^32)
     // a label beyond M or a null proposal (x1 above the last threshold) is
     // evaluated on a clamped x1 without a branch and can never pass theta
     const uint32_t x1 = min(x[1], thr_last);
     const bool live = valid && x[1] <= thr_last;
     const int v = tower_lookup(S.guide, S.thr, x1);
     const int dxy = S.disp[v];
-    const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
-    if (kPow2) {
-        const int Lm = L - 1;
-        const int xj = ((int)p.i + dx) & Lm;
-        const int yj = (((int)p.i >> log2L) + dy) & Lm;
-        p.j = (unsigned)((yj << log2L) | xj);
+    if (kDim == 3) {
+        // cubic lattice: 10-bit fields dx | dy << 10 | dz << 20, site
+        // s = (z L + y) L + x
+        const int dx = (dxy << 22) >> 22, dy = (dxy << 12) >> 22, dz = dxy >> 20;
+        int xi, yi, zi;
+        if (kPow2) {
+            const int m = L - 1;
+            xi = (int)p.i & m;
+            yi = (int)(p.i >> log2L) & m;
+            zi = (int)(p.i >> (2 * log2L));
+            const int xj = (xi + dx) & m, yj = (yi + dy) & m, zj = (zi + dz) & m;
+            p.j = (unsigned)((((zj << log2L) | yj) << log2L) | xj);
+        } else {
+            const unsigned q = __umulhi(p.i, magic);
+            xi = (int)(p.i - q * (unsigned)L);
+            zi = (int)__umulhi(q, magic);
+            yi = (int)q - zi * L;
+            int xj = xi + dx, yj = yi + dy, zj = zi + dz;
+            xj += (xj < 0) ? L : 0;
+            xj -= (xj >= L) ? L : 0;
+            yj += (yj < 0) ? L : 0;
+            yj -= (yj >= L) ? L : 0;
+            zj += (zj < 0) ? L : 0;
+            zj -= (zj >= L) ? L : 0;
+            p.j = (unsigned)((zj * L + yj) * L + xj);
+        }
     } else {
-        const int yi = (int)__umulhi(p.i, magic), xi = (int)p.i - yi * L;
-        int xj = xi + dx, yj = yi + dy;
-        xj += (xj < 0) ? L : 0;
-        xj -= (xj >= L) ? L : 0;
-        yj += (yj < 0) ? L : 0;
-        yj -= (yj >= L) ? L : 0;
-        p.j = (unsigned)(yj * L + xj);
+        const int dx = (int)(short)(dxy & 0xffff), dy = dxy >> 16;
+        if (kPow2) {
+            const int Lm = L - 1;
+            const int xj = ((int)p.i + dx) & Lm;
+            const int yj = (((int)p.i >> log2L) + dy) & Lm;
+            p.j = (unsigned)((yj << log2L) | xj);
+        } else {
+            const int yi = (int)__umulhi(p.i, magic), xi = (int)p.i - yi * L;
+            int xj = xi + dx, yj = yi + dy;
+            xj += (xj < 0) ? L : 0;
+            xj -= (xj >= L) ? L : 0;
+            yj += (yj < 0) ? L : 0;
+            yj -= (yj >= L) ? L : 0;
+            p.j = (unsigned)(yj * L + xj);
+        }
     }
     p.v = v;
     p.dxy = dxy;

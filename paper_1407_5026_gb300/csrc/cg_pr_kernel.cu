@@ -1,364 +1,10 @@
-// cg_pr_kernel.cu -- the persistent parallel-rejection kernel.
-//
-// One CTA runs one disorder replica for a whole launch.  Its local energies
-// eps (N values), the folded minimum-image 1/r table, the occupation bitmask
-// and the tower (thresholds + a guide table) live in shared memory; global
-// memory is touched only to load the state at the start and store it at the
-// end.
-//
-// Per executed hop (mixed PR algorithm, section "Hopping conduction in the
-// Coulomb glass", steps 1-3):
-//   rounds r = 0, 1, ...: the M labels of a round are evaluated in chunks of
-//   C labels in increasing order, two labels per thread.  Label k draws
-//   Philox(key = seed, ctr = (k, r lo, r hi, replica)) -> site i from word 0,
-//   hop vector from word 1 by tower sampling, acceptance variate from word 2
-//   (step 1 and the three random numbers per label of the GPU paragraph);
-//   theta = n_i (1 - n_j) and the Metropolis test on
-//   dH = eps_j - eps_i - 1/r_ij - E dx (step 2, Eq. 2).  A chunk with no
-//   accept costs one block-wide OR barrier; the first chunk with an accept
-//   gives the lowest accepting label q by warp ballot + find-first-set and a
-//   minimum over the warps.  Labels after q are never looked at, so the hop
-//   equals the serial rejection chain's on the same random numbers.  C follows
-//   the replica's recent attempts per hop (C ~ sqrt(128 m), clamped to
-//   [64, 2 * blockDim]); it changes which labels are evaluated, never the hop.
-//   Commit (step 3a/3c): flip n_i, n_j, P += dx, attempts += (p-1)M + q.
-//   Update (step 3b): eps_l += 1/r_lj - 1/r_li for every l, with the table
-//   holding 0 at the origin so l = i and l = j need no special case.  A
-//   thread takes the four sites (x, y), (x + L/2, y), (x, y + L/2),
-//   (x + L/2, y + L/2): on an even ring fold(d + L/2) = L/2 - fold(d), so one
-//   folded offset per axis serves all four.
-//
-// Binary64 form: every operation that feeds the chain is a round-to-nearest
-// intrinsic in the serial chain's order, so the trajectory is bit-identical
-// to the serial CPU chain.  The Metropolis comparison u < exp(-dH/T) is first
-// decided by a binary32 estimate with a relative margin of 2e-4 (ten times
-// its error bound); only the undecided cases evaluate the binary64
-// exponential, so every decision is the binary64 one.
-// Binary32 form: eps, the table and dH in binary32 (dH in binary64 when
-// |dH| < 1e-5), exp from the fast intrinsic.
-#include "cg_pr_common.cuh"
+// cg_pr_kernel.cu -- launches of the persistent parallel-rejection kernel
+// (cg_pr_persistent.cuh) on the square lattice, with L = 64 and L = 128
+// fixed at compile time and any other L at run time; cubic lattices go to
+// cg_pr_kernel3d.cu.
+#include "cg_pr_persistent.cuh"
 
 namespace cg {
-
-// kLog2L > 0: L = 2^kLog2L fixed at compile time (the lattice constants
-// fold into immediates and free registers for the labels); kLog2L = 0: L a
-// power of two known at run time; kLog2L < 0: any even L.
-// kTime: CG_TIME_GAUSSIAN runs (the step-3c deviates are drawn in the
-// kernel); the default deterministic clock compiles without that code.
-template <typename Real, int kThreads, int kLog2L, bool kTime>
-__global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
-pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
-{
-    constexpr bool kPow2 = kLog2L >= 0;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned int s_wlabel[32];
-    __shared__ Cand s_cand[32];
-    // step-3c deviates of the next hops (CG_TIME_GAUSSIAN): warp 0 draws 32
-    // at a time, one per lane, so the binary64 Box-Muller chain runs once
-    // per 32 hops instead of on thread 0's path at every commit
-    __shared__ double s_z[32];
-    __shared__ unsigned long long s_zbase;
-    // counters and pointers only thread 0 uses (registers stay free for the
-    // labels)
-    __shared__ struct {
-        unsigned long long hops, attempts, evaluated, cyc_rej, cyc_upd;
-        long long P, t0;
-        double energy, time;
-        cg_hop *log;
-        int tracing;
-        float m_ema;
-    } s_c;
-
-    const DevReplica &Rg = reps[index[blockIdx.x]];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int L = kLog2L > 0 ? (1 << kLog2L) : Rg.L;
-    const int N = L * L, H1 = L / 2 + 1, words = (N + 31) / 32;
-    const int V = Rg.V;
-    const unsigned magic = kPow2 ? 0u : Rg.magicL;
-    const int log2L = kLog2L > 0 ? kLog2L : __ffs(L) - 1;   // used when L is a power of two
-    const uint32_t key0 = Rg.key0, key1 = Rg.key1, rep = Rg.replica;
-    const double T = Rg.T;
-    const float invTf = (float)(1.0 / T);
-
-    const SmemLayout lay = smem_layout(N, H1, V, words, (int)sizeof(Real));
-    Shared S;
-    S.eps = smem + lay.off_eps;
-    S.tinv = smem + lay.off_tinv;
-    S.occ = reinterpret_cast<unsigned *>(smem + lay.off_occ);
-    S.guide = reinterpret_cast<unsigned short *>(smem + lay.off_guide);
-    S.thr = reinterpret_cast<unsigned *>(smem + lay.off_thr);
-    S.disp = reinterpret_cast<int *>(smem + lay.off_disp);
-    S.vr64 = reinterpret_cast<double *>(smem + lay.off_vr64);
-    S.edx64 = reinterpret_cast<double *>(smem + lay.off_edx64);
-    S.cv32 = reinterpret_cast<float *>(smem + lay.off_cv32);
-    Real *eps = reinterpret_cast<Real *>(S.eps);
-    const Real *tinv = reinterpret_cast<const Real *>(S.tinv);
-
-    // ---- stage the replica into shared memory ----
-    {
-        const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps);
-        for (int l = tid; l < N; l += kThreads) eps[l] = eps_g[l];
-        const Real *tab_g = (sizeof(Real) == 8)
-                                ? reinterpret_cast<const Real *>(Rg.tinv64)
-                                : reinterpret_cast<const Real *>(Rg.tinv32);
-        Real *tab_s = reinterpret_cast<Real *>(S.tinv);
-        for (int l = tid; l < H1 * H1; l += kThreads) tab_s[l] = tab_g[l];
-        for (int l = tid; l < words; l += kThreads) S.occ[l] = Rg.occ[l];
-        for (int l = tid; l < kGuide; l += kThreads) S.guide[l] = Rg.guide[l];
-        for (int l = tid; l < V; l += kThreads) {
-            const int dxy = Rg.disp[l];
-            const int dx = (int)(short)(dxy & 0xffff);
-            S.thr[l] = Rg.thr[l];
-            S.disp[l] = dxy;
-            S.vr64[l] = Rg.tinvd[l];
-            S.edx64[l] = d_mul(Rg.E, (double)dx);       // E * dx, as in the serial chain
-            S.cv32[l] = (float)d_add(Rg.tinvd[l], S.edx64[l]);   // one rounding to binary32
-        }
-    }
-    unsigned long long rounds = Rg.ctr->rounds;
-    if (tid == 0) {
-        const DevCounters *cnt = Rg.ctr;
-        s_c.log = Rg.log;
-        s_c.tracing = Rg.trace != nullptr;
-        s_c.hops = cnt->hops;
-        s_c.attempts = cnt->attempts;
-        s_c.evaluated = cnt->evaluated;
-        s_c.P = cnt->P;
-        s_c.energy = cnt->energy;
-        s_c.time = cnt->time;
-        s_c.m_ema = cnt->m_ema > 0.f ? cnt->m_ema : 64.0f;
-        s_c.cyc_rej = 0;
-        s_c.cyc_upd = 0;
-    }
-    int status = CG_OK;
-    __syncthreads();
-
-    const unsigned M = a.M;
-    const unsigned thr_last = S.thr[V - 1];
-
-    if (kTime) {
-        if (tid == 0) s_zbase = ~0ull;
-        __syncthreads();
-    }
-    for (unsigned long long h = 0; h < a.n_hops; ++h) {
-        if (kTime && warp == 0) {
-            // s_c.hops was last written before the previous hop's final barrier
-            const unsigned long long hcur = s_c.hops;
-            if (hcur < s_zbase || hcur - s_zbase >= 32ull) {
-                s_z[lane] = cg_gauss(key0, key1, rep, hcur + (unsigned long long)lane);
-                __syncwarp();
-                if (lane == 0) s_zbase = hcur;
-                __syncwarp();
-            }
-        }
-        if (tid == 0) s_c.t0 = clock64();
-        // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
-        // worth b ~ 64 labels: two per thread (C = 2 blockDim) when that
-        // exceeds blockDim, else one per thread for the first C threads (C a
-        // power of two >= 64); m_ema is identical in every thread, so the
-        // choice is uniform and idle warps skip the labels whole
-        const float want = sqrtf(128.0f * s_c.m_ema);
-        unsigned C;
-        if (want > (float)kThreads) {
-            C = 2u * kThreads;
-        } else {
-            C = 64;
-            while (C < (unsigned)kThreads && (float)C < want) C <<= 1;
-            if (C > (unsigned)kThreads) C = kThreads;
-        }
-        const bool two = C > (unsigned)kThreads;
-        const bool act = (unsigned)tid < C;
-        unsigned long long p = 0;
-        unsigned q = 0, win = 0, kb_hit = 0;
-        bool found = false;
-        while (!found) {
-            ++p;
-            const PhiloxPrefix PP =
-                philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
-            for (unsigned kb = 0; kb < M; kb += C) {
-                const unsigned k0 = kb + (unsigned)tid, k1 = k0 + (unsigned)kThreads;
-                const bool v0 = k0 < M, v1 = two && k1 < M;
-                Prop p0{}, p1{};
-                double dE0 = 0.0, dE1 = 0.0;
-                bool acc0 = false, acc1 = false;
-                if (act) {
-                    p0 = propose<kPow2>(S, k0, PP, key0, key1, L, log2L, (unsigned)N, magic,
-                                        thr_last, v0);
-                    if (two)
-                        p1 = propose<kPow2>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
-                                            thr_last, v1);
-                    if (a.toy) {
-                        const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
-                        const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
-                        acc0 = v0 && u0 < a.toy_A0;
-                        acc1 = v1 && u1 < a.toy_A0;
-                    } else if (sizeof(Real) == 4 && two) {
-                        accept2_f32(S, p0, p1, T, invTf, acc0, acc1, dE0, dE1);
-                    } else {
-                        if (p0.theta) acc0 = accept<Real>(S, p0, T, invTf, dE0);
-                        if (p1.theta) acc1 = accept<Real>(S, p1, T, invTf, dE1);
-                    }
-                }
-                const int any = __syncthreads_or(acc0 || acc1);
-                if (any) {
-                    const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
-                    const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
-                    unsigned off = 0xffffffffu;
-                    if (b0) {
-                        const int first = __ffs(b0) - 1;
-                        off = (unsigned)(warp * 32 + first);
-                        if (lane == first) {
-                            s_cand[warp].i = p0.i;
-                            s_cand[warp].j = p0.j;
-                            s_cand[warp].dxy = p0.dxy;
-                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p0, dE0);
-                        }
-                    } else if (b1) {
-                        const int first = __ffs(b1) - 1;
-                        off = (unsigned)(kThreads + warp * 32 + first);
-                        if (lane == first) {
-                            s_cand[warp].i = p1.i;
-                            s_cand[warp].j = p1.j;
-                            s_cand[warp].dxy = p1.dxy;
-                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p1, dE1);
-                        }
-                    }
-                    if (lane == 0) s_wlabel[warp] = off;
-                    __syncthreads();
-                    unsigned wl = (lane < kThreads / 32) ? s_wlabel[lane] : 0xffffffffu;
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-                    q = kb + wl + 1;                 // 1-based label in the round
-                    kb_hit = kb;
-                    win = (wl >= (unsigned)kThreads ? wl - (unsigned)kThreads : wl) >> 5;
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) {
-                if (tid == 0) {
-                    s_c.attempts += M;
-                    s_c.evaluated += M;
-                }
-                rounds += 1;
-                // bounded hop: thread 0 reads its SM's cycle counter (the limit
-                // is in cycles at the peak clock), the block-wide OR makes the
-                // decision uniform
-                const int late = __syncthreads_or(
-                    tid == 0 && (unsigned long long)(clock64() - s_c.t0) > a.hop_timeout_cyc);
-                if (late) {
-                    status = CG_ETIMEOUT;
-                    break;
-                }
-                if (p >= a.max_rounds) {
-                    status = CG_ESTUCK;
-                    break;
-                }
-            }
-        }
-        if (!found) break;
-
-        // ---- commit (step 3a, 3c) ----
-        const Cand c = s_cand[win];
-        const unsigned ci = c.i, cj = c.j;
-        const int cdx = (int)(short)(c.dxy & 0xffff), cdy = c.dxy >> 16;
-        long long t1 = 0;
-        if (tid == 0) {
-            const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
-            if (kTime)           // step 3c: Gaussian dt of hop number s_c.hops
-                s_c.time = d_add(s_c.time, cg_time_increment(Rg.Gamma, m_hop,
-                                                            s_z[s_c.hops - s_zbase]));
-            s_c.m_ema = 0.9f * s_c.m_ema + 0.1f * (float)m_hop;
-            s_c.attempts += q;
-            // the chunks of the hop's round up to the accepting one
-            s_c.evaluated += (kb_hit + C < M) ? (kb_hit + C) : M;
-            s_c.hops += 1;
-            if (!a.toy) {
-                s_c.P += cdx;
-                s_c.energy = d_add(s_c.energy, c.dE);
-            }
-            if (s_c.tracing)
-                trace_hop(Rg, s_c.attempts, s_c.hops, s_c.P, s_c.energy, kTime ? 1 : 0, s_c.time);
-            t1 = clock64();
-            s_c.cyc_rej += (unsigned long long)(t1 - s_c.t0);
-            if (s_c.log) {
-                cg_hop e;
-                e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
-                e.dx = a.toy ? 0 : cdx; e.dy = a.toy ? 0 : cdy;
-                e.dE = a.toy ? 0.0 : c.dE;
-                s_c.log[a.log_offset + h] = e;
-            }
-            if (!a.toy) {
-                S.occ[ci >> 5] &= ~(1u << (ci & 31));
-                S.occ[cj >> 5] |= (1u << (cj & 31));
-            }
-        }
-        rounds += 1;
-
-        // ---- local-energy update (step 3b) ----
-        // thread -> base column bx < L/2, base rows by0, by0 + rpp, ...
-        const int Lh = L >> 1;
-        const int rpp = kThreads / Lh;
-        if (!a.toy && tid < rpp * Lh) {
-            const int bx = tid % Lh, by0 = tid / Lh;
-            const int yi = kPow2 ? (int)(ci >> log2L) : (int)__umulhi(ci, magic);
-            const int yj = kPow2 ? (int)(cj >> log2L) : (int)__umulhi(cj, magic);
-            const int xi = (int)ci - yi * L, xj = (int)cj - yj * L;
-            const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);
-            // columns of (x, .) and (x + L/2, .) relative to j and to i
-            const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
-            const Real *ci0 = tinv + fxi, *ci1 = tinv + (Lh - fxi);
-            const int LhH1 = Lh * H1, LhL = Lh * L;
-            Real *e = eps + by0 * L + bx;
-#pragma unroll 4
-            for (int y = by0; y < Lh; y += rpp, e += rpp * L) {
-                int fyj, fyi;
-                if (kPow2) {
-                    const int dj = (y - yj) & (L - 1), di = (y - yi) & (L - 1);
-                    fyj = min(dj, L - dj);
-                    fyi = min(di, L - di);
-                } else {
-                    fyj = fold_axis(y - yj, L);
-                    fyi = fold_axis(y - yi, L);
-                }
-                // rows fold(y - .) and L/2 - fold(y - .) = fold(y + L/2 - .)
-                const int oj0 = fyj * H1, oj1 = LhH1 - oj0;
-                const int oi0 = fyi * H1, oi1 = LhH1 - oi0;
-                const Real a00 = cj0[oj0], b00 = ci0[oi0];
-                const Real a10 = cj1[oj0], b10 = ci1[oi0];
-                const Real a01 = cj0[oj1], b01 = ci0[oi1];
-                const Real a11 = cj1[oj1], b11 = ci1[oi1];
-                e[0] = Prec<Real>::add(e[0], Prec<Real>::sub(a00, b00));
-                e[Lh] = Prec<Real>::add(e[Lh], Prec<Real>::sub(a10, b10));
-                e[LhL] = Prec<Real>::add(e[LhL], Prec<Real>::sub(a01, b01));
-                e[LhL + Lh] = Prec<Real>::add(e[LhL + Lh], Prec<Real>::sub(a11, b11));
-            }
-        }
-        __syncthreads();
-        if (tid == 0) s_c.cyc_upd += (unsigned long long)(clock64() - t1);
-    }
-
-    // ---- store the replica back ----
-    {
-        Real *eps_g = reinterpret_cast<Real *>(Rg.eps);
-        for (int l = tid; l < N; l += kThreads) eps_g[l] = eps[l];
-        for (int l = tid; l < words; l += kThreads) Rg.occ[l] = S.occ[l];
-    }
-    if (tid == 0) {
-        DevCounters *cnt = Rg.ctr;
-        cnt->rounds = rounds;
-        cnt->hops = s_c.hops;
-        cnt->attempts = s_c.attempts;
-        cnt->evaluated = s_c.evaluated;
-        cnt->P = s_c.P;
-        cnt->energy = s_c.energy;
-        cnt->time = s_c.time;
-        cnt->cycles_reject += s_c.cyc_rej;
-        cnt->cycles_update += s_c.cyc_upd;
-        cnt->m_ema = s_c.m_ema;
-        cnt->status = status;
-    }
-}
 
 template <typename Real, int kThreads, bool kTime>
 static void launch_tt(const DevReplica *d_reps, const int *d_index, int n_ctas, int smem_bytes,
@@ -430,14 +76,19 @@ static cudaError_t set_smem_t(int bytes)
 
 cudaError_t set_pr_smem_limit(int precision, int bytes)
 {
-    return precision == CG_FP64 ? set_smem_t<double>(bytes) : set_smem_t<float>(bytes);
+    const cudaError_t e =
+        precision == CG_FP64 ? set_smem_t<double>(bytes) : set_smem_t<float>(bytes);
+    return e ? e : set_pr3_smem_limit(precision, bytes);
 }
 
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const int *d_index,
                                  int n_ctas, int threads, int smem_bytes, const RunArgs &args,
-                                 cudaStream_t st, int L)
+                                 cudaStream_t st, int L, int dim)
 {
     if (threads < L / 2) return cudaErrorInvalidValue;     // the update needs L/2 columns
+    if (dim == 3)
+        return launch_pr_persistent3(precision, d_reps, d_index, n_ctas, threads, smem_bytes,
+                                     args, st, L);
     if (precision == CG_FP64) {
         switch (threads) {
         case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);

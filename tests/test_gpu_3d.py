@@ -1,0 +1,149 @@
+"""GPU checks of the cubic lattice (cg_replica_desc.dim = 3; the
+three-dimensional extension of the lattice model named in the paper's
+conclusions) against the serial oracle on the L x L x L torus.
+
+In binary64 the initial state, every logged hop and the final state are
+bit-identical to the oracle's for powers of two and other even L, with and
+without a field; the tower sampler on cubic tables equals the oracle's; a
+batch that mixes square and cubic replicas keeps each chain exact; the
+stochastic clock of step 3c is exact in 3D too; in binary32 (refreshed in
+binary64) eps stays within 1e-4 of its definition.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_5026_gb300 import build, binding
+    build.build()
+    binding.load()
+    return binding
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.uint64)
+
+
+def _oracle_for(p):
+    ch = oracle.Chain(p["L"], nu=p["nu"], W=p["W"], xi=p["xi"], r_max=p["r_max"], T=p["T"],
+                      E=p["E"], seed=p["seed"], replica=p.get("replica", 0),
+                      dim=p.get("dim", 2))
+    return ch
+
+
+def _cubic(**kw):
+    p = dict(nu=0.5, W=1.0, xi=1.0, T=0.1, E=0.01, seed=5, replica=0, dim=3)
+    p.update(kw)
+    return p
+
+
+def _assert_same(B, s, k, p, ch, log=None, olog=None):
+    if log is not None:
+        for f in ("i", "j", "q", "p", "round", "dx", "dy"):
+            np.testing.assert_array_equal(log[f], olog[f], err_msg=f)
+        np.testing.assert_array_equal(_bits(log["dE"]), _bits(olog["dE"]))
+    n, eps, phi, cnt = s.state(k)
+    on, oeps, ophi = ch.state()
+    np.testing.assert_array_equal(n, on)
+    np.testing.assert_array_equal(_bits(phi), _bits(ophi))
+    np.testing.assert_array_equal(_bits(eps), _bits(oeps))
+    oc = ch.counters()
+    for f in ("rounds", "hops", "attempts", "P"):
+        assert cnt[f] == oc[f], f
+    assert abs(cnt["energy"] - oc["energy"]) <= 1e-9 * max(1.0, abs(oc["energy"]))
+
+
+@pytest.mark.parametrize("L,r_max", [(8, 2), (6, 2), (10, 3), (16, 3)])
+def test_initial_state_bit_exact(B, L, r_max):
+    p = _cubic(L=L, r_max=r_max)
+    s = B.System([p], precision=B.CG_FP64)
+    try:
+        assert B.cg_num_sites(s.h, 0) == L ** 3
+        _assert_same(B, s, 0, p, _oracle_for(p))
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("L,r_max,T,E,M", [(8, 2, 0.1, 0.01, 256), (6, 2, 0.05, 0.0, 64),
+                                           (10, 3, 0.2, 0.05, 500), (16, 3, 0.05, 0.02, 1024)])
+def test_cubic_trajectory_bit_exact(B, L, r_max, T, E, M):
+    p = _cubic(L=L, r_max=r_max, T=T, E=E)
+    s = B.System([p], precision=B.CG_FP64)
+    try:
+        rc, log = s.run_logged(1500, M)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p)
+        _, olog = ch.run(1500, M, log=True)
+        _assert_same(B, s, 0, p, ch, log[0], olog)
+    finally:
+        s.close()
+
+
+def test_tower_on_cubic_tables(B):
+    p = _cubic(L=16, r_max=4, xi=1.5)
+    s = B.System([p], precision=B.CG_FP64)
+    try:
+        ch = _oracle_for(p)
+        _, _, Wi, _ = ch.vectors()
+        C = np.cumsum(Wi.astype(np.uint64)).astype(np.int64)
+        x1 = np.concatenate([C - 1, C, C + 1,
+                             np.random.default_rng(2).integers(0, 1 << 32, 200000)])
+        x1 = x1[(x1 >= 0) & (x1 < (1 << 32))].astype(np.uint32)
+        np.testing.assert_array_equal(B.cg_debug_tower(s.h, 0, x1), ch.tower(x1))
+    finally:
+        s.close()
+
+
+def test_batch_mixing_square_and_cubic_replicas(B):
+    reps = [dict(L=16, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.01, seed=1, replica=0),
+            _cubic(L=8, r_max=2, seed=2, replica=1),
+            dict(L=8, nu=0.5, W=1.0, xi=1.0, r_max=3, T=0.05, E=0.01, seed=3, replica=2),
+            _cubic(L=8, r_max=2, seed=4, replica=3, T=0.3)]
+    s = B.System(reps, precision=B.CG_FP64, use_graph=1)
+    try:
+        assert B.cg_num_groups(s.h) == 3          # (2D, 8), (2D, 16), (3D, 8)
+        rc, log = s.run_logged(700, 300)
+        assert rc == B.CG_OK
+        for k, p in enumerate(reps):
+            ch = _oracle_for(p)
+            _, olog = ch.run(700, 300, log=True)
+            _assert_same(B, s, k, p, ch, log[k], olog)
+    finally:
+        s.close()
+
+
+def test_cubic_stochastic_clock_bit_exact(B):
+    p = _cubic(L=8, r_max=2)
+    s = B.System([p], precision=B.CG_FP64, time_mode=B.CG_TIME_GAUSSIAN)
+    try:
+        s.run(1000, 256)
+        ch = _oracle_for(p)
+        ch.set_time_mode(1)
+        ch.run(1000, 256)
+        assert s.state(0)[3]["time"] == ch.counters()["time"]
+    finally:
+        s.close()
+
+
+def test_cubic_binary32_with_binary64_refresh(B):
+    reps = [_cubic(L=16, r_max=3, T=0.05, seed=s, replica=s) for s in range(6)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=256)
+    try:
+        s.run(2000, 512)
+        for k in range(6):
+            o = s.observables(k)
+            assert o["refreshes"] >= 7 and o["max_eps_err_last_refresh"] <= 1e-4
+            n, eps, phi, _ = s.state(k)
+            ch = _oracle_for(reps[k])
+            ch.set_state(n, phi)
+            assert np.max(np.abs(eps - ch.state()[1])) <= 1e-4
+    finally:
+        s.close()
