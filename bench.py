@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # workload (304 replicas x 1024 hops), from the ncu capture summarised in
 # profiles/pr_persistent_fp32_L128_R304_relaxed.md; valid only while the
 # kernel sources hash to the captured version.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "bb72bd921f7ac59b", "bytes_per_launch": 20.715e6,
+TRAFFIC_CAPTURE = {"sources_sha256_16": "acea4e505e5a977d", "bytes_per_launch": 20.717e6,
                    "replicas": 304, "hops_per_replica": 1024}
 
 
@@ -544,19 +544,21 @@ def shape_of(B, h, g, tuned):
 
 
 def other_configs(args, B, local):
-    """Throughput of the two other batch configurations: 256 replicas with L
+    """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
     replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
-    tensor-core refresh per same-L group every 1024 hops), and 16 replicas of
+    tensor-core refresh per same-L group every 1024 hops), 16 replicas of
     L=256 whose eps is split over a thread-block cluster (refresh every 4096
-    hops).  Each is timed with CUDA events over hops that follow a relaxation
-    from the random start."""
+    hops), and 152 replicas of the 32 x 32 x 32 cubic lattice (binary64
+    refresh every 1024 hops).  Each is timed with CUDA events over hops that
+    follow a relaxation from the random start."""
     import torch
     from paper_1407_5026_gb300 import workloads as W
     out = {}
     for name, wl, relax, hops, graph, tune in (
             ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
-            ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, False)):
+            ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, False),
+            ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False)):
         reps = [r.as_dict() for r in wl.replicas]
         s = B.System(reps, precision=B.CG_FP32, refresh_every=wl.refresh_every,
                      use_graph=graph, device=local)

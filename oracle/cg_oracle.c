@@ -77,7 +77,8 @@
  * Geometry is a general Lx x Ly x Lz torus (Ly = Lz = 1 gives a ring, Lz = 1
  * the square lattice, Lx = Ly = Lz the cubic lattice of the 3D extension) so
  * that tiny
- * systems can be enumerated exactly; the library itself only builds L x L.
+ * systems can be enumerated exactly; the library itself builds L x L and
+ * L x L x L.
  */
 #include <math.h>
 #include <stdint.h>

@@ -158,14 +158,20 @@ cudaError_t set_pr_smem_limit(int precision, int bytes);
 int microbench(int kind, int device, double *result);
 cudaError_t launch_reset_refresh_err(const DevReplica *d_reps, const int *d_index, int R,
                                      cudaStream_t st);
-// Tensor-core refresh of R <= 512 binary32 replicas of one L (L*L % 128 == 0).
-// d_scratch: refresh_tc_scratch_bytes(L, R) bytes (the S image and the K-split
-// partial sums), 256-byte aligned.
+// log2 of the factor applied to 1/r before its binary16 split (cubic lattice)
+constexpr int kTcF16Log2Scale = 10;
+
+// Tensor-core refresh of R <= 512 binary32 replicas of one L and dimension
+// (dim 2: N = L^2, dim 3: N = L^3; N % 128 == 0).  d_tab: the folded table's
+// two-term split (H1^dim entries; BF16 of 1/r for dim 2, binary16 of
+// 2^kTcF16Log2Scale / r for dim 3).  d_scratch: refresh_tc_scratch_bytes(N, R)
+// bytes (the S image and the K-split partial sums), 256-byte aligned.
 cudaError_t launch_refresh_tc(const DevReplica *d_reps, const int *d_index, int R, int L,
-                              const uint32_t *d_tab, unsigned char *d_scratch, int *d_err,
-                              cudaStream_t st);
-int refresh_tc_smem_bytes(int R_pad, int H1);
-int refresh_tc_ksplit(int L);
-size_t refresh_tc_scratch_bytes(int L, int R);
+                              int dim, const uint32_t *d_tab, unsigned char *d_scratch,
+                              int *d_err, cudaStream_t st);
+int refresh_tc_smem_bytes(int R_pad, int tab_entries);
+int refresh_tc_ksplit(int N, int dim);
+int refresh_tc_max_replicas(int dim);   // replicas per launch
+size_t refresh_tc_scratch_bytes(int N, int dim, int R);
 
 }  // namespace cg

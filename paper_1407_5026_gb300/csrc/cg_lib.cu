@@ -81,6 +81,30 @@ float bf16_to_float(uint32_t h)
     return f;
 }
 
+// Round-to-nearest-even of a finite double with |v| < 65520 to IEEE binary16
+// bits (subnormals included), and back.
+uint32_t f16_rne(double v)
+{
+    const uint32_t sign = v < 0 ? 0x8000u : 0u;
+    const double a = std::fabs(v);
+    if (a == 0.0) return sign;
+    int e;
+    std::frexp(a, &e);                         // a = m 2^e, m in [1/2, 1)
+    int E = e - 1 < -14 ? -14 : e - 1;         // binade; below 2^-14 the subnormal spacing
+    double k = std::nearbyint(std::ldexp(a, 10 - E));   // units of 2^(E-10), ties to even
+    if (k >= 2048.0) { k = 1024.0; E += 1; }   // rounded up into the next binade
+    const uint32_t bits = k < 1024.0 ? (uint32_t)k
+                                     : ((uint32_t)(E + 15) << 10) | ((uint32_t)k - 1024u);
+    return sign | bits;
+}
+
+double f16_to_double(uint32_t h)
+{
+    const int ex = (int)((h >> 10) & 31u), man = (int)(h & 1023u);
+    const double v = ex == 0 ? std::ldexp((double)man, -24) : std::ldexp((double)(man + 1024), ex - 25);
+    return (h & 0x8000u) ? -v : v;
+}
+
 struct Tables {
     int L = 0, r_max = 0, H1 = 0, V = 0;
     double xi = 0, Z = 0, C0 = 0;
@@ -91,7 +115,8 @@ struct Tables {
     std::vector<int> disp;
     std::vector<double> tinvd;
     std::vector<unsigned short> guide;
-    std::vector<uint32_t> split;      // BF16 hi | lo << 16 of each 1/r entry
+    std::vector<uint32_t> split;      // hi | lo << 16 of each 1/r entry: BF16 of 1/r on the
+                                      // square lattice, binary16 of 2^10 / r on the cubic one
     unsigned short *d_guide = nullptr;
     uint32_t *d_split = nullptr;
     double *d_t64 = nullptr;
@@ -115,14 +140,26 @@ int build_tables(Tables &t, int L, double xi, int r_max, int dim)
                         ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy + fz * fz));
     t.t32.resize(t.t64.size());
     for (size_t k = 0; k < t.t64.size(); ++k) t.t32[k] = (float)t.t64[k];
-    // two-term BF16 split of 1/r for the tensor-core refresh: hi = bf16(T),
-    // lo = bf16(T - hi), so T - hi - lo is below 2^-16 of T
+    // two-term split of 1/r for the tensor-core refresh.  Square lattice:
+    // hi = bf16(T), lo = bf16(T - hi), so T - hi - lo is below 2^-16 of T.
+    // Cubic lattice, where sum_t G_st^2 is about eight times larger and that
+    // residual would reach 1e-4 on eps at L = 32: binary16 terms of
+    // T' = 2^10 T (hi = f16(T'), lo = f16(T' - hi), residual below 2^-21 of
+    // T'; the scale keeps lo out of the subnormal range), undone in binary64
+    // after the contraction.
     t.split.resize(t.t64.size());
     for (size_t k = 0; k < t.t64.size(); ++k) {
-        const uint32_t hi = bf16_rne((float)t.t64[k]);
-        const double rest = t.t64[k] - (double)bf16_to_float(hi);
-        const uint32_t lo = bf16_rne((float)rest);
-        t.split[k] = hi | (lo << 16);
+        if (dim == 3) {
+            const double Ts = std::ldexp(t.t64[k], kTcF16Log2Scale);
+            const uint32_t hi = f16_rne(Ts);
+            const uint32_t lo = f16_rne(Ts - f16_to_double(hi));
+            t.split[k] = hi | (lo << 16);
+        } else {
+            const uint32_t hi = bf16_rne((float)t.t64[k]);
+            const double rest = t.t64[k] - (double)bf16_to_float(hi);
+            const uint32_t lo = bf16_rne((float)rest);
+            t.split[k] = hi | (lo << 16);
+        }
     }
     // sum_{t != s} 1/r_st is the same for every s: every displacement once
     double C0 = 0.0;
@@ -206,21 +243,30 @@ struct Group {
     int *d_err = nullptr;            // its error word
 };
 
-constexpr int kTcMaxReplicas = 512;  // TMEM columns of one accumulator
+// dynamic shared memory the contraction may take: the 227 KiB per-CTA opt-in
+// of sm_100-class GPUs less 1 KiB for its static barriers
+constexpr int kTcSmemLimit = 227 * 1024 - 1024;
 
-// Whether a group of `count` binary32 replicas of side L refreshes on the
-// tensor cores (it needs L*L to be a multiple of 128).
+// Whether a group of `count` binary32 replicas of side L and dimension dim
+// refreshes on the tensor cores: the site count must be a multiple of 128 and
+// the contraction's stages plus the folded table must fit one CTA's shared
+// memory.
 bool group_uses_tc(const cg_opts &o, int L, int count, int dim)
 {
-    if (o.precision != CG_FP32 || dim == 3 || (L * L) % 128 != 0) return false;
+    const long long N = dim == 3 ? (long long)L * L * L : (long long)L * L;
+    const int H1 = L / 2 + 1, tab = dim == 3 ? H1 * H1 * H1 : H1 * H1;
+    const int R_pad = (std::min(count, refresh_tc_max_replicas(dim)) + 15) / 16 * 16;
+    if (o.precision != CG_FP32 || N % 128 != 0) return false;
+    if (refresh_tc_smem_bytes(R_pad, tab) > kTcSmemLimit) return false;
     if (o.refresh_kind == CG_REFRESH_BF16X2) return true;
     if (o.refresh_kind == CG_REFRESH_AUTO) return count >= 8;
     return false;
 }
 
-size_t tc_img_bytes(int L, int count)
+size_t tc_img_bytes(int L, int dim, int count)
 {
-    return refresh_tc_scratch_bytes(L, std::min(count, kTcMaxReplicas));
+    const int N = dim == 3 ? L * L * L : L * L;
+    return refresh_tc_scratch_bytes(N, dim, std::min(count, refresh_tc_max_replicas(dim)));
 }
 
 }  // namespace
@@ -503,7 +549,8 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
     size_t tc_total = 0;
     for (auto &g : groups)
         if (group_uses_tc(o, std::get<0>(g), std::get<2>(g), std::get<1>(g)))
-            tc_total += up(tc_img_bytes(std::get<0>(g), std::get<2>(g))) + up(sizeof(int));
+            tc_total += up(tc_img_bytes(std::get<0>(g), std::get<1>(g), std::get<2>(g))) +
+                        up(sizeof(int));
     size_t total = up(sizeof(DevReplica) * (size_t)R) + up(sizeof(int) * (size_t)R);
     std::vector<std::tuple<int, int, double, int>> seen;
     for (int k = 0; k < R; ++k) {
@@ -687,7 +734,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             while (g.threads < g.L && g.threads < 1024) g.threads *= 2;
         }
         g.tc = group_uses_tc(o, g.L, g.count, g.dim);
-        if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.count)) ||
+        if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.dim, g.count)) ||
                      dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
             destroy_partial();
             return nullptr;
@@ -760,9 +807,10 @@ int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
     CG_CUDA(launch_reset_refresh_err(h->d_reps, h->d_index + g.first, g.count, st));
     if (g.tc) {
         const uint32_t *split = h->reps[h->order[g.first]].tab->d_split;
-        for (int c0 = 0; c0 < g.count; c0 += kTcMaxReplicas) {
-            const int n = std::min(kTcMaxReplicas, g.count - c0);
-            CG_CUDA(launch_refresh_tc(h->d_reps, h->d_index + g.first + c0, n, g.L, split,
+        const int per = refresh_tc_max_replicas(g.dim);
+        for (int c0 = 0; c0 < g.count; c0 += per) {
+            const int n = std::min(per, g.count - c0);
+            CG_CUDA(launch_refresh_tc(h->d_reps, h->d_index + g.first + c0, n, g.L, g.dim, split,
                                       g.d_img, g.d_err, st));
         }
     } else {

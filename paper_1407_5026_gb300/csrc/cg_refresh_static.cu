@@ -127,7 +127,7 @@ size_t noalloc_scratch_bytes(int L, int R)
     const size_t H1 = L / 2 + 1;
     return up256(sizeof(DevReplica) * R) + up256(sizeof(int) * R) +
            up256(sizeof(DevCounters) * R) + up256(H1 * H1 * 4) + up256(sizeof(int)) +
-           refresh_tc_scratch_bytes(L, R);
+           refresh_tc_scratch_bytes(L * L, 2, R);
 }
 
 }  // namespace cg
@@ -200,7 +200,8 @@ extern "C" int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int
                                                          C0, occ, phi, eps);
     static_split_table_kernel<<<(H1 * H1 + 255) / 256, 256, 0, st>>>(d_tab, L);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_refresh_tc(d_reps, d_index, R, L, d_tab, d_scratch, d_err, st);
+    if (e == cudaSuccess)
+        e = launch_refresh_tc(d_reps, d_index, R, L, 2, d_tab, d_scratch, d_err, st);
     if (e == cudaSuccess && max_err) {
         static_err_out_kernel<<<(R + 127) / 128, 128, 0, st>>>(d_ctr, max_err, R);
         e = cudaGetLastError();

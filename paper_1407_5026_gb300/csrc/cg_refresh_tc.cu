@@ -8,11 +8,16 @@
 // and for R replicas of one L the matrix S has R columns, so D = G S is an
 // (N x N) x (N x R) product.  G is split as G_hi + G_lo (two BF16 terms,
 // residual ~2^-17 |G|) and both products accumulate in FP32 in tensor memory.
+// On the cubic lattice, where sum_t G_st^2 is about eight times larger, the
+// split is instead two binary16 terms of 2^10 G (residual ~2^-22 |G|), with S
+// in binary16 too; the reduction undoes the scale in binary64.
 //
 // Kernel layout (one CTA per 128 sites, 288 threads):
 //   warps 0-7  generate the 128 x 64 tiles of G_hi and G_lo for each K-block
 //              from the folded 1/r table into 128B-swizzled shared memory
-//              (G is never stored), then run the epilogue;
+//              (G is never stored), then run the epilogue; on the cubic
+//              lattice (kDim = 3) the table is (L/2+1)^3 and a site decodes
+//              to (x, y, z);
 //   warp 8     bulk-copies the K-block of S (a pre-swizzled BF16 image built
 //              by pack_s_kernel) with cp.async.bulk and, from one lane,
 //              issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128,
@@ -20,6 +25,8 @@
 // Two pipeline stages; every mbarrier wait is bounded in time and on expiry
 // sets an error word, stops the CTA's loops, waits for its own MMAs and frees
 // its tensor memory before returning.
+#include <cmath>
+
 #include "cg_device.cuh"
 #include "cg_internal.h"
 
@@ -183,13 +190,21 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with A and B in binary16 (format 0): FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 }  // namespace tc
 
 // S image: for K-block kb (64 sites) and replica row r, 128 bytes holding
-// S_t = 2 n_t - 1 as BF16 for t = 64 kb ... 64 kb + 63, 16-byte chunk c stored
-// at chunk c ^ (r & 7) (the 128-byte swizzle); rows r >= R are zero.
+// S_t = 2 n_t - 1 (one = the 16-bit pattern of +1: BF16 0x3f80 or binary16
+// 0x3c00; -1 adds the sign bit) for t = 64 kb ... 64 kb + 63, 16-byte chunk c
+// stored at chunk c ^ (r & 7) (the 128-byte swizzle); rows r >= R are zero.
 __global__ void pack_s_kernel(const DevReplica *__restrict__ reps, const int *__restrict__ index,
-                              int R, int R_pad, int kblocks, unsigned char *__restrict__ img)
+                              int R, int R_pad, int kblocks, uint32_t one,
+                              unsigned char *__restrict__ img)
 {
     const long long total = (long long)kblocks * R_pad * 8;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
@@ -205,8 +220,8 @@ __global__ void pack_s_kernel(const DevReplica *__restrict__ reps, const int *__
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t lo = ((bits >> (2 * e)) & 1u) ? 0x3f80u : 0xbf80u;
-                const uint32_t hi = ((bits >> (2 * e + 1)) & 1u) ? 0x3f80u : 0xbf80u;
+                const uint32_t lo = ((bits >> (2 * e)) & 1u) ? one : (one | 0x8000u);
+                const uint32_t hi = ((bits >> (2 * e + 1)) & 1u) ? one : (one | 0x8000u);
                 w[e] = lo | (hi << 16);
             }
             out = make_uint4(w[0], w[1], w[2], w[3]);
@@ -223,14 +238,17 @@ struct TcArgs {
     int R, R_pad, n0, n1;    // n0 + n1 = R_pad, each a multiple of 16, n0 <= 256
     int L, N, H1, kblocks;
     int kb_per;              // K-blocks per CTA (the K range is split over gridDim.y)
+    int tab_entries;         // H1^2 (square lattice) or H1^3 (cubic lattice)
+    int lo_off;              // TMEM column of the G_lo accumulator (0: shared with G_hi)
     unsigned magicL;
     uint32_t tmem_cols;
-    const uint32_t *tab;     // H1*H1 entries: BF16 hi | BF16 lo << 16 of 1/r
+    const uint32_t *tab;     // folded table: BF16 hi | BF16 lo << 16 of 1/r
     const unsigned char *img;
     float *part;             // gridDim.y x R_pad x N partial sums of D
     int *err;                // set nonzero when a bounded wait expired
 };
 
+template <int kDim>
 __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
 {
     using namespace tc;
@@ -260,7 +278,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
         fence_barrier_init();
     }
     if (warp == 0) tmem_alloc(&s_tmem, a.tmem_cols);
-    for (int l = tid; l < a.H1 * a.H1; l += tc::kThreads) tab[l] = a.tab[l];
+    for (int l = tid; l < a.tab_entries; l += tc::kThreads) tab[l] = a.tab[l];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -275,7 +293,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
         // ---- G tile generators: thread -> row (site s), half of the 8 chunks ----
         const int row = tid & 127, half = tid >> 7;
         const int s = m0 + row;
-        const int ys = (int)__umulhi((unsigned)s, a.magicL), xs = s - ys * L;
+        int xs, ys, zs = 0;
+        if (kDim == 3) {
+            const unsigned q = __umulhi((unsigned)s, a.magicL);    // s / L
+            xs = s - (int)q * L;
+            zs = (int)__umulhi(q, a.magicL);                      // s / L^2
+            ys = (int)q - zs * L;
+        } else {
+            ys = (int)__umulhi((unsigned)s, a.magicL);
+            xs = s - ys * L;
+        }
         for (int kk = 0; kk < a.kb_per; ++kk) {
             const int kb = kb0 + kk;
             const int st = kk % kStages, use = kk / kStages;
@@ -295,8 +322,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int t = kb * 64 + c * 8 + 2 * e + h;
-                        const int yt = (int)__umulhi((unsigned)t, a.magicL), xt = t - yt * L;
-                        v2[h] = tab[fold_axis(ys - yt, L) * H1 + fold_axis(xs - xt, L)];
+                        if (kDim == 3) {
+                            const unsigned q = __umulhi((unsigned)t, a.magicL);
+                            const int xt = t - (int)q * L, zt = (int)__umulhi(q, a.magicL);
+                            const int yt = (int)q - zt * L;
+                            v2[h] = tab[(fold_axis(zs - zt, L) * H1 + fold_axis(ys - yt, L)) * H1 +
+                                        fold_axis(xs - xt, L)];
+                        } else {
+                            const int yt = (int)__umulhi((unsigned)t, a.magicL), xt = t - yt * L;
+                            v2[h] = tab[fold_axis(ys - yt, L) * H1 + fold_axis(xs - xt, L)];
+                        }
                     }
                     whi[e] = (v2[0] & 0xffffu) | (v2[1] << 16);
                     wlo[e] = (v2[0] >> 16) | (v2[1] & 0xffff0000u);
@@ -310,8 +345,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
         }
     } else if (lane == 0) {
         // ---- S loader and MMA issuer ----
-        const uint32_t id0 = idesc_bf16(128, a.n0);
-        const uint32_t id1 = a.n1 ? idesc_bf16(128, a.n1) : 0u;
+        // both operands in one format: BF16 (square lattice) or binary16 (cubic)
+        const uint32_t id0 = kDim == 3 ? idesc_f16(128, a.n0) : idesc_bf16(128, a.n0);
+        const uint32_t id1 = a.n1 ? (kDim == 3 ? idesc_f16(128, a.n1) : idesc_bf16(128, a.n1))
+                                  : 0u;
         for (int kk = 0; kk < a.kb_per; ++kk) {
             const int kb = kb0 + kk;
             const int st = kk % kStages, use = kk / kStages;
@@ -331,15 +368,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
             tc_fence_after();
             const uint32_t ahi = smem_u32(stage), alo = ahi + kTileBytes, b = smem_u32(bsm);
 #pragma unroll
+            // G_lo products go to their own accumulator when lo_off > 0, which
+            // halves the adds into each (the accumulation error grows with
+            // their count)
+            const uint32_t tlo = tmem + (uint32_t)a.lo_off;
             for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t koff = ks * 32;    // 16 BF16 along K
+                const uint32_t koff = ks * 32;    // 16 elements along K
                 const uint32_t acc = (kk > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc_lo = a.lo_off ? acc : 1u;
                 mma_bf16(tmem, sw128_desc(ahi + koff), sw128_desc(b + koff), id0, acc);
-                mma_bf16(tmem, sw128_desc(alo + koff), sw128_desc(b + koff), id0, 1u);
+                mma_bf16(tlo, sw128_desc(alo + koff), sw128_desc(b + koff), id0, acc_lo);
                 if (a.n1) {
                     const uint32_t b1 = b + a.n0 * 128;
                     mma_bf16(tmem + a.n0, sw128_desc(ahi + koff), sw128_desc(b1 + koff), id1, acc);
-                    mma_bf16(tmem + a.n0, sw128_desc(alo + koff), sw128_desc(b1 + koff), id1, 1u);
+                    mma_bf16(tlo + a.n0, sw128_desc(alo + koff), sw128_desc(b1 + koff), id1, acc_lo);
                 }
             }
             mma_commit(&empty[st]);
@@ -358,6 +400,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
         for (int c = (warp >> 2); c * 16 < a.R_pad; c += 2) {
             uint32_t v[16];
             tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(c * 16), v);
+            if (a.lo_off) {
+                uint32_t w[16];
+                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(a.lo_off + c * 16), w);
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(w[e]));
+            }
 #pragma unroll
             for (int e = 0; e < 16; ++e)
                 part[(size_t)(c * 16 + e) * a.N + s] = __uint_as_float(v[e]);
@@ -373,11 +422,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) refresh_tc_kernel(TcArgs a)
 }
 
 // D = sum of the K-split partials in binary64, then eps = phi + D/2 +
-// (1/2 - nu) C0 for replica blockIdx.y; the largest |eps_old - eps_new| of the
-// replica goes to its counters.
+// (1/2 - nu) C0 for replica blockIdx.y (half = 1/2, or 2^-11 when the
+// contraction ran on 2^10 / r); the largest |eps_old - eps_new| of the replica
+// goes to its counters.
 __global__ void __launch_bounds__(256) refresh_tc_reduce_kernel(
     const DevReplica *__restrict__ reps, const int *__restrict__ index, int R_pad, int N,
-    int ksplit, const float *__restrict__ part)
+    int ksplit, double half, const float *__restrict__ part)
 {
     const int r = blockIdx.y;
     const int s = blockIdx.x * 256 + threadIdx.x;
@@ -387,7 +437,7 @@ __global__ void __launch_bounds__(256) refresh_tc_reduce_kernel(
         double D = 0.0;
         for (int y = 0; y < ksplit; ++y) D += (double)part[((size_t)y * R_pad + r) * N + s];
         float *eps = reinterpret_cast<float *>(Rr.eps);
-        const double enew = Rr.phi[s] + (0.5 * D + (0.5 - Rr.nu) * Rr.C0);
+        const double enew = Rr.phi[s] + (half * D + (0.5 - Rr.nu) * Rr.C0);
         err = fabs((double)eps[s] - enew);
         eps[s] = __double2float_rn(enew);
     }
@@ -401,45 +451,61 @@ __global__ void __launch_bounds__(256) refresh_tc_reduce_kernel(
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&Rr.ctr->refreshes, 1ull);
 }
 
-int refresh_tc_smem_bytes(int R_pad, int H1)
+int refresh_tc_smem_bytes(int R_pad, int tab_entries)
 {
-    return 1024 + tc::kStages * (2 * tc::kTileBytes + R_pad * 128) + H1 * H1 * 4;
+    return 1024 + tc::kStages * (2 * tc::kTileBytes + R_pad * 128) + tab_entries * 4;
 }
 
-// K split of the contraction: the largest divisor of the K-block count that is
-// at most max(8, K-blocks / 32), so each CTA's FP32 partial sum covers at most
-// an eighth of the lattice and at most 32 K-blocks (2048 sites) on large ones.
-int refresh_tc_ksplit(int L)
+// K split of the contraction.  Square lattice: the largest divisor of the
+// K-block count that is at most max(8, K-blocks / 32), so each CTA's FP32
+// partial sum covers at most an eighth of the lattice and at most 32 K-blocks
+// (2048 sites) on large ones.  Cubic lattice (larger sums of G^2, so a
+// tighter bound on the accumulation): the smallest divisor that leaves at most
+// 16 K-blocks (1024 sites) per CTA.
+int refresh_tc_ksplit(int N, int dim)
 {
-    const int kblocks = L * L / 64;
+    const int kblocks = N / 64;
+    if (dim == 3) {
+        for (int k = 1; k <= kblocks; ++k)
+            if (kblocks % k == 0 && kblocks / k <= 16) return k;
+        return kblocks;
+    }
     const int cap = kblocks / 32 > 8 ? kblocks / 32 : 8;
     for (int k = cap; k > 1; --k)
         if (kblocks % k == 0) return k;
     return 1;
 }
 
-size_t refresh_tc_scratch_bytes(int L, int R)
+int refresh_tc_max_replicas(int dim)
 {
-    const size_t R_pad = (size_t)(R + 15) / 16 * 16, N = (size_t)L * L;
-    const size_t img = 2 * N * R_pad;
-    const size_t part = (size_t)refresh_tc_ksplit(L) * R_pad * N * 4;
+    return dim == 3 ? 256 : 512;   // TMEM columns: one accumulator, or G_hi and G_lo apart
+}
+
+size_t refresh_tc_scratch_bytes(int N, int dim, int R)
+{
+    const size_t R_pad = (size_t)(R + 15) / 16 * 16;
+    const size_t img = 2 * (size_t)N * R_pad;
+    const size_t part = (size_t)refresh_tc_ksplit(N, dim) * R_pad * (size_t)N * 4;
     return ((img + 255) & ~(size_t)255) + part;
 }
 
 cudaError_t launch_refresh_tc(const DevReplica *d_reps, const int *d_index, int R, int L,
-                              const uint32_t *d_tab, unsigned char *d_scratch, int *d_err,
-                              cudaStream_t st)
+                              int dim, const uint32_t *d_tab, unsigned char *d_scratch,
+                              int *d_err, cudaStream_t st)
 {
-    const int N = L * L, H1 = L / 2 + 1;
+    const int H1 = L / 2 + 1;
+    const int N = dim == 3 ? L * L * L : L * L;
+    const int tab_entries = dim == 3 ? H1 * H1 * H1 : H1 * H1;
     if (N % 128 != 0 || R < 1) return cudaErrorInvalidValue;
     const int R_pad = (R + 15) / 16 * 16;
-    if (R_pad > 512) return cudaErrorInvalidValue;
+    if (R > refresh_tc_max_replicas(dim)) return cudaErrorInvalidValue;
     const int kblocks = N / 64;
-    const int ksplit = refresh_tc_ksplit(L);
+    const int ksplit = refresh_tc_ksplit(N, dim);
     unsigned char *d_img = d_scratch;
     float *d_part = reinterpret_cast<float *>(
         d_scratch + ((2 * (size_t)N * R_pad + 255) & ~(size_t)255));
-    pack_s_kernel<<<2 * 152, 256, 0, st>>>(d_reps, d_index, R, R_pad, kblocks, d_img);
+    pack_s_kernel<<<2 * 152, 256, 0, st>>>(d_reps, d_index, R, R_pad, kblocks,
+                                           dim == 3 ? 0x3c00u : 0x3f80u, d_img);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     TcArgs a;
@@ -454,22 +520,33 @@ cudaError_t launch_refresh_tc(const DevReplica *d_reps, const int *d_index, int 
     a.H1 = H1;
     a.kblocks = kblocks;
     a.kb_per = kblocks / ksplit;
+    a.tab_entries = tab_entries;
+    a.lo_off = dim == 3 ? R_pad : 0;
     a.part = d_part;
     a.magicL = (unsigned)(4294967296ull / (unsigned long long)L + 1ull);
     uint32_t cols = 32;
-    while (cols < (uint32_t)R_pad) cols <<= 1;
+    while (cols < (uint32_t)(R_pad + a.lo_off)) cols <<= 1;
     a.tmem_cols = cols;
     a.tab = d_tab;
     a.img = d_img;
     a.err = d_err;
-    const int smem = refresh_tc_smem_bytes(R_pad, H1);
-    e = cudaFuncSetAttribute(refresh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e) return e;
-    refresh_tc_kernel<<<dim3(N / 128, ksplit), tc::kThreads, smem, st>>>(a);
+    const int smem = refresh_tc_smem_bytes(R_pad, tab_entries);
+    if (dim == 3) {
+        e = cudaFuncSetAttribute(refresh_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e) return e;
+        refresh_tc_kernel<3><<<dim3(N / 128, ksplit), tc::kThreads, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(refresh_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e) return e;
+        refresh_tc_kernel<2><<<dim3(N / 128, ksplit), tc::kThreads, smem, st>>>(a);
+    }
     e = cudaGetLastError();
     if (e) return e;
+    const double half = dim == 3 ? std::ldexp(0.5, -kTcF16Log2Scale) : 0.5;
     refresh_tc_reduce_kernel<<<dim3((N + 255) / 256, R), 256, 0, st>>>(d_reps, d_index, R_pad,
-                                                                     N, ksplit, d_part);
+                                                                     N, ksplit, half, d_part);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ class Replica:
     E: float
     seed: int
     replica: int = 0
+    dim: int = 2      # 2: L x L square lattice; 3: L x L x L cubic lattice
 
     def as_dict(self):
         return asdict(self)
@@ -108,6 +109,17 @@ def l256(R: int = 16, hops: int = 10_000_000) -> Workload:
                          E=0.005, seed=s, replica=s) for s in range(R))
     return Workload(f"L256_T0.02_R{R}", reps, M=16384, hops=hops,
                     precision="fp32", refresh_every=4096)
+
+
+def cubic(R: int = 152, L: int = 32, hops: int = 1_000_000) -> Workload:
+    """The cubic lattice the paper's conclusions name as the next extension:
+    L x L x L sites (N = 32768 for L=32), nu=1/2, phi ~ U[-0.5, 0.5], xi=1,
+    hops inside the ball |d| <= 3 (122 vectors), T=0.05, E=0.01, one replica
+    per SM, FP32 eps with a binary64 refresh every 1024 hops."""
+    reps = tuple(Replica(L=L, nu=0.5, W=1.0, xi=1.0, r_max=3, T=0.05, E=0.01,
+                         seed=s, replica=s, dim=3) for s in range(R))
+    return Workload(f"cubic_L{L}_T0.05_R{R}", reps, M=4096, hops=hops,
+                    precision="fp32", refresh_every=1024)
 
 
 # ---------------------------------------------------------------------------

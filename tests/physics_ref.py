@@ -80,3 +80,15 @@ def coupling_matrix3(Lx, Ly, Lz):
     D = min_image_distance_matrix3(Lx, Ly, Lz)
     with np.errstate(divide="ignore"):
         return np.where(D > 0, 1.0 / np.where(D > 0, D, 1.0), 0.0)
+
+
+def site_energies_fft3(n, phi, nu, L):
+    """eps = phi + G (n - nu) as a circular convolution on the L x L x L torus
+    (site s = (z L + y) L + x), G the minimum-image 1/r with G(0) = 0."""
+    a = np.minimum(np.arange(L), L - np.arange(L)).astype(np.float64)
+    r = np.sqrt(a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2)
+    with np.errstate(divide="ignore"):
+        g = np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), 0.0)
+    s = (n.astype(np.float64) - nu).reshape(L, L, L)
+    conv = np.fft.irfftn(np.fft.rfftn(g) * np.fft.rfftn(s), s=(L, L, L))
+    return phi + conv.reshape(-1)

@@ -7,12 +7,15 @@ bit-identical to the oracle's for powers of two and other even L, with and
 without a field; the tower sampler on cubic tables equals the oracle's; a
 batch that mixes square and cubic replicas keeps each chain exact; the
 stochastic clock of step 3c is exact in 3D too; in binary32 (refreshed in
-binary64) eps stays within 1e-4 of its definition.
+binary64) eps stays within 1e-4 of its definition; the split-BF16 tensor-core
+refresh on cubic tables (N = L^3 a multiple of 128) gives eps within 5e-5 of
+its definition, alone and inside runs.
 """
 import numpy as np
 import pytest
 
 import oracle
+from tests import physics_ref as ref
 
 pytestmark = pytest.mark.gpu
 
@@ -145,5 +148,40 @@ def test_cubic_binary32_with_binary64_refresh(B):
             ch = _oracle_for(reps[k])
             ch.set_state(n, phi)
             assert np.max(np.abs(eps - ch.state()[1])) <= 1e-4
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("L,R", [(8, 9), (16, 40), (24, 17), (32, 152)])
+def test_cubic_tensor_core_refresh_matches_definition(B, L, R):
+    # D = G (2n - 1) with G built from the (L/2+1)^3 folded table on the fly
+    reps = [_cubic(L=L, r_max=3, T=0.05, seed=s, replica=s) for s in range(R)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_kind=B.CG_REFRESH_BF16X2)
+    try:
+        s.run(40, 256)
+        B.cg_refresh(s.h)
+        worst = 0.0
+        for k in sorted({0, 1, R // 2, R - 1}):
+            n, eps, phi, _ = s.state(k)
+            exact = ref.site_energies_fft3(n, phi, 0.5, L)
+            worst = max(worst, float(np.abs(eps - exact).max()))
+            obs = s.observables(k)
+            assert obs["refreshes"] == 1 and obs["max_eps_err_last_refresh"] <= 1e-4
+        assert worst <= 5e-5, worst
+    finally:
+        s.close()
+
+
+def test_cubic_tensor_core_refresh_in_runs(B):
+    # the automatic choice takes the tensor cores for 16 cubic replicas
+    reps = [_cubic(L=16, r_max=3, T=0.03, seed=s, replica=s) for s in range(16)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=256)
+    try:
+        s.run(4 * 256 + 50, 1024)
+        for k in (0, 7, 15):
+            n, eps, phi, _ = s.state(k)
+            assert np.abs(eps - ref.site_energies_fft3(n, phi, 0.5, 16)).max() <= 1e-4
+            o = s.observables(k)
+            assert o["refreshes"] == 4 and o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()

@@ -138,3 +138,14 @@ def test_detailed_balance_two_electrons_on_a_cube():
     K[np.diag_indices_from(K)] += 1.0 - K.sum(axis=1)
     F = pi[:, None] * K
     assert np.abs(F - F.T).max() <= 1e-14 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("L", [4, 6])
+def test_fft_reference_matches_dense_3d(L):
+    # the FFT form of eps used by the GPU refresh tests equals the dense
+    # contraction with the minimum-image coupling matrix
+    N = L ** 3
+    n = workloads.random_occupation(N, N // 2, seed=L)
+    phi = workloads.random_phi(N, 1.0, seed=L + 1)
+    dense = ref.site_energies(n, phi, 0.5, ref.coupling_matrix3(L, L, L))
+    assert np.abs(ref.site_energies_fft3(n, phi, 0.5, L) - dense).max() <= 1e-12
