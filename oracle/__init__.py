@@ -35,6 +35,16 @@ Parity status of each oracle function (what pins it, in ``tests/``):
   ``time_increment``)    correlation), ``time_increment`` against its closed
                         forms, a chain's time against the increments
                         recomputed from its hop log (tests/test_oracle_time.py).
+* two-electron hops     pinned: ``delta_e_pair`` against numpy evaluations of
+  (``set_pair``,         Eq. 1 before and after the pair move; detailed balance
+  ``delta_e_pair``)      of the single + pair kernel by exact enumeration of
+                        every state of three electrons on a 4 x 4 torus (and
+                        its failure without the reverse-offset condition); the
+                        oracle's own labels against that kernel's row
+                        (chi-square); attempt-weighted Boltzmann visits;
+                        incremental eps, energy and dipole against scratch;
+                        p2 = 0 equal to the single-hop chain
+                        (tests/test_oracle_pair.py).
 """
 from __future__ import annotations
 
@@ -86,12 +96,15 @@ class Hop(ctypes.Structure):
     _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32),
                 ("q", ctypes.c_uint32), ("p", ctypes.c_uint32),
                 ("round", ctypes.c_uint64), ("dx", ctypes.c_int32),
-                ("dy", ctypes.c_int32), ("dE", ctypes.c_double)]
+                ("dy", ctypes.c_int32), ("dE", ctypes.c_double),
+                ("k", ctypes.c_uint32), ("l", ctypes.c_uint32),
+                ("dx2", ctypes.c_int32), ("dy2", ctypes.c_int32)]
 
 
 HOP_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("q", "<u4"), ("p", "<u4"),
                       ("round", "<u8"), ("dx", "<i4"), ("dy", "<i4"),
-                      ("dE", "<f8")])
+                      ("dE", "<f8"), ("k", "<u4"), ("l", "<u4"),
+                      ("dx2", "<i4"), ("dy2", "<i4")])
 assert HOP_DTYPE.itemsize == ctypes.sizeof(Hop)
 
 
@@ -100,7 +113,12 @@ class Label(ctypes.Structure):
                 ("i", ctypes.c_uint32), ("j", ctypes.c_uint32),
                 ("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
                 ("theta", ctypes.c_int32), ("dE", ctypes.c_double),
-                ("u", ctypes.c_double), ("x", ctypes.c_uint32 * 4)]
+                ("u", ctypes.c_double), ("x", ctypes.c_uint32 * 4),
+                ("pair", ctypes.c_int32), ("vec2", ctypes.c_int32),
+                ("ex", ctypes.c_int32), ("ey", ctypes.c_int32),
+                ("k", ctypes.c_uint32), ("l", ctypes.c_uint32),
+                ("dx2", ctypes.c_int32), ("dy2", ctypes.c_int32),
+                ("y", ctypes.c_uint32 * 4)]
 
 
 def lib():
@@ -175,6 +193,12 @@ def lib():
         L.orc_delta_e.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int]
         L.orc_delta_e.restype = ctypes.c_double
+        L.orc_delta_e_pair.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 6
+        L.orc_delta_e_pair.restype = ctypes.c_double
+        L.orc_set_pair.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
+        L.orc_set_pair.restype = ctypes.c_int
+        L.orc_pair_threshold.argtypes = [ctypes.c_void_p]
+        L.orc_pair_threshold.restype = ctypes.c_uint32
         L.orc_eps_scratch.argtypes = [ctypes.c_void_p, dp]
         L.orc_eps_scratch.restype = None
         L.orc_eval_label.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
@@ -235,8 +259,9 @@ class Chain:
     """One replica of the serial mixed-rejection chain on an Lx x Ly torus."""
 
     def __init__(self, Lx, Ly=None, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05,
-                 E=0.0, seed=0, replica=0, Lz=1, dim=None):
-        """Lx x Ly x Lz torus; dim=3 makes the cubic lattice Lx = Ly = Lz."""
+                 E=0.0, seed=0, replica=0, Lz=1, dim=None, pair_frac=0.0, pair_rmax=0):
+        """Lx x Ly x Lz torus; dim=3 makes the cubic lattice Lx = Ly = Lz;
+        pair_frac > 0 adds two-electron hops (reading R15)."""
         Ly = Lx if Ly is None else Ly
         if dim == 3:
             Ly = Lz = Lx
@@ -246,6 +271,8 @@ class Chain:
                                      int(seed), int(replica))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
+        if pair_frac:
+            self.set_pair(pair_frac, pair_rmax)
         self.Lx, self.Ly, self.Lz = int(Lx), int(Ly), int(Lz)
         self.N = self.Lx * self.Ly * self.Lz
         self.nu, self.W, self.xi, self.r_max = nu, W, xi, r_max
@@ -353,6 +380,17 @@ class Chain:
         """0: t = attempts / Gamma (R4, default); 1: Gaussian dt per hop (R13)."""
         self._lib.orc_set_time_mode(self._h, int(mode))
 
+    def set_pair(self, p2, R):
+        """Two-electron hops (reading R15): a fraction p2 of the labels
+        proposes a pair move with offsets inside the disk of radius R."""
+        if self._lib.orc_set_pair(self._h, float(p2), int(R)) != ORC_OK:
+            raise ValueError("bad pair parameters")
+
+    @property
+    def pair_threshold(self):
+        """T_p: a label is a pair proposal iff its word x3 < T_p."""
+        return self._lib.orc_pair_threshold(self._h)
+
     def set_toy(self, A0=None):
         self._lib.orc_set_toy(self._h, 0 if A0 is None else 1,
                               0.0 if A0 is None else float(A0))
@@ -360,6 +398,11 @@ class Chain:
     # ---- physics ----
     def delta_e(self, i, j, dx):
         return self._lib.orc_delta_e(self._h, int(i), int(j), int(dx))
+
+    def delta_e_pair(self, i, j, k, l, dx1, dx2):
+        """dH of the pair hop i -> j, k -> l (reading R15)."""
+        return self._lib.orc_delta_e_pair(self._h, int(i), int(j), int(k), int(l),
+                                          int(dx1), int(dx2))
 
     def eval_label(self, rnd, k):
         lab = Label()

@@ -37,7 +37,7 @@
  *                     mixed PR algorithm (3a commit, 3b dipole and local-energy
  *                     update, 3c time through the attempt count).
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *   R1  Philox key = (seed lo 32, seed hi 32); proposal counter for round r,
  *       label k (0-based) of replica c = (k, r lo 32, r hi 32, c); three of
  *       the four output words are used (site, displacement, acceptance).
@@ -73,6 +73,20 @@
  *       this one: z = sqrt(-2 ln u1) cos(2 pi u2), u1 = (x0 + 1/2) 2^-32,
  *       u2 = x1 2^-32.  The paper's Gaussian can go negative for small m and
  *       it is silent on that case; it is clamped at zero.
+ *   R15 Two-electron hops (the multi-electron hops the paper names as an
+ *       extension, optional; square lattice).  A label is a pair proposal
+ *       iff its fourth Philox word x3 < T_p = floor(p2 2^32).  A second
+ *       Philox block of counter (k, r lo, r hi | 2^31, c) gives y0 -> ex,
+ *       y2 -> ey, each floor(y (2R+1) / 2^32) - R (an offset e uniform on
+ *       the square [-R, R]^2), and y1 -> a second tower vector d2.  The
+ *       second electron moves k = i + e -> l = k + d2.  The pair passes
+ *       theta iff n_i = n_k = 1, n_j = n_l = 0, 0 < |e|^2 <= R^2 and
+ *       0 < |e'|^2 <= R^2 with e' = e + d2 - d1 (the reverse move's offset),
+ *       so every pair proposal and its reverse have the same probability.
+ *       dH = (dH1 + dH2) + ((1/r_lj - 1/r_li) - (1/r_kj - 1/r_ki)),
+ *       dH1 = ((eps_j - eps_i) - 1/r_ij) - E dx1, dH2 likewise for k -> l:
+ *       the exact change of Eq. 1.  The commit applies the two single-hop
+ *       eps updates in turn; P gains dx1 + dx2; Gamma = N Z / (1 - T_p 2^-32).
  *
  * Geometry is a general Lx x Ly x Lz torus (Ly = Lz = 1 gives a ring, Lz = 1
  * the square lattice, Lx = Ly = Lz the cubic lattice of the 3D extension) so
@@ -281,6 +295,8 @@ typedef struct {
     uint64_t round;       /* global round counter of the accepting round */
     int32_t dx, dy;       /* hop vector */
     double dE;            /* dH of the executed hop */
+    uint32_t k, l;        /* second electron of a pair hop (R15); 0xFFFFFFFF otherwise */
+    int32_t dx2, dy2;     /* its hop vector; 0 otherwise */
 } orc_hop;
 
 typedef struct orc_chain {
@@ -305,6 +321,8 @@ typedef struct orc_chain {
     int toy;                  /* test-only constant acceptance mode */
     double toy_A0;
     int time_mode;            /* 0: t = attempts / Gamma (R4); 1: Gaussian dt (R13) */
+    uint32_t pair_T;          /* R15: pair proposal iff x3 < pair_T (0: single hops only) */
+    int pair_R;               /* R15: pair offsets inside the disk |e| <= pair_R */
 } orc_chain;
 
 static int fold(int d, int L)
@@ -518,7 +536,27 @@ orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
 int orc_num_vectors(const orc_chain *c) { return c->V; }
 int orc_num_sites(const orc_chain *c) { return c->N; }
 double orc_Z(const orc_chain *c) { return c->Z; }
-double orc_Gamma(const orc_chain *c) { return (double)c->N * c->Z; }
+double orc_Gamma(const orc_chain *c)
+{
+    /* R4; with pair proposals (R15) a fraction T_p 2^-32 of the attempts is
+       spent on them, so the single-hop attempts keep their rate */
+    const double g = (double)c->N * c->Z;
+    return c->pair_T ? g / (1.0 - (double)c->pair_T * 0x1p-32) : g;
+}
+
+/* R15: pair proposals with probability p2 (0 <= p2 < 1) and offset radius R
+ * (1 <= R, 2R < Lx, Ly; square lattice only). */
+int orc_set_pair(orc_chain *c, double p2, int R)
+{
+    if (!(p2 >= 0.0 && p2 < 1.0)) return ORC_EINVAL;
+    if (p2 > 0.0 && (c->Lz != 1 || c->Ly == 1 || R < 1 || 2 * R >= c->Lx || 2 * R >= c->Ly))
+        return ORC_EINVAL;
+    c->pair_T = (uint32_t)floor(p2 * 4294967296.0);
+    c->pair_R = p2 > 0.0 ? R : 0;
+    return ORC_OK;
+}
+
+uint32_t orc_pair_threshold(const orc_chain *c) { return c->pair_T; }
 
 void orc_get_vectors(const orc_chain *c, int32_t *dx, int32_t *dy,
                      uint64_t *Wint, double *w)
@@ -592,6 +630,18 @@ double orc_delta_e(const orc_chain *c, int i, int j, int dx)
     return d - c->E * (double)dx;
 }
 
+/* dH of the pair hop i -> j, k -> l (x-displacements dx1, dx2) from the
+ * current eps (R15): the two single-hop terms, then the interaction of the
+ * second electron with the first one's move. */
+double orc_delta_e_pair(const orc_chain *c, int i, int j, int k, int l, int dx1, int dx2)
+{
+    double d1 = orc_delta_e(c, i, j, dx1);
+    double d2 = orc_delta_e(c, k, l, dx2);
+    double cross = (tinv_sites(c, l, j) - tinv_sites(c, l, i)) -
+                   (tinv_sites(c, k, j) - tinv_sites(c, k, i));
+    return (d1 + d2) + cross;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One label: steps 1-2 of the mixed PR algorithm                            */
 /* ------------------------------------------------------------------------ */
@@ -601,10 +651,16 @@ typedef struct {
     int32_t vec;          /* displacement index, -1 for a null proposal */
     uint32_t i, j;
     int32_t dx, dy, dz;
-    int32_t theta;        /* n_i = 1 and n_j = 0 */
+    int32_t theta;        /* n_i = 1 and n_j = 0 (and the pair conditions of R15) */
     double dE;
     double u;
     uint32_t x[4];        /* raw Philox words */
+    int32_t pair;         /* 1: a pair proposal (x3 < T_p, R15) */
+    int32_t vec2;         /* its second vector, -1 for a null proposal */
+    int32_t ex, ey;       /* its offset e */
+    uint32_t k, l;        /* its second electron's origin and destination */
+    int32_t dx2, dy2;
+    uint32_t y[4];        /* raw words of its second Philox block */
 } orc_label;
 
 static int tower_sample(const orc_chain *c, uint32_t x1)
@@ -641,6 +697,7 @@ void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *o
 
     out->i = (uint32_t)(((uint64_t)out->x[0] * (uint64_t)c->N) >> 32);
     out->u = ((double)out->x[2] + 0.5) * 0x1p-32;
+    out->pair = out->x[3] < c->pair_T;       /* R15 */
     v = tower_sample(c, out->x[1]);
     out->vec = v;
     if (c->toy) {                        /* test-only: constant acceptance */
@@ -659,8 +716,38 @@ void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *o
     zj = (zi + out->dz + c->Lz) % c->Lz;
     out->j = (uint32_t)((zj * c->Ly + yj) * c->Lx + xj);
     out->theta = (c->n[out->i] == 1) && (c->n[out->j] == 0);
-    if (!out->theta) { out->accepted = 0; return; }
-    out->dE = orc_delta_e(c, (int)out->i, (int)out->j, out->dx);
+    out->k = 0xFFFFFFFFu;
+    out->l = 0xFFFFFFFFu;
+    if (out->pair) {
+        /* R15: a pair proposal */
+        int R = c->pair_R, W = 2 * c->pair_R + 1, xk, yk, xl, yl, fx, fy;
+        ctr[2] = (uint32_t)(round >> 32) | 0x80000000u;
+        orc_philox(ctr, key, out->y);
+        out->ex = (int)(((uint64_t)out->y[0] * (uint64_t)W) >> 32) - R;
+        out->ey = (int)(((uint64_t)out->y[2] * (uint64_t)W) >> 32) - R;
+        out->vec2 = tower_sample(c, out->y[1]);
+        if (out->vec2 < 0) { out->theta = 0; out->accepted = 0; return; }
+        out->dx2 = c->vdx[out->vec2];
+        out->dy2 = c->vdy[out->vec2];
+        xk = (xi + out->ex + c->Lx) % c->Lx;
+        yk = (yi + out->ey + c->Ly) % c->Ly;
+        xl = (xk + out->dx2 + c->Lx) % c->Lx;
+        yl = (yk + out->dy2 + c->Ly) % c->Ly;
+        out->k = (uint32_t)(yk * c->Lx + xk);
+        out->l = (uint32_t)(yl * c->Lx + xl);
+        fx = out->ex + out->dx2 - out->dx;          /* e' = l - j */
+        fy = out->ey + out->dy2 - out->dy;
+        out->theta = out->theta && c->n[out->k] == 1 && c->n[out->l] == 0 &&
+                     out->ex * out->ex + out->ey * out->ey > 0 &&
+                     out->ex * out->ex + out->ey * out->ey <= R * R &&
+                     fx * fx + fy * fy > 0 && fx * fx + fy * fy <= R * R;
+        if (!out->theta) { out->accepted = 0; return; }
+        out->dE = orc_delta_e_pair(c, (int)out->i, (int)out->j, (int)out->k, (int)out->l,
+                                   out->dx, out->dx2);
+    } else {
+        if (!out->theta) { out->accepted = 0; return; }
+        out->dE = orc_delta_e(c, (int)out->i, (int)out->j, out->dx);
+    }
     if (out->dE <= 0.0) { out->accepted = 1; return; }
     out->accepted = out->u < orc_cg_exp((-out->dE) / c->T);
 }
@@ -681,6 +768,17 @@ static void commit_hop(orc_chain *c, const orc_label *lab)
     for (l = 0; l < c->N; ++l) {
         double delta = tinv_sites(c, l, (int)j) - tinv_sites(c, l, (int)i);
         c->eps[l] = c->eps[l] + delta;
+    }
+    if (lab->pair) {
+        /* R15: the second electron's move, applied after the first one's */
+        uint32_t k = lab->k, m = lab->l;
+        c->n[k] = 0;
+        c->n[m] = 1;
+        c->cnt.P += lab->dx2;
+        for (l = 0; l < c->N; ++l) {
+            double delta = tinv_sites(c, l, (int)m) - tinv_sites(c, l, (int)k);
+            c->eps[l] = c->eps[l] + delta;
+        }
     }
 }
 
@@ -712,12 +810,15 @@ int orc_run(orc_chain *c, uint64_t n_hops, uint32_t M, uint64_t max_rounds,
                     e->i = lab.i; e->j = lab.j; e->q = q; e->p = p;
                     e->round = c->cnt.rounds;
                     e->dx = lab.dx; e->dy = lab.dy; e->dE = lab.dE;
+                    e->k = lab.pair ? lab.k : 0xFFFFFFFFu;
+                    e->l = lab.pair ? lab.l : 0xFFFFFFFFu;
+                    e->dx2 = lab.pair ? lab.dx2 : 0;
+                    e->dy2 = lab.pair ? lab.dy2 : 0;
                 }
                 if (c->time_mode) {
                     uint64_t m = (uint64_t)(p - 1) * M + q;
                     double z = orc_gauss(c->seed, c->replica, c->cnt.hops);
-                    c->cnt.time = c->cnt.time +
-                                  orc_time_increment((double)c->N * c->Z, m, z);
+                    c->cnt.time = c->cnt.time + orc_time_increment(orc_Gamma(c), m, z);
                 }
                 c->cnt.attempts += q;
                 c->cnt.rounds += 1;
