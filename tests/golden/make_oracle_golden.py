@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import oracle  # noqa: E402
+from numpy.lib.recfunctions import repack_fields  # noqa: E402
 
 
 def summary(Lx, nu, W, xi, r_max, T, E, seed, M, hops):
@@ -26,7 +27,9 @@ def summary(Lx, nu, W, xi, r_max, T, E, seed, M, hops):
         "counters": c.counters(),
         "n_sha256": hashlib.sha256(n.tobytes()).hexdigest(),
         "eps_sha256": hashlib.sha256(eps.tobytes()).hexdigest(),
-        "log_sha256": hashlib.sha256(log.tobytes()).hexdigest(),
+        # the single-hop fields of each log record, packed in this order
+        "log_sha256": hashlib.sha256(repack_fields(
+            log[["i", "j", "q", "p", "round", "dx", "dy", "dE"]]).tobytes()).hexdigest(),
         "first_hops": [[int(h["i"]), int(h["j"]), int(h["q"]), int(h["p"])]
                        for h in log[:8]],
     }

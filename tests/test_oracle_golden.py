@@ -5,8 +5,11 @@ import json
 import os
 
 import numpy as np
+from numpy.lib.recfunctions import repack_fields
 
 import oracle
+
+LOG_FIELDS = ("i", "j", "q", "p", "round", "dx", "dy", "dE")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
@@ -44,4 +47,6 @@ def test_oracle_regression_digest():
     n, eps, _ = c.state()
     assert hashlib.sha256(n.tobytes()).hexdigest() == g["n_sha256"]
     assert hashlib.sha256(eps.tobytes()).hexdigest() == g["eps_sha256"]
-    assert hashlib.sha256(log.tobytes()).hexdigest() == g["log_sha256"]
+    # the digest covers the single-hop fields of the log record
+    base = repack_fields(log[list(LOG_FIELDS)])
+    assert hashlib.sha256(base.tobytes()).hexdigest() == g["log_sha256"]
