@@ -552,8 +552,9 @@ def other_configs(args, B, local):
     replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
     tensor-core refresh per same-L group every 1024 hops), 16 replicas of
     L=256 whose eps is split over a thread-block cluster (refresh every 4096
-    hops), and 152 replicas of the 32 x 32 x 32 cubic lattice (binary64
-    refresh every 1024 hops).  Each is timed with CUDA events over hops that
+    hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
+    tensor-core refresh every 1024 hops), and 304 replicas of L=64 with and
+    without two-electron hops (a fifth of the labels proposing a pair).  Each is timed with CUDA events over hops that
     follow a relaxation from the random start."""
     import torch
     from paper_1407_5026_gb300 import workloads as W
@@ -561,10 +562,13 @@ def other_configs(args, B, local):
     for name, wl, relax, hops, graph, tune in (
             ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
             ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, False),
-            ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False)):
+            ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
+            ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
+            ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False)):
         reps = [r.as_dict() for r in wl.replicas]
+        pair = {k: wl.extra[k] for k in ("pair_frac", "pair_rmax") if wl.extra.get("pair_frac")}
         s = B.System(reps, precision=B.CG_FP32, refresh_every=wl.refresh_every,
-                     use_graph=graph, device=local)
+                     use_graph=graph, device=local, **pair)
         s.run(relax, wl.M)
         if tune:
             B.cg_autotune(s.h, 256)
@@ -586,8 +590,19 @@ def other_configs(args, B, local):
                      "groups": [shape_of(B, s.h, g, tune) for g in range(B.cg_num_groups(s.h))],
                      "max_eps_err": max(o["max_eps_err_last_refresh"] for o in o1),
                      "graph": bool(graph)}
+        if pair:
+            out[name].update(pair)
+            out[name]["pair_hops_share"] = pair_share(B, s, reps, wl.M)
         s.close()
     return out
+
+
+def pair_share(B, s, reps, M, hops=64):
+    """Share of two-electron hops among the next `hops` hops of every
+    replica (from their hop logs)."""
+    import numpy as np
+    rc, log = s.run_logged(hops, M)
+    return float(np.mean(log["k"] != 0xFFFFFFFF))
 
 
 def e2e(args, B, reps, local, snapshot):

@@ -107,6 +107,20 @@ typedef struct {
                                    Gaussian dt of mean m/Gamma and standard
                                    deviation sqrt(m)/Gamma, m = (p-1)M + q
                                    (mixed PR algorithm, step 3c), clamped at 0 */
+    int32_t pair_rmax;          /* two-electron hops (pair_frac > 0): the second
+                                   electron sits at an offset e with
+                                   0 < |e| <= pair_rmax from the first, and the
+                                   reverse move's offset must obey the same
+                                   bound; 1 <= pair_rmax, 2 pair_rmax < L      */
+    double pair_frac;           /* fraction p2 in [0, 1) of the labels that
+                                   propose a two-electron hop (the paper's
+                                   multi-electron hops, named in its
+                                   conclusions as an extension): a label is a
+                                   pair proposal iff its fourth Philox word is
+                                   below floor(p2 2^32).  0 = single hops only.
+                                   Square lattices on one CTA with the
+                                   deterministic time only (else CG_EINVAL);
+                                   Gamma becomes N Z / (1 - floor(p2 2^32) 2^-32) */
 } cg_opts;
 
 /* Counters of one replica (step 3 of the mixed PR algorithm). */
@@ -152,7 +166,11 @@ typedef struct {
     uint32_t p;          /* rounds used for this hop                   */
     uint64_t round;      /* round counter of the accepting round       */
     int32_t dx, dy;      /* hop vector                                 */
-    double dE;           /* dH of the hop (binary64)                   */
+    double dE;           /* dH of the hop (binary64; of both electrons
+                            for a two-electron hop)                    */
+    uint32_t k, l;       /* second electron of a two-electron hop:
+                            origin, destination; 0xFFFFFFFF otherwise  */
+    int32_t dx2, dy2;    /* its hop vector; 0 otherwise                */
 } cg_hop;
 
 /* ---------------------------------------------------------------------- */

@@ -57,7 +57,8 @@ class cg_opts(ctypes.Structure):
                 ("max_rounds_per_hop", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("hop_timeout_ms", ctypes.c_uint32), ("cluster_size", ctypes.c_int32),
-                ("time_mode", ctypes.c_int32)]
+                ("time_mode", ctypes.c_int32), ("pair_rmax", ctypes.c_int32),
+                ("pair_frac", ctypes.c_double)]
 
 
 class cg_counters(ctypes.Structure):
@@ -87,11 +88,13 @@ class cg_obs(ctypes.Structure):
 class cg_hop(ctypes.Structure):
     _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("q", ctypes.c_uint32),
                 ("p", ctypes.c_uint32), ("round", ctypes.c_uint64), ("dx", ctypes.c_int32),
-                ("dy", ctypes.c_int32), ("dE", ctypes.c_double)]
+                ("dy", ctypes.c_int32), ("dE", ctypes.c_double), ("k", ctypes.c_uint32),
+                ("l", ctypes.c_uint32), ("dx2", ctypes.c_int32), ("dy2", ctypes.c_int32)]
 
 
 HOP_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("q", "<u4"), ("p", "<u4"),
-                      ("round", "<u8"), ("dx", "<i4"), ("dy", "<i4"), ("dE", "<f8")])
+                      ("round", "<u8"), ("dx", "<i4"), ("dy", "<i4"), ("dE", "<f8"),
+                      ("k", "<u4"), ("l", "<u4"), ("dx2", "<i4"), ("dy2", "<i4")])
 
 
 class cg_trace_point(ctypes.Structure):
@@ -188,12 +191,12 @@ def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0, di
 
 def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,
          max_rounds_per_hop=0, device=0, use_graph=0, stream=None, hop_timeout_ms=0,
-         cluster_size=0, time_mode=CG_TIME_DETERMINISTIC):
+         cluster_size=0, time_mode=CG_TIME_DETERMINISTIC, pair_frac=0.0, pair_rmax=0):
     return cg_opts(precision=precision, refresh_kind=refresh_kind, refresh_every=refresh_every,
                    block_threads=block_threads, max_rounds_per_hop=max_rounds_per_hop,
                    device=device, use_graph=use_graph, stream=stream,
                    hop_timeout_ms=hop_timeout_ms, cluster_size=cluster_size,
-                   time_mode=time_mode)
+                   time_mode=time_mode, pair_rmax=pair_rmax, pair_frac=pair_frac)
 
 
 # ---- the C entry points, one to one ----
@@ -472,7 +475,8 @@ class System:
 
     def __init__(self, reps, precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO,
                  block_threads=0, max_rounds_per_hop=0, device=0, torch_memory=True,
-                 hop_timeout_ms=0, cluster_size=0, use_graph=0, time_mode=0):
+                 hop_timeout_ms=0, cluster_size=0, use_graph=0, time_mode=0, pair_frac=0.0,
+                 pair_rmax=0):
         import torch
         self.reps = [r if isinstance(r, dict) else r for r in reps]
         torch.cuda.set_device(device)
@@ -483,7 +487,8 @@ class System:
                          refresh_kind=refresh_kind, block_threads=block_threads,
                          max_rounds_per_hop=max_rounds_per_hop, device=device,
                          stream=self.stream.cuda_stream, hop_timeout_ms=hop_timeout_ms,
-                         cluster_size=cluster_size, use_graph=use_graph, time_mode=time_mode)
+                         cluster_size=cluster_size, use_graph=use_graph, time_mode=time_mode,
+                         pair_frac=pair_frac, pair_rmax=pair_rmax)
         self.workspace = None
         if torch_memory:
             nbytes = cg_workspace_bytes(self.reps, self.opts)

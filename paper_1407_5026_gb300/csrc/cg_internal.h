@@ -49,10 +49,12 @@ struct alignas(16) DevReplica {
     unsigned int key0, key1;  // Philox key (seed lo, seed hi)
     unsigned int replica;     // Philox counter word 3
     int dim;                  // 2 (square lattice) or 3 (cubic lattice)
+    unsigned int pair_T;      // two-electron hops: a label pairs iff its word x3 < pair_T
+    int pair_R;               // their offset bound |e| <= pair_R
     double nu, T, E;
     double negC0nu;           // -nu * sum_{t != s} 1/r_st (same for every s)
     double C0;                // sum_{t != s} 1/r_st
-    double Gamma;             // N * Z, the total proposal rate
+    double Gamma;             // N * Z (/ (1 - pair_T 2^-32)), the total proposal rate
     // tables (device)
     const double *tinv64;     // H1*H1, [fy*H1 + fx] = 1/sqrt(fx^2+fy^2), 0 at origin
     const float *tinv32;      // the same rounded to binary32
@@ -98,6 +100,7 @@ struct RunArgs {
     unsigned int M;                // labels per round
     int toy;                       // constant-acceptance test mode
     int time_mode;                 // CG_TIME_DETERMINISTIC or CG_TIME_GAUSSIAN
+    int pair;                      // 1: two-electron hops (the kPair instances)
     double toy_A0;
 };
 
@@ -138,6 +141,13 @@ cudaError_t launch_pr_persistent3(int precision, const DevReplica *d_reps, const
                                   int n_ctas, int threads, int smem_bytes, const RunArgs &args,
                                   cudaStream_t st, int L);
 cudaError_t set_pr3_smem_limit(int precision, int bytes);
+// The two-electron-hop instances (cg_pr_kernel_pair.cu): square lattice, one
+// CTA per replica, deterministic time.
+cudaError_t launch_pr_persistent_pair(int precision, const DevReplica *d_reps,
+                                      const int *d_index, int n_ctas, int threads,
+                                      int smem_bytes, const RunArgs &args, cudaStream_t st,
+                                      int L);
+cudaError_t set_pr_pair_smem_limit(int precision, int bytes);
 // The same chain over a thread-block cluster of `cluster` CTAs per replica
 // (eps split by rows); grid = n_reps * cluster CTAs.
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,

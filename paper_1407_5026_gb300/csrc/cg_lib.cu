@@ -356,6 +356,22 @@ int check_desc(const cg_replica_desc &d)
     return CG_OK;
 }
 
+// Two-electron hops: a label is a pair proposal iff its fourth Philox word
+// is below this threshold, floor(pair_frac 2^32).
+unsigned pair_threshold(const cg_opts &o)
+{
+    return o.pair_frac > 0.0 ? (unsigned)std::floor(o.pair_frac * 4294967296.0) : 0u;
+}
+
+// The total proposal rate: N Z, and with pair proposals N Z / (1 - T_p 2^-32),
+// so that the single-hop attempts keep their rate.
+double gamma_of(const Rep &r, const cg_opts &o)
+{
+    const double g = (double)r.N * r.tab->Z;
+    const unsigned Tp = pair_threshold(o);
+    return Tp ? g / (1.0 - (double)Tp * 0x1p-32) : g;
+}
+
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
     const int rb = precision == CG_FP64 ? 8 : 4;
@@ -368,7 +384,7 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
 int choose_cluster(const cg_opts &o, const Rep &r, int optin)
 {
     const int budget = optin - 2048;     // room for the kernels' static shared memory
-    if (dim_of(r.d) == 3)                // the cubic lattice runs on one CTA
+    if (dim_of(r.d) == 3 || o.pair_frac > 0.0)   // the cubic lattice and pair hops: one CTA
         return persistent_smem(r, o.precision, 1) <= budget ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
@@ -395,7 +411,7 @@ int choose_threads(const cg_opts &o, int L, int smem)
 
 unsigned magic_for(int L) { return (unsigned)(4294967296ull / (unsigned long long)L + 1ull); }
 
-void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
+void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
 {
     std::memset(&dr, 0, sizeof(dr));
     const Tables &t = *r.tab;
@@ -407,14 +423,15 @@ void fill_dev(const Rep &r, int precision, DevReplica &dr, cg_hop *log)
     dr.replica = r.d.replica;
     dr.nu = r.d.nu; dr.T = r.d.T; dr.E = r.d.E;
     dr.negC0nu = -r.d.nu * t.C0;
-    dr.Gamma = (double)r.N * t.Z;
+    dr.Gamma = gamma_of(r, o);
+    dr.pair_T = pair_threshold(o);
+    dr.pair_R = dr.pair_T ? o.pair_rmax : 0;
     dr.tinv64 = t.d_t64; dr.tinv32 = t.d_t32; dr.thr = t.d_thr; dr.disp = t.d_disp;
     dr.tinvd = t.d_tinvd;
     dr.guide = t.d_guide;
     dr.C0 = t.C0;
     dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
     dr.log = log;
-    (void)precision;
 }
 
 void host_setup_state(const cg_replica_desc &d, std::vector<double> &phi,
@@ -600,6 +617,23 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     if (o.max_rounds_per_hop == 0) o.max_rounds_per_hop = 1ull << 32;
     for (int k = 0; k < R; ++k)
         if (check_desc(reps[k]) != CG_OK) return nullptr;
+    if (!(o.pair_frac >= 0.0 && o.pair_frac < 1.0)) {
+        fail(CG_EINVAL, "pair_frac must be in [0, 1)");
+        return nullptr;
+    }
+    if (o.pair_frac > 0.0) {
+        if (o.time_mode != CG_TIME_DETERMINISTIC || o.cluster_size > 1) {
+            fail(CG_EINVAL, "two-electron hops run on one CTA per replica with the "
+                            "deterministic time");
+            return nullptr;
+        }
+        for (int k = 0; k < R; ++k)
+            if (dim_of(reps[k]) != 2 || o.pair_rmax < 1 || 2 * o.pair_rmax >= reps[k].L) {
+                fail(CG_EINVAL, "two-electron hops need square lattices and "
+                                "1 <= pair_rmax < L/2");
+                return nullptr;
+            }
+    }
 
     std::unique_ptr<cg_handle> h(new cg_handle());
     h->opts = o;
@@ -759,7 +793,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     }
     h->order = order;
     h->h_reps.resize(R);
-    for (int k = 0; k < R; ++k) fill_dev(h->reps[k], o.precision, h->h_reps[k], nullptr);
+    for (int k = 0; k < R; ++k) fill_dev(h->reps[k], o, h->h_reps[k], nullptr);
     if (cudaMemcpyAsync(h->d_reps, h->h_reps.data(), sizeof(DevReplica) * R,
                         cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
         cudaMemcpyAsync(h->d_index, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
@@ -848,6 +882,7 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.toy = h->toy;
     a.toy_A0 = h->toy_A0;
     a.time_mode = h->opts.time_mode;
+    a.pair = h->opts.pair_frac > 0.0 ? 1 : 0;
     if (g.cluster > 1)
         CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
                                   g.cluster, g.threads, g.smem, a, st, g.L));
@@ -1225,7 +1260,7 @@ int cg_observables(cg_handle *h, int replica, cg_obs *out)
     out->c.rounds = dc.rounds; out->c.hops = dc.hops; out->c.attempts = dc.attempts;
     out->c.evaluated = dc.evaluated; out->c.P = dc.P; out->c.energy = dc.energy;
     out->c.time = dc.time;
-    out->Gamma = (double)r.N * r.tab->Z;
+    out->Gamma = gamma_of(r, h->opts);
     out->time = h->opts.time_mode == CG_TIME_GAUSSIAN ? dc.time
                                                       : (double)dc.attempts / out->Gamma;
     out->acceptance = dc.attempts ? (double)dc.hops / (double)dc.attempts : 0.0;
@@ -1431,7 +1466,7 @@ int cg_set_trace(cg_handle *h, double first_time, double points_per_decade, int 
         // the first point is the present state; later points at first_time * ratio^n
         cg_trace_point p0{c.attempts, c.hops, c.P, c.energy};
         CG_CUDA(cudaMemcpy(h->d_trace + k * capacity, &p0, sizeof(p0), cudaMemcpyHostToDevice));
-        const double Gamma = (double)r.N * r.tab->Z;
+        const double Gamma = gamma_of(r, h->opts);
         c.trace_count = 1;
         c.trace_cap = capacity;
         c.trace_ratio = ratio;

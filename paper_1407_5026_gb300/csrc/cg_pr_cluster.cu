@@ -300,6 +300,8 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
                 e.dx = a.toy ? 0 : cdx; e.dy = a.toy ? 0 : cdy;
                 e.dE = a.toy ? 0.0 : win.dE;
+                e.k = e.l = 0xFFFFFFFFu;
+                e.dx2 = e.dy2 = 0;
                 Rg.log[a.log_offset + h] = e;
             }
             if (!a.toy) {

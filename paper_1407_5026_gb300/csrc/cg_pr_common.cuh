@@ -81,6 +81,7 @@ struct Prop {
     unsigned i, j;
     int v, dxy;
     uint32_t x2;
+    uint32_t x3;              // fourth word: the pair decision of two-electron hops
     bool theta;
 };
 
@@ -97,6 +98,7 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     uint32_t x[4];
     philox_finish(k, P, key0, key1, x);
     p.x2 = x[2];
+    p.x3 = x[3];
     p.i = kPow2 ? (x[0] >> (32 - kDim * log2L)) : __umulhi(x[0], N);   // floor(x0 N / 2^32)
     // a label beyond M or a null proposal (x1 above the last threshold) is
     // evaluated on a clamped x1 without a branch and can never pass theta
@@ -233,6 +235,175 @@ __device__ __forceinline__ void accept2_f32(const Shared &S, const Prop &p0, con
         if (tie0) acc0 = accept_vals<float>(eps[p0.i], eps[p0.j], S, p0, T, invTf, dE0);
         if (tie1) acc1 = accept_vals<float>(eps[p1.i], eps[p1.j], S, p1, T, invTf, dE1);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Two-electron hops.  A label whose fourth word x3 is below pair_T proposes a
+// pair: from the Philox block of counter (k, r lo, r hi | 2^31, replica), y0
+// and y2 give the offset e = (floor(y0 W / 2^32) - R, floor(y2 W / 2^32) - R),
+// W = 2R + 1, of the second electron k = i + e, and y1 its hop vector d2 by
+// the same tower, l = k + d2.  theta also needs n_k = 1, n_l = 0,
+// 0 < |e|^2 <= R^2 and 0 < |e'|^2 <= R^2 for the reverse offset
+// e' = e + d2 - d1, so that a pair and its reverse are proposed with the
+// same probability.
+// ---------------------------------------------------------------------------
+
+struct PairProp {
+    unsigned k, l;            // 0xFFFFFFFF for a single hop
+    int v2, dxy2;
+    bool pair;
+};
+
+template <bool kPow2>
+__device__ __forceinline__ void site_xy(unsigned s, int L, int log2L, unsigned magic, int &x,
+                                        int &y)
+{
+    y = kPow2 ? (int)(s >> log2L) : (int)__umulhi(s, magic);
+    x = (int)s - y * L;
+}
+
+__device__ __forceinline__ int wrap_axis(int c, int L)
+{
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return c;
+}
+
+template <bool kPow2>
+__device__ __forceinline__ PairProp pair_extend(const Shared &S, Prop &p, unsigned k,
+                                                const PhiloxPrefix &P2, uint32_t key0,
+                                                uint32_t key1, int L, int log2L, unsigned magic,
+                                                unsigned thr_last, uint32_t pair_T, int R)
+{
+    PairProp q;
+    q.k = q.l = 0xFFFFFFFFu;
+    q.v2 = 0;
+    q.dxy2 = 0;
+    q.pair = p.x3 < pair_T;
+    if (!q.pair) return q;
+    uint32_t y[4];
+    philox_finish(k, P2, key0, key1, y);
+    const unsigned W = (unsigned)(2 * R + 1);
+    const int ex = (int)__umulhi(y[0], W) - R, ey = (int)__umulhi(y[2], W) - R;
+    const bool live2 = y[1] <= thr_last;
+    const int v2 = tower_lookup(S.guide, S.thr, min(y[1], thr_last));
+    const int dxy2 = S.disp[v2];
+    const int dx2 = (int)(short)(dxy2 & 0xffff), dy2 = dxy2 >> 16;
+    const int dx1 = (int)(short)(p.dxy & 0xffff), dy1 = p.dxy >> 16;
+    int xi, yi;
+    site_xy<kPow2>(p.i, L, log2L, magic, xi, yi);
+    const int xk = wrap_axis(xi + ex, L), yk = wrap_axis(yi + ey, L);
+    const int xl = wrap_axis(xk + dx2, L), yl = wrap_axis(yk + dy2, L);
+    const unsigned ks = (unsigned)(yk * L + xk), ls = (unsigned)(yl * L + xl);
+    const int fx = ex + dx2 - dx1, fy = ey + dy2 - dy1;
+    const int e2 = ex * ex + ey * ey, f2 = fx * fx + fy * fy, R2 = R * R;
+    const unsigned wk = S.occ[ks >> 5], wl = S.occ[ls >> 5];
+    const bool ok = live2 && e2 > 0 && e2 <= R2 && f2 > 0 && f2 <= R2 &&
+                    ((wk >> (ks & 31)) & 1u) && !((wl >> (ls & 31)) & 1u);
+    p.theta = p.theta && ok;
+    q.k = ks;
+    q.l = ls;
+    q.v2 = v2;
+    q.dxy2 = dxy2;
+    return q;
+}
+
+// 1/r between sites a and b from a folded table [fy * H1 + fx].
+template <typename T, bool kPow2>
+__device__ __forceinline__ T tinv_sites(const T *tab, unsigned a, unsigned b, int L, int log2L,
+                                        unsigned magic, int H1)
+{
+    int xa, ya, xb, yb;
+    site_xy<kPow2>(a, L, log2L, magic, xa, ya);
+    site_xy<kPow2>(b, L, log2L, magic, xb, yb);
+    return tab[fold_axis(ya - yb, L) * H1 + fold_axis(xa - xb, L)];
+}
+
+// dH of the pair i -> j, k -> l in binary64, in the serial chain's order:
+// (dH1 + dH2) + ((1/r_lj - 1/r_li) - (1/r_kj - 1/r_ki)), each dH as R9.
+template <bool kPow2>
+__device__ __forceinline__ double pair_dE64(const Shared &S, const double *tab64, double ei,
+                                            double ej, double ek, double el, const Prop &p,
+                                            const PairProp &q, int L, int log2L,
+                                            unsigned magic, int H1)
+{
+    const double d1 = d_sub(d_sub(d_sub(ej, ei), S.vr64[p.v]), S.edx64[p.v]);
+    const double d2 = d_sub(d_sub(d_sub(el, ek), S.vr64[q.v2]), S.edx64[q.v2]);
+    const double tlj = tinv_sites<double, kPow2>(tab64, q.l, p.j, L, log2L, magic, H1);
+    const double tli = tinv_sites<double, kPow2>(tab64, q.l, p.i, L, log2L, magic, H1);
+    const double tkj = tinv_sites<double, kPow2>(tab64, q.k, p.j, L, log2L, magic, H1);
+    const double tki = tinv_sites<double, kPow2>(tab64, q.k, p.i, L, log2L, magic, H1);
+    return d_add(d_add(d1, d2), d_sub(d_sub(tlj, tli), d_sub(tkj, tki)));
+}
+
+// The Metropolis decision u < e^(-dH/T) for dH > 0 in binary64 semantics
+// (a binary32 estimate with a margin decides most cases).
+__device__ __forceinline__ bool metropolis64(double dE, uint32_t x2, double T, float invTf)
+{
+    if (dE <= 0.0) return true;
+    const float df = approx_f32(dE);
+    if (df > 0.0f) {
+        const float y = -df * invTf;
+        if (y < -23.01f) return false;
+        const float e = __expf(y);
+        const float u = __uint2float_rn(x2) * 0x1p-32f;
+        if (u + 0x1p-31f < e * (1.0f - 2e-4f)) return true;
+        if (u > e * (1.0f + 2e-4f) + 0x1p-31f) return false;
+    }
+    const double u = d_mul(d_add((double)x2, 0.5), 0x1p-32);
+    return u < cg_exp_accept(d_div(-dE, T));
+}
+
+// Step 2 for a pair whose theta holds.  Binary64: exact dH.  Binary32: the
+// same sum in binary32 from the binary32 table, re-decided in binary64 from
+// the widened energies and the binary64 table when |dH| < 1e-5 (dE_out is
+// then the binary64 value, else 0: the executed pair is widened once).
+template <typename Real, bool kPow2>
+__device__ __forceinline__ bool accept_pair(const Shared &S, const DevReplica &Rg, const Prop &p,
+                                            const PairProp &q, double T, float invTf,
+                                            double &dE_out, int L, int log2L, unsigned magic,
+                                            int H1)
+{
+    const Real *eps = reinterpret_cast<const Real *>(S.eps);
+    const Real ei = eps[p.i], ej = eps[p.j], ek = eps[q.k], el = eps[q.l];
+    if (sizeof(Real) == 8) {
+        const double dE = pair_dE64<kPow2>(S, reinterpret_cast<const double *>(S.tinv),
+                                           (double)ei, (double)ej, (double)ek, (double)el, p, q,
+                                           L, log2L, magic, H1);
+        dE_out = dE;
+        return metropolis64(dE, p.x2, T, invTf);
+    }
+    const float *t32 = reinterpret_cast<const float *>(S.tinv);
+    const float d1 = __fsub_rn(__fsub_rn((float)ej, (float)ei), S.cv32[p.v]);
+    const float d2 = __fsub_rn(__fsub_rn((float)el, (float)ek), S.cv32[q.v2]);
+    const float cr = __fsub_rn(
+        __fsub_rn(tinv_sites<float, kPow2>(t32, q.l, p.j, L, log2L, magic, H1),
+                  tinv_sites<float, kPow2>(t32, q.l, p.i, L, log2L, magic, H1)),
+        __fsub_rn(tinv_sites<float, kPow2>(t32, q.k, p.j, L, log2L, magic, H1),
+                  tinv_sites<float, kPow2>(t32, q.k, p.i, L, log2L, magic, H1)));
+    const float dEf = __fadd_rn(__fadd_rn(d1, d2), cr);
+    if (fabsf(dEf) < 1e-5f) {
+        const double dE = pair_dE64<kPow2>(S, Rg.tinv64, (double)ei, (double)ej, (double)ek,
+                                           (double)el, p, q, L, log2L, magic, H1);
+        dE_out = dE;
+        return metropolis64(dE, p.x2, T, invTf);
+    }
+    dE_out = 0.0;
+    if (dEf <= 0.0f) return true;
+    return (float)(p.x2 >> 9) < __fmaf_rn(__expf(-dEf * invTf), 0x1p23f, -0.5f);
+}
+
+// dH of an executed pair in binary64 (binary32 form: from the widened
+// energies and the binary64 table, once per hop).
+template <typename Real, bool kPow2>
+__device__ __forceinline__ double pair_hop_dE(const Shared &S, const DevReplica &Rg,
+                                              const Prop &p, const PairProp &q, double dE,
+                                              int L, int log2L, unsigned magic, int H1)
+{
+    if (sizeof(Real) == 8 || dE != 0.0) return dE;
+    const float *eps = reinterpret_cast<const float *>(S.eps);
+    return pair_dE64<kPow2>(S, Rg.tinv64, (double)eps[p.i], (double)eps[p.j], (double)eps[q.k],
+                            (double)eps[q.l], p, q, L, log2L, magic, H1);
 }
 
 template <typename Real>

@@ -78,7 +78,9 @@ cudaError_t set_pr_smem_limit(int precision, int bytes)
 {
     const cudaError_t e =
         precision == CG_FP64 ? set_smem_t<double>(bytes) : set_smem_t<float>(bytes);
-    return e ? e : set_pr3_smem_limit(precision, bytes);
+    if (e) return e;
+    const cudaError_t e3 = set_pr3_smem_limit(precision, bytes);
+    return e3 ? e3 : set_pr_pair_smem_limit(precision, bytes);
 }
 
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const int *d_index,
@@ -89,6 +91,9 @@ cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const 
     if (dim == 3)
         return launch_pr_persistent3(precision, d_reps, d_index, n_ctas, threads, smem_bytes,
                                      args, st, L);
+    if (args.pair)
+        return launch_pr_persistent_pair(precision, d_reps, d_index, n_ctas, threads, smem_bytes,
+                                         args, st, L);
     if (precision == CG_FP64) {
         switch (threads) {
         case 1024: return launch_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);

@@ -48,7 +48,10 @@ namespace cg {
 // kernel); the default deterministic clock compiles without that code.
 // kDim: 2 for the L x L square lattice, 3 for the L x L x L cubic lattice
 // (site s = (z L + y) L + x; hop vectors packed in 10-bit fields).
-template <typename Real, int kThreads, int kLog2L, bool kTime, int kDim = 2>
+// kPair: two-electron hops (square lattice): labels whose fourth Philox word
+// is below Rg.pair_T propose a pair move (pair_extend); an executed pair
+// applies the two single-hop eps updates in turn.
+template <typename Real, int kThreads, int kLog2L, bool kTime, int kDim = 2, bool kPair = false>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
@@ -56,6 +59,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
+    __shared__ PairProp s_pcand[kPair ? 32 : 1];   // the second electron of a pair candidate
     // step-3c deviates of the next hops (CG_TIME_GAUSSIAN): warp 0 draws 32
     // at a time, one per lane, so the binary64 Box-Muller chain runs once
     // per 32 hops instead of on thread 0's path at every commit
@@ -180,10 +184,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             ++p;
             const PhiloxPrefix PP =
                 philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
+            PhiloxPrefix PP2{};
+            if (kPair)
+                PP2 = philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32) | 0x80000000u, rep,
+                                    key0, key1);
             for (unsigned kb = 0; kb < M; kb += C) {
                 const unsigned k0 = kb + (unsigned)tid, k1 = k0 + (unsigned)kThreads;
                 const bool v0 = k0 < M, v1 = two && k1 < M;
                 Prop p0{}, p1{};
+                PairProp q0{}, q1{};
                 double dE0 = 0.0, dE1 = 0.0;
                 bool acc0 = false, acc1 = false;
                 if (act) {
@@ -192,11 +201,27 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                     if (two)
                         p1 = propose<kPow2, kDim>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
                                             thr_last, v1);
+                    if (kPair && !a.toy) {
+                        q0 = pair_extend<kPow2>(S, p0, k0, PP2, key0, key1, L, log2L, magic,
+                                                thr_last, Rg.pair_T, Rg.pair_R);
+                        if (two)
+                            q1 = pair_extend<kPow2>(S, p1, k1, PP2, key0, key1, L, log2L, magic,
+                                                    thr_last, Rg.pair_T, Rg.pair_R);
+                    }
                     if (a.toy) {
                         const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
                         const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
                         acc0 = v0 && u0 < a.toy_A0;
                         acc1 = v1 && u1 < a.toy_A0;
+                    } else if (kPair) {
+                        if (p0.theta)
+                            acc0 = q0.pair ? accept_pair<Real, kPow2>(S, Rg, p0, q0, T, invTf, dE0,
+                                                                     L, log2L, magic, H1)
+                                           : accept<Real>(S, p0, T, invTf, dE0);
+                        if (p1.theta)
+                            acc1 = q1.pair ? accept_pair<Real, kPow2>(S, Rg, p1, q1, T, invTf, dE1,
+                                                                     L, log2L, magic, H1)
+                                           : accept<Real>(S, p1, T, invTf, dE1);
                     } else if (sizeof(Real) == 4 && two) {
                         accept2_f32(S, p0, p1, T, invTf, acc0, acc1, dE0, dE1);
                     } else {
@@ -216,7 +241,16 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                             s_cand[warp].i = p0.i;
                             s_cand[warp].j = p0.j;
                             s_cand[warp].dxy = p0.dxy;
-                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p0, dE0);
+                            if (kPair) {
+                                s_pcand[warp] = q0;
+                                s_cand[warp].dE =
+                                    a.toy ? 0.0
+                                    : q0.pair ? pair_hop_dE<Real, kPow2>(S, Rg, p0, q0, dE0, L,
+                                                                         log2L, magic, H1)
+                                              : hop_dE<Real>(S, p0, dE0);
+                            } else {
+                                s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p0, dE0);
+                            }
                         }
                     } else if (b1) {
                         const int first = __ffs(b1) - 1;
@@ -225,7 +259,16 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                             s_cand[warp].i = p1.i;
                             s_cand[warp].j = p1.j;
                             s_cand[warp].dxy = p1.dxy;
-                            s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p1, dE1);
+                            if (kPair) {
+                                s_pcand[warp] = q1;
+                                s_cand[warp].dE =
+                                    a.toy ? 0.0
+                                    : q1.pair ? pair_hop_dE<Real, kPow2>(S, Rg, p1, q1, dE1, L,
+                                                                         log2L, magic, H1)
+                                              : hop_dE<Real>(S, p1, dE1);
+                            } else {
+                                s_cand[warp].dE = a.toy ? 0.0 : hop_dE<Real>(S, p1, dE1);
+                            }
                         }
                     }
                     if (lane == 0) s_wlabel[warp] = off;
@@ -268,6 +311,12 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         const unsigned ci = c.i, cj = c.j;
         const int cdx = kDim == 3 ? (c.dxy << 22) >> 22 : (int)(short)(c.dxy & 0xffff);
         const int cdy = kDim == 3 ? (c.dxy << 12) >> 22 : c.dxy >> 16;
+        // second electron of an executed pair (toy mode has none)
+        PairProp cq{};
+        if (kPair) cq = s_pcand[win];
+        const bool cpair = kPair && !a.toy && cq.pair;
+        const int cdx2 = cpair ? (int)(short)(cq.dxy2 & 0xffff) : 0;
+        const int cdy2 = cpair ? cq.dxy2 >> 16 : 0;
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
@@ -280,7 +329,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             s_c.evaluated += (kb_hit + C < M) ? (kb_hit + C) : M;
             s_c.hops += 1;
             if (!a.toy) {
-                s_c.P += cdx;
+                s_c.P += cdx + cdx2;
                 s_c.energy = d_add(s_c.energy, c.dE);
             }
             if (s_c.tracing)
@@ -292,11 +341,17 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 e.i = ci; e.j = cj; e.q = q; e.p = (uint32_t)p; e.round = rounds;
                 e.dx = a.toy ? 0 : cdx; e.dy = a.toy ? 0 : cdy;
                 e.dE = a.toy ? 0.0 : c.dE;
+                e.k = cpair ? cq.k : 0xFFFFFFFFu; e.l = cpair ? cq.l : 0xFFFFFFFFu;
+                e.dx2 = cdx2; e.dy2 = cdy2;
                 s_c.log[a.log_offset + h] = e;
             }
             if (!a.toy) {
                 S.occ[ci >> 5] &= ~(1u << (ci & 31));
                 S.occ[cj >> 5] |= (1u << (cj & 31));
+                if (cpair) {
+                    S.occ[cq.k >> 5] &= ~(1u << (cq.k & 31));
+                    S.occ[cq.l >> 5] |= (1u << (cq.l & 31));
+                }
             }
         }
         rounds += 1;
@@ -358,11 +413,17 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             // thread -> base column bx < L/2, base rows by0, by0 + rpp, ...
             const int Lh = L >> 1;
             const int rpp = kThreads / Lh;
+            // an executed pair applies the second electron's update after the
+            // first one's (each site rounds twice, in the serial order)
+            const int passes = (kPair && cpair) ? 2 : 1;
+#pragma unroll 1
+            for (int pass = 0; pass < passes; ++pass) {
+            const unsigned ui = pass ? cq.k : ci, uj = pass ? cq.l : cj;
             if (!a.toy && tid < rpp * Lh) {
                 const int bx = tid % Lh, by0 = tid / Lh;
-                const int yi = kPow2 ? (int)(ci >> log2L) : (int)__umulhi(ci, magic);
-                const int yj = kPow2 ? (int)(cj >> log2L) : (int)__umulhi(cj, magic);
-                const int xi = (int)ci - yi * L, xj = (int)cj - yj * L;
+                const int yi = kPow2 ? (int)(ui >> log2L) : (int)__umulhi(ui, magic);
+                const int yj = kPow2 ? (int)(uj >> log2L) : (int)__umulhi(uj, magic);
+                const int xi = (int)ui - yi * L, xj = (int)uj - yj * L;
                 const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);
                 // columns of (x, .) and (x + L/2, .) relative to j and to i
                 const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
@@ -392,6 +453,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                     e[LhL] = Prec<Real>::add(e[LhL], Prec<Real>::sub(a01, b01));
                     e[LhL + Lh] = Prec<Real>::add(e[LhL + Lh], Prec<Real>::sub(a11, b11));
                 }
+            }
             }
         }
         __syncthreads();

@@ -111,6 +111,18 @@ def l256(R: int = 16, hops: int = 10_000_000) -> Workload:
                     precision="fp32", refresh_every=4096)
 
 
+def pairs(R: int = 304, pair_frac: float = 0.2, hops: int = 1_000_000) -> Workload:
+    """Two-electron hops (the paper's multi-electron extension): L=64,
+    nu=1/2, phi ~ U[-0.5, 0.5], xi=1, r_max=6, T=0.05, E=0.01, a fraction
+    pair_frac of the labels proposing a pair with offsets |e| <= 4, FP32 eps
+    refreshed every 1024 hops."""
+    reps = tuple(Replica(L=64, nu=0.5, W=1.0, xi=1.0, r_max=6, T=0.05, E=0.01,
+                         seed=s, replica=s) for s in range(R))
+    return Workload(f"pairs_L64_T0.05_R{R}_p{pair_frac}", reps, M=4096, hops=hops,
+                    precision="fp32", refresh_every=1024,
+                    extra={"pair_frac": pair_frac, "pair_rmax": 4})
+
+
 def cubic(R: int = 152, L: int = 32, hops: int = 1_000_000) -> Workload:
     """The cubic lattice the paper's conclusions name as the next extension:
     L x L x L sites (N = 32768 for L=32), nu=1/2, phi ~ U[-0.5, 0.5], xi=1,

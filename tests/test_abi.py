@@ -84,12 +84,28 @@ def test_create_rejects_bad_parameters_on_host(libcg, bad, msg):
 
 @pytest.mark.parametrize("bad,msg", [(dict(time_mode=2), "time_mode"),
                                      (dict(block_threads=300), "block_threads"),
-                                     (dict(precision=7), "precision")])
+                                     (dict(precision=7), "precision"),
+                                     (dict(pair_frac=1.0, pair_rmax=2), "pair_frac"),
+                                     (dict(pair_frac=-0.1, pair_rmax=2), "pair_frac"),
+                                     (dict(pair_frac=0.1, pair_rmax=0), "pair_rmax"),
+                                     (dict(pair_frac=0.1, pair_rmax=8), "pair_rmax"),
+                                     (dict(pair_frac=0.1, pair_rmax=2, time_mode=1),
+                                      "deterministic time"),
+                                     (dict(pair_frac=0.1, pair_rmax=2, cluster_size=2),
+                                      "one CTA")])
 def test_create_batch_rejects_bad_options_on_host(libcg, bad, msg):
     from paper_1407_5026_gb300 import binding as B
     with pytest.raises(B.CgError) as ei:
         B.cg_create_batch([B.desc(L=16)], B.opts(**bad))
     assert msg in str(ei.value)
+
+
+def test_pair_hops_refuse_the_cubic_lattice_on_host(libcg):
+    from paper_1407_5026_gb300 import binding as B
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create_batch([B.desc(L=16), B.desc(L=8, r_max=2, dim=3)],
+                          B.opts(pair_frac=0.2, pair_rmax=2))
+    assert "square lattices" in str(ei.value)
 
 
 def test_workspace_plan_counts_every_buffer(libcg):
