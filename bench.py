@@ -553,7 +553,8 @@ def other_configs(args, B, local):
     tensor-core refresh per same-L group every 1024 hops), 16 replicas of
     L=256 whose eps is split over a thread-block cluster (refresh every 4096
     hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
-    tensor-core refresh every 1024 hops), and 304 replicas of L=64 with and
+    tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
+    4-CTA clusters (eps split by z-planes), and 304 replicas of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair).  Each is timed with CUDA events over hops that
     follow a relaxation from the random start."""
     import torch
@@ -563,6 +564,7 @@ def other_configs(args, B, local):
             ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
             ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, False),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
+            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False)):
         reps = [r.as_dict() for r in wl.replicas]

@@ -72,7 +72,10 @@ typedef struct cg_handle cg_handle;
  *   dim    0 or 2: the L x L square lattice of the paper; 3: the L x L x L
  *          cubic lattice (the three-dimensional extension named in the
  *          paper's conclusions; L <= 64, hop ball dx^2+dy^2+dz^2 <= r_max^2,
- *          one CTA per replica, binary32 refreshed in binary64)        */
+ *          one CTA per replica or, when eps does not fit one, a cluster
+ *          of 2, 4 or 8 CTAs splitting it by z-planes; binary32 refreshed
+ *          on the tensor cores when L^3 is a multiple of 128, else in
+ *          binary64)                                                    */
 typedef struct {
     int32_t L;
     int32_t r_max;

@@ -149,10 +149,11 @@ cudaError_t launch_pr_persistent_pair(int precision, const DevReplica *d_reps,
                                       int L);
 cudaError_t set_pr_pair_smem_limit(int precision, int bytes);
 // The same chain over a thread-block cluster of `cluster` CTAs per replica
-// (eps split by rows); grid = n_reps * cluster CTAs.
+// (eps split by rows, or by z-planes on the cubic lattice, dim = 3);
+// grid = n_reps * cluster CTAs.
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
                               int n_reps, int cluster, int threads, int smem_bytes,
-                              const RunArgs &args, cudaStream_t st, int L);
+                              const RunArgs &args, cudaStream_t st, int L, int dim);
 cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int tab_entries, int words,
                             int precision, cudaStream_t st);
 cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int tab_entries, int words,

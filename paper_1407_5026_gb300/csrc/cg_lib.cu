@@ -379,12 +379,13 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
 }
 
 // CTAs per replica: 1 when the replica fits one CTA's shared memory, else the
-// smallest cluster of 2, 4 or 8 CTAs (each holding L/C rows of eps) that fits;
-// a forced size is used when it fits.  0 when nothing fits.
+// smallest cluster of 2, 4 or 8 CTAs (each holding L/C rows of eps, or L/C
+// z-planes on the cubic lattice) that fits; a forced size is used when it
+// fits.  0 when nothing fits.
 int choose_cluster(const cg_opts &o, const Rep &r, int optin)
 {
     const int budget = optin - 2048;     // room for the kernels' static shared memory
-    if (dim_of(r.d) == 3 || o.pair_frac > 0.0)   // the cubic lattice and pair hops: one CTA
+    if (o.pair_frac > 0.0)               // two-electron hops: one CTA
         return persistent_smem(r, o.precision, 1) <= budget ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
@@ -885,7 +886,7 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.pair = h->opts.pair_frac > 0.0 ? 1 : 0;
     if (g.cluster > 1)
         CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
-                                  g.cluster, g.threads, g.smem, a, st, g.L));
+                                  g.cluster, g.threads, g.smem, a, st, g.L, g.dim));
     else
         CG_CUDA(launch_pr_persistent(h->opts.precision, h->d_reps, h->d_index + g.first,
                                      g.count, g.threads, g.smem, a, st, g.L, g.dim));

@@ -18,6 +18,9 @@
 //     executed hop is the lowest accepting label of the whole chunk;
 //   * each CTA updates its own rows; a cluster barrier ends the hop so that
 //     the next hop's remote reads see updated energies.
+// On the L x L x L cubic lattice (kDim = 3) CTA `rank` owns the z-planes
+// [rank L/C, (rank+1) L/C) instead of rows, and every CTA holds the
+// (L/2+1)^3 folded table.
 // The wall-clock limit of a hop is decided by rank 0 and published in its
 // exchange slot, so every exit decision is uniform over the cluster.
 #include <cooperative_groups.h>
@@ -34,20 +37,27 @@ struct Slot {
     Cand cand;
 };
 
-template <typename Real>
+// eps of site s, from the CTA that owns its row (square lattice) or z-plane
+// (cubic lattice).
+template <typename Real, int kDim>
 __device__ __forceinline__ Real cluster_eps(coop::cluster_group &cl, Real *local, unsigned s,
                                             int rows_local, int log2L, int L, unsigned magic,
                                             bool pow2, unsigned rank)
 {
-    const int y = pow2 ? (int)(s >> log2L) : (int)__umulhi(s, magic);
-    const unsigned owner = (unsigned)(y / rows_local);
-    const unsigned off = s - owner * (unsigned)(rows_local * L);
+    int slow;
+    if (kDim == 3)
+        slow = pow2 ? (int)(s >> (2 * log2L)) : (int)__umulhi(__umulhi(s, magic), magic);
+    else
+        slow = pow2 ? (int)(s >> log2L) : (int)__umulhi(s, magic);
+    const unsigned owner = (unsigned)(slow / rows_local);
+    const unsigned plane = kDim == 3 ? (unsigned)(L * L) : (unsigned)L;
+    const unsigned off = s - owner * (unsigned)rows_local * plane;
     if (owner == rank) return local[off];
     Real *peer = cl.map_shared_rank(local, owner);
     return peer[off];
 }
 
-template <typename Real, int kThreads, bool kPow2>
+template <typename Real, int kThreads, bool kPow2, int kDim>
 __global__ void __launch_bounds__(kThreads, 1)
 pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
@@ -76,11 +86,14 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const uint32_t key0 = Rg.key0, key1 = Rg.key1, rep = Rg.replica;
     const double T = Rg.T, E = Rg.E;
     const float invTf = (float)(1.0 / T);
-    const int rows_local = L / (int)C, N_local = rows_local * L;
+    // rows (square lattice) or z-planes (cubic lattice) of this CTA
+    const int plane = kDim == 3 ? L * L : L;
+    const int rows_local = L / (int)C, N_local = rows_local * plane;
     const int row0 = (int)rank * rows_local;
     const int log2L = __ffs(L) - 1;
+    const int ntab = kDim == 3 ? H1 * H1 * H1 : H1 * H1;
 
-    const SmemLayout lay = smem_layout(N_local, H1 * H1, V, words, (int)sizeof(Real));
+    const SmemLayout lay = smem_layout(N_local, ntab, V, words, (int)sizeof(Real));
     Shared S;
     S.eps = smem + lay.off_eps;
     S.tinv = smem + lay.off_tinv;
@@ -96,18 +109,19 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
 
     // ---- stage: own rows of eps, full tables and bitmask ----
     {
-        const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps) + (size_t)row0 * L;
+        const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps) + (size_t)row0 * plane;
         for (int l = tid; l < N_local; l += kThreads) eps[l] = eps_g[l];
         const Real *tab_g = (sizeof(Real) == 8)
                                 ? reinterpret_cast<const Real *>(Rg.tinv64)
                                 : reinterpret_cast<const Real *>(Rg.tinv32);
         Real *tab_s = reinterpret_cast<Real *>(S.tinv);
-        for (int l = tid; l < H1 * H1; l += kThreads) tab_s[l] = tab_g[l];
+        for (int l = tid; l < ntab; l += kThreads) tab_s[l] = tab_g[l];
         for (int l = tid; l < words; l += kThreads) S.occ[l] = Rg.occ[l];
         for (int l = tid; l < kGuide; l += kThreads) S.guide[l] = Rg.guide[l];
         for (int l = tid; l < V; l += kThreads) {
             const int dxy = Rg.disp[l];
-            const int dx = (int)(short)(dxy & 0xffff);
+            // dx of the packed vector (10-bit fields on the cubic lattice)
+            const int dx = kDim == 3 ? (dxy << 22) >> 22 : (int)(short)(dxy & 0xffff);
             S.thr[l] = Rg.thr[l];
             S.disp[l] = dxy;
             S.vr64[l] = Rg.tinvd[l];
@@ -174,10 +188,10 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 const unsigned base = kb + rank * sub;
                 const bool mine = (unsigned)tid < half;
                 const unsigned k0 = base + (unsigned)tid, k1 = k0 + half;
-                const Prop p0 = propose<kPow2>(S, k0, PP, key0, key1, L, log2L, (unsigned)N,
-                                               magic, thr_last, mine && k0 < M);
-                const Prop p1 = propose<kPow2>(S, k1, PP, key0, key1, L, log2L, (unsigned)N,
-                                               magic, thr_last, mine && k1 < M);
+                const Prop p0 = propose<kPow2, kDim>(S, k0, PP, key0, key1, L, log2L,
+                                                     (unsigned)N, magic, thr_last, mine && k0 < M);
+                const Prop p1 = propose<kPow2, kDim>(S, k1, PP, key0, key1, L, log2L,
+                                                     (unsigned)N, magic, thr_last, mine && k1 < M);
                 double dE0 = 0.0, dE1 = 0.0;
                 bool acc0 = false, acc1 = false;
                 Real ei0 = 0, ej0 = 0, ei1 = 0, ej1 = 0;
@@ -188,13 +202,13 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                     acc1 = mine && k1 < M && u1 < a.toy_A0;
                 } else {
                     if (p0.theta) {
-                        ei0 = cluster_eps<Real>(cl, eps, p0.i, rows_local, log2L, L, magic, kPow2, rank);
-                        ej0 = cluster_eps<Real>(cl, eps, p0.j, rows_local, log2L, L, magic, kPow2, rank);
+                        ei0 = cluster_eps<Real, kDim>(cl, eps, p0.i, rows_local, log2L, L, magic, kPow2, rank);
+                        ej0 = cluster_eps<Real, kDim>(cl, eps, p0.j, rows_local, log2L, L, magic, kPow2, rank);
                         acc0 = accept_vals<Real>(ei0, ej0, S, p0, T, invTf, dE0);
                     }
                     if (p1.theta) {
-                        ei1 = cluster_eps<Real>(cl, eps, p1.i, rows_local, log2L, L, magic, kPow2, rank);
-                        ej1 = cluster_eps<Real>(cl, eps, p1.j, rows_local, log2L, L, magic, kPow2, rank);
+                        ei1 = cluster_eps<Real, kDim>(cl, eps, p1.i, rows_local, log2L, L, magic, kPow2, rank);
+                        ej1 = cluster_eps<Real, kDim>(cl, eps, p1.j, rows_local, log2L, L, magic, kPow2, rank);
                         acc1 = accept_vals<Real>(ei1, ej1, S, p1, T, invTf, dE1);
                     }
                 }
@@ -277,7 +291,8 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
 
         // ---- commit (step 3a, 3c): every CTA flips its bitmask copy ----
         const unsigned ci = win.i, cj = win.j;
-        const int cdx = (int)(short)(win.dxy & 0xffff), cdy = win.dxy >> 16;
+        const int cdx = kDim == 3 ? (win.dxy << 22) >> 22 : (int)(short)(win.dxy & 0xffff);
+        const int cdy = kDim == 3 ? (win.dxy << 12) >> 22 : win.dxy >> 16;
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
@@ -312,7 +327,31 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         rounds += 1;
 
         // ---- local-energy update of this CTA's rows (step 3b) ----
-        if (!a.toy && tid < active) {
+        if (kDim == 3 && !a.toy && tid < active) {
+            // thread -> column x = ux of the (z, y) rows uy0, uy0 + rows_per_pass,
+            // ... of this CTA's planes (row r = zl L + y, site r L + x)
+            int xi, yi, zi, xj, yj, zj;
+            if (kPow2) {
+                const int m = L - 1;
+                xi = (int)ci & m; yi = (int)(ci >> log2L) & m; zi = (int)(ci >> (2 * log2L));
+                xj = (int)cj & m; yj = (int)(cj >> log2L) & m; zj = (int)(cj >> (2 * log2L));
+            } else {
+                const unsigned qi = __umulhi(ci, magic), qj = __umulhi(cj, magic);
+                xi = (int)(ci - qi * (unsigned)L); zi = (int)__umulhi(qi, magic);
+                yi = (int)qi - zi * L;
+                xj = (int)(cj - qj * (unsigned)L); zj = (int)__umulhi(qj, magic);
+                yj = (int)qj - zj * L;
+            }
+            const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
+            for (int r = uy0; r < rows_local * L; r += rows_per_pass) {
+                const int zl = kPow2 ? (r >> log2L) : (int)__umulhi((unsigned)r, magic);
+                const int y = r - zl * L, z = row0 + zl;
+                const int oj = (fold_axis(z - zj, L) * H1 + fold_axis(y - yj, L)) * H1 + fxj;
+                const int oi = (fold_axis(z - zi, L) * H1 + fold_axis(y - yi, L)) * H1 + fxi;
+                Real *e = eps + r * L + ux;
+                *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[oj], tinv[oi]));
+            }
+        } else if (!a.toy && tid < active) {
             int yi, xi, yj, xj;
             if (kPow2) {
                 yi = (int)(ci >> log2L); xi = (int)ci & (L - 1);
@@ -337,7 +376,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
 
     // ---- store back: own rows of eps; rank 0 the bitmask and counters ----
     {
-        Real *eps_g = reinterpret_cast<Real *>(Rg.eps) + (size_t)row0 * L;
+        Real *eps_g = reinterpret_cast<Real *>(Rg.eps) + (size_t)row0 * plane;
         for (int l = tid; l < N_local; l += kThreads) eps_g[l] = eps[l];
         if (rank == 0)
             for (int l = tid; l < words; l += kThreads) Rg.occ[l] = S.occ[l];
@@ -358,12 +397,12 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
 }
 
-template <typename Real, int kThreads, bool kPow2>
-static cudaError_t launch_cluster_t(const DevReplica *d_reps, const int *d_index, int n_reps,
+template <typename Real, int kThreads, bool kPow2, int kDim>
+static cudaError_t launch_cluster_d(const DevReplica *d_reps, const int *d_index, int n_reps,
                                     int cluster, int smem_bytes, const RunArgs &args,
                                     cudaStream_t st)
 {
-    auto kern = pr_cluster<Real, kThreads, kPow2>;
+    auto kern = pr_cluster<Real, kThreads, kPow2, kDim>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes);
     if (e) return e;
@@ -382,35 +421,47 @@ static cudaError_t launch_cluster_t(const DevReplica *d_reps, const int *d_index
     return cudaLaunchKernelEx(&cfg, kern, d_reps, d_index, args);
 }
 
+template <typename Real, int kThreads, bool kPow2>
+static cudaError_t launch_cluster_t(const DevReplica *d_reps, const int *d_index, int n_reps,
+                                    int cluster, int smem_bytes, const RunArgs &args,
+                                    cudaStream_t st, int dim)
+{
+    return dim == 3 ? launch_cluster_d<Real, kThreads, kPow2, 3>(d_reps, d_index, n_reps, cluster,
+                                                                 smem_bytes, args, st)
+                    : launch_cluster_d<Real, kThreads, kPow2, 2>(d_reps, d_index, n_reps, cluster,
+                                                                 smem_bytes, args, st);
+}
+
 template <typename Real>
 static cudaError_t launch_cluster_p(const DevReplica *d_reps, const int *d_index, int n_reps,
                                     int cluster, int threads, int smem_bytes,
-                                    const RunArgs &args, cudaStream_t st, bool pow2)
+                                    const RunArgs &args, cudaStream_t st, bool pow2, int dim)
 {
     if (threads == 1024)
         return pow2 ? launch_cluster_t<Real, 1024, true>(d_reps, d_index, n_reps, cluster,
-                                                         smem_bytes, args, st)
+                                                         smem_bytes, args, st, dim)
                     : launch_cluster_t<Real, 1024, false>(d_reps, d_index, n_reps, cluster,
-                                                          smem_bytes, args, st);
+                                                          smem_bytes, args, st, dim);
     if (threads == 512)
         return pow2 ? launch_cluster_t<Real, 512, true>(d_reps, d_index, n_reps, cluster,
-                                                        smem_bytes, args, st)
+                                                        smem_bytes, args, st, dim)
                     : launch_cluster_t<Real, 512, false>(d_reps, d_index, n_reps, cluster,
-                                                         smem_bytes, args, st);
+                                                         smem_bytes, args, st, dim);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
                               int n_reps, int cluster, int threads, int smem_bytes,
-                              const RunArgs &args, cudaStream_t st, int L)
+                              const RunArgs &args, cudaStream_t st, int L, int dim)
 {
-    if (cluster < 2 || cluster > 8 || (L % cluster) != 0) return cudaErrorInvalidValue;
+    if (cluster < 2 || cluster > 8 || (L % cluster) != 0 || threads < L)
+        return cudaErrorInvalidValue;
     const bool pow2 = (L & (L - 1)) == 0;
     return precision == CG_FP64
                ? launch_cluster_p<double>(d_reps, d_index, n_reps, cluster, threads, smem_bytes,
-                                          args, st, pow2)
+                                          args, st, pow2, dim)
                : launch_cluster_p<float>(d_reps, d_index, n_reps, cluster, threads, smem_bytes,
-                                         args, st, pow2);
+                                         args, st, pow2, dim);
 }
 
 }  // namespace cg

@@ -9,7 +9,9 @@ batch that mixes square and cubic replicas keeps each chain exact; the
 stochastic clock of step 3c is exact in 3D too; in binary32 (refreshed in
 binary64) eps stays within 1e-4 of its definition; the split-BF16 tensor-core
 refresh on cubic tables (N = L^3 a multiple of 128) gives eps within 5e-5 of
-its definition, alone and inside runs.
+its definition, alone and inside runs; on thread-block clusters (eps split
+by z-planes) binary64 stays bit-exact and binary32 lattices beyond one CTA
+(L = 40, 48) refresh within 1e-4.
 """
 import numpy as np
 import pytest
@@ -183,5 +185,51 @@ def test_cubic_tensor_core_refresh_in_runs(B):
             assert np.abs(eps - ref.site_energies_fft3(n, phi, 0.5, 16)).max() <= 1e-4
             o = s.observables(k)
             assert o["refreshes"] == 4 and o["max_eps_err_last_refresh"] <= 1e-4
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("L,cluster,E", [(16, 2, 0.01), (16, 4, 0.0), (16, 8, 0.03),
+                                         (24, 2, 0.02), (24, 8, 0.01)])
+def test_cubic_cluster_trajectory_bit_exact(B, L, cluster, E):
+    p = _cubic(L=L, r_max=3, T=0.1, E=E, seed=6, replica=1)
+    s = B.System([p], precision=B.CG_FP64, cluster_size=cluster)
+    try:
+        assert B.cg_group_shape(s.h, 0)["cluster"] == cluster
+        rc, log = s.run_logged(1500, 512)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p)
+        _, olog = ch.run(1500, 512, log=True)
+        _assert_same(B, s, 0, p, ch, log[0], olog)
+    finally:
+        s.close()
+
+
+def test_cubic_cluster_stochastic_clock(B):
+    p = _cubic(L=16, r_max=2, seed=3)
+    s = B.System([p], precision=B.CG_FP64, cluster_size=4, time_mode=B.CG_TIME_GAUSSIAN)
+    try:
+        s.run(800, 256)
+        ch = _oracle_for(p)
+        ch.set_time_mode(1)
+        ch.run(800, 256)
+        assert s.state(0)[3]["time"] == ch.counters()["time"]
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("L,R,cluster", [(40, 8, 2), (48, 8, 4)])
+def test_cubic_binary32_beyond_one_cta(B, L, R, cluster):
+    reps = [_cubic(L=L, r_max=3, T=0.05, seed=s, replica=s) for s in range(R)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=512)
+    try:
+        sh = B.cg_group_shape(s.h, 0)
+        assert sh["cluster"] == cluster
+        s.run(3 * 512 + 40, 1024)
+        for k in (0, R - 1):
+            n, eps, phi, _ = s.state(k)
+            assert np.abs(eps - ref.site_energies_fft3(n, phi, 0.5, L)).max() <= 1e-4
+            o = s.observables(k)
+            assert o["refreshes"] == 3 and o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()
