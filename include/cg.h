@@ -385,6 +385,23 @@ int cg_debug_gauss(const uint64_t *seed_host, const uint32_t *replica_host,
  * error; allocates and frees device memory internally. */
 int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *v_host, int n);
 
+/* Density of states of the local energies: the histogram g(eps) whose
+ * Coulomb gap the paper discusses (section "Results for the lattice model in
+ * two dimensions", single-particle density of states).  For the sites s of
+ * replicas first .. first+count-1 (handle order), with x = (eps_s - lo) *
+ * (nbins / (hi - lo)) (eps widened to binary64, each operation rounded once,
+ * the scale computed once in binary64): a site with eps_s >= lo and
+ * x < nbins adds 1 to counts_dev[floor(x)]; other sites are not counted.
+ *   counts_dev  DEVICE array of nbins uint64, owned by the caller; the
+ *               counts are ADDED to it (zero it first; repeated calls sum
+ *               snapshots over time without leaving the device)
+ *   nbins       1 .. 4096;  lo < hi, both finite
+ * Enqueued on the handle's stream after its pending work; returns without
+ * waiting (read counts_dev after cg_sync).  Allocates nothing.  CG_EINVAL
+ * for bad arguments, CG_ECUDA on a launch error. */
+int cg_eps_histogram(cg_handle *h, int first, int count, int nbins, double lo, double hi,
+                     uint64_t *counts_dev);
+
 /* Library version string. */
 const char *cg_version(void);
 

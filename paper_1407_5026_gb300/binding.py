@@ -33,7 +33,7 @@ EXPORTED = [
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_debug_tower", "cg_version",
     "cg_group_replicas", "cg_read_group_state", "cg_write_group_state", "cg_debug_gauss",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
-    "cg_set_trace", "cg_read_trace",
+    "cg_set_trace", "cg_read_trace", "cg_eps_histogram",
 ]
 
 
@@ -157,6 +157,8 @@ def load(path: str | None = None):
             "cg_debug_tower": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u32p,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
             "cg_version": (ctypes.c_char_p, []),
+            "cg_eps_histogram": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, vp]),
             "cg_refresh_tc_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      vp, vp, vp, vp, vp]),
             "cg_autotune": (ctypes.c_int, [vp, ctypes.c_uint32]),
@@ -469,6 +471,13 @@ def cg_debug_tower(h, replica, x1):
     return out
 
 
+def cg_eps_histogram(h, first, count, nbins, lo, hi, counts_dev_ptr):
+    """Add the g(eps) counts of replicas first..first+count-1 to the device
+    array of nbins uint64 at counts_dev_ptr (enqueued; cg_sync to read)."""
+    return _check(load().cg_eps_histogram(h, int(first), int(count), int(nbins), float(lo),
+                                          float(hi), ctypes.c_void_p(int(counts_dev_ptr))))
+
+
 class System:
     """Owns one libcg handle over R replicas, with device memory and the
     stream supplied by PyTorch."""
@@ -490,6 +499,7 @@ class System:
                          cluster_size=cluster_size, use_graph=use_graph, time_mode=time_mode,
                          pair_frac=pair_frac, pair_rmax=pair_rmax)
         self.workspace = None
+        self.device = device
         if torch_memory:
             nbytes = cg_workspace_bytes(self.reps, self.opts)
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
@@ -522,6 +532,18 @@ class System:
 
     def observables(self, replica=0):
         return cg_observables(self.h, replica)
+
+    def eps_histogram(self, nbins, lo, hi, first=0, count=None, counts=None):
+        """g(eps) counts of the replicas as a device int64 tensor (uint64
+        bits); pass ``counts`` to keep adding snapshots into the same one."""
+        import torch
+        if count is None:
+            count = len(self.reps) - first
+        if counts is None:
+            counts = torch.zeros(int(nbins), dtype=torch.int64, device=f"cuda:{self.device}")
+        cg_eps_histogram(self.h, first, count, nbins, lo, hi, counts.data_ptr())
+        cg_sync(self.h)
+        return counts
 
     def group_dims(self, group):
         if not hasattr(self, "_dims"):

@@ -188,6 +188,42 @@ __global__ void debug_tower_kernel(const unsigned short *guide, const unsigned *
     out[t] = x1[t] > thr[V - 1] ? -1 : tower_lookup(guide, thr, x1[t]);
 }
 
+// g(eps): one CTA per (chunk of sites, replica) builds a shared-memory
+// histogram and adds it to the output; bin floor((eps - lo) * scale) in
+// binary64, for eps >= lo and (eps - lo) * scale < nbins.
+template <typename Real>
+__global__ void eps_histogram_kernel(const DevReplica *__restrict__ reps, int nbins, double lo,
+                                     double scale, unsigned long long *__restrict__ out)
+{
+    extern __shared__ unsigned int hist[];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    const DevReplica &R = reps[blockIdx.y];
+    const Real *eps = reinterpret_cast<const Real *>(R.eps);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < R.N; s += gridDim.x * blockDim.x) {
+        const double e = (double)eps[s];
+        const double x = d_mul(d_sub(e, lo), scale);
+        if (e >= lo && x < (double)nbins) atomicAdd(&hist[(int)floor(x)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (hist[b]) atomicAdd(&out[b], (unsigned long long)hist[b]);
+}
+
+cudaError_t launch_eps_histogram(const DevReplica *d_reps, int count, int max_N, int precision,
+                                 int nbins, double lo, double scale, unsigned long long *out,
+                                 cudaStream_t st)
+{
+    const int per = (max_N + 255) / 256;
+    const dim3 grid((unsigned)(per < 16 ? per : 16), (unsigned)count);
+    const size_t smem = sizeof(unsigned int) * (size_t)nbins;
+    if (precision == CG_FP64)
+        eps_histogram_kernel<double><<<grid, 256, smem, st>>>(d_reps, nbins, lo, scale, out);
+    else
+        eps_histogram_kernel<float><<<grid, 256, smem, st>>>(d_reps, nbins, lo, scale, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr, int V,
                                const uint32_t *x1, int *out, int n, cudaStream_t st)
 {

@@ -167,6 +167,11 @@ cudaError_t launch_debug_tower(const unsigned short *guide, const unsigned *thr,
                                const uint32_t *x1, int *out, int n, cudaStream_t st);
 cudaError_t set_pr_smem_limit(int precision, int bytes);
 int microbench(int kind, int device, double *result);
+// Histogram of eps (binary64 or binary32 by precision) of `count` replicas
+// starting at d_reps, added to the nbins counters at out.
+cudaError_t launch_eps_histogram(const DevReplica *d_reps, int count, int max_N, int precision,
+                                 int nbins, double lo, double scale, unsigned long long *out,
+                                 cudaStream_t st);
 cudaError_t launch_reset_refresh_err(const DevReplica *d_reps, const int *d_index, int R,
                                      cudaStream_t st);
 // log2 of the factor applied to 1/r before its binary16 split (cubic lattice)

@@ -1592,6 +1592,24 @@ int cg_debug_gauss(const uint64_t *seed_host, const uint32_t *replica_host,
     return CG_OK;
 }
 
+int cg_eps_histogram(cg_handle *h, int first, int count, int nbins, double lo, double hi,
+                     uint64_t *counts_dev)
+{
+    if (!h || !counts_dev) return fail(CG_EINVAL, "cg_eps_histogram: null handle or output");
+    if (first < 0 || count < 1 || first + count > (int)h->reps.size())
+        return fail(CG_EINVAL, "cg_eps_histogram: replicas out of range");
+    if (nbins < 1 || nbins > 4096) return fail(CG_EINVAL, "cg_eps_histogram: nbins must be 1..4096");
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi))
+        return fail(CG_EINVAL, "cg_eps_histogram: need finite lo < hi");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    int max_N = 0;
+    for (int k = first; k < first + count; ++k) max_N = std::max(max_N, h->reps[k].N);
+    const double scale = (double)nbins / (hi - lo);
+    CG_CUDA(launch_eps_histogram(h->d_reps + first, count, max_N, h->opts.precision, nbins, lo,
+                                 scale, reinterpret_cast<unsigned long long *>(counts_dev), h->st));
+    return CG_OK;
+}
+
 int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *v_host, int n)
 {
     if (!h || n <= 0 || !x1_host || !v_host) return fail(CG_EINVAL, "bad arguments");
