@@ -296,6 +296,11 @@ struct cg_handle {
     double toy_A0 = 0.0;
     cg_hop *d_log = nullptr;
     bool pending = false;
+    // pinned host copies of every replica's counter block (group order) and
+    // of each group's refresh error word, read back in one copy per group
+    // when a run is collected
+    DevCounters *h_ctr = nullptr;
+    int *h_err = nullptr;
     cudaEvent_t fork = nullptr;      // fork event for the groups' side streams
     cg_trace_point *d_trace = nullptr;
     int trace_cap = 0;
@@ -823,6 +828,12 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         destroy_partial();
         return nullptr;
     }
+    if (cudaMallocHost((void **)&h->h_ctr, sizeof(DevCounters) * (size_t)R) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_err, sizeof(int) * h->groups.size()) != cudaSuccess) {
+        fail(CG_ECUDA, "pinned host buffers could not be allocated");
+        destroy_partial();
+        return nullptr;
+    }
     return h.release();
 }
 
@@ -969,28 +980,33 @@ int enqueue_run_graph(cg_handle *h, unsigned long long n_hops, unsigned M)
 
 int finish_run(cg_handle *h)
 {
+    // a group's counter blocks are contiguous: one copy per group (and one
+    // per refresh error word) into pinned memory, queued behind the run
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+        const Group &g = h->groups[gi];
+        CG_CUDA(cudaMemcpyAsync(h->h_ctr + g.first, h->reps[h->order[g.first]].d_ctr,
+                                sizeof(DevCounters) * (size_t)g.count, cudaMemcpyDeviceToHost,
+                                h->st));
+        if (g.tc)
+            CG_CUDA(cudaMemcpyAsync(h->h_err + gi, g.d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    h->st));
+    }
     CG_CUDA(cudaStreamSynchronize(h->st));
     h->pending = false;
-    std::vector<DevCounters> c(h->reps.size());
-    for (size_t k = 0; k < h->reps.size(); ++k)
-        CG_CUDA(cudaMemcpyAsync(&c[k], h->reps[k].d_ctr, sizeof(DevCounters),
-                                cudaMemcpyDeviceToHost, h->st));
-    CG_CUDA(cudaStreamSynchronize(h->st));
     int rc = CG_OK;
-    for (size_t k = 0; k < c.size(); ++k) {
+    for (size_t k = 0; k < h->reps.size(); ++k) {
+        const DevCounters &c = h->h_ctr[k];
         double e;
-        std::memcpy(&e, &c[k].max_err_bits, 8);
+        std::memcpy(&e, &c.max_err_bits, 8);
         h->max_err_run = std::max(h->max_err_run, e);
-        if (c[k].status == CG_ESTUCK) rc = fail(CG_ESTUCK, "a replica reached max rounds per hop");
-        if (c[k].status == CG_ETIMEOUT)
+        if (c.status == CG_ESTUCK) rc = fail(CG_ESTUCK, "a replica reached max rounds per hop");
+        if (c.status == CG_ETIMEOUT)
             rc = fail(CG_ETIMEOUT, "a hop exceeded the device time limit");
     }
-    for (const Group &g : h->groups) {
-        if (!g.tc) continue;
-        int err = 0;
-        CG_CUDA(cudaMemcpy(&err, g.d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) {
-            CG_CUDA(cudaMemset(g.d_err, 0, sizeof(int)));
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+        const Group &g = h->groups[gi];
+        if (g.tc && h->h_err[gi]) {
+            CG_CUDA(cudaMemsetAsync(g.d_err, 0, sizeof(int), h->st));
             rc = fail(CG_ETIMEOUT, "a tensor-core refresh wait exceeded its time limit");
         }
     }
@@ -1054,6 +1070,8 @@ void cg_destroy(cg_handle *h)
     }
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    if (h->h_err) cudaFreeHost(h->h_err);
     delete h;
 }
 
@@ -1181,14 +1199,12 @@ int cg_read_group_state(cg_handle *h, int group, uint32_t *occ_words_host, void 
     if (eps_host)
         CG_CUDA(cudaMemcpyAsync(eps_host, r0.d_eps, cnt * r0.N * rb, cudaMemcpyDeviceToHost,
                                 h->st));
-    std::vector<DevCounters> dc;
-    if (c_host) {
-        dc.resize(cnt);
-        CG_CUDA(cudaMemcpyAsync(dc.data(), r0.d_ctr, cnt * sizeof(DevCounters),
-                                cudaMemcpyDeviceToHost, h->st));
-    }
+    DevCounters *dc = h->h_ctr + g.first;      // pinned, group order
+    if (c_host)
+        CG_CUDA(cudaMemcpyAsync(dc, r0.d_ctr, cnt * sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                h->st));
     CG_CUDA(cudaStreamSynchronize(h->st));
-    for (size_t k = 0; k < dc.size(); ++k) {
+    for (size_t k = 0; c_host && k < cnt; ++k) {
         c_host[k].rounds = dc[k].rounds; c_host[k].hops = dc[k].hops;
         c_host[k].attempts = dc[k].attempts; c_host[k].evaluated = dc[k].evaluated;
         c_host[k].P = dc[k].P; c_host[k].energy = dc[k].energy;
@@ -1229,8 +1245,8 @@ int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host
     if (c_host) {
         // the public counters are replaced; the library's own fields (chunk
         // statistics, refresh record, trace state, phase clocks) are kept
-        std::vector<DevCounters> dc(cnt);
-        CG_CUDA(cudaMemcpyAsync(dc.data(), r0.d_ctr, cnt * sizeof(DevCounters),
+        DevCounters *dc = h->h_ctr + g.first;  // pinned, group order
+        CG_CUDA(cudaMemcpyAsync(dc, r0.d_ctr, cnt * sizeof(DevCounters),
                                 cudaMemcpyDeviceToHost, h->st));
         CG_CUDA(cudaStreamSynchronize(h->st));
         for (size_t k = 0; k < cnt; ++k) {
@@ -1239,7 +1255,7 @@ int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host
             dc[k].P = c_host[k].P; dc[k].energy = c_host[k].energy;
             dc[k].time = c_host[k].time;
         }
-        CG_CUDA(cudaMemcpyAsync(r0.d_ctr, dc.data(), cnt * sizeof(DevCounters),
+        CG_CUDA(cudaMemcpyAsync(r0.d_ctr, dc, cnt * sizeof(DevCounters),
                                 cudaMemcpyHostToDevice, h->st));
     }
     CG_CUDA(cudaStreamSynchronize(h->st));
