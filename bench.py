@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--obs-hops", type=int, default=32768)
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-m-sweep", action="store_true")
+    ap.add_argument("--sigma-hops", type=int, default=200_000,
+                    help="hops per replica of the L=256 sigma(t) comparison (0 skips it)")
     ap.add_argument("--clocks-dir", default=None,
                     help="folder for the raw nvidia-smi clock samples (default: the temp folder)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,6 +395,27 @@ def run_ours(args):
         "peaks_measured": {"smem_rmw32_GBps": smem_peak / 1e9, "dadd_per_s": dadd_peak},
         "wall_s_timed": t_wall,
     }
+    # M sweep of the same relaxed batch: one refresh period of hops per M,
+    # the persistent launch timed with events (M changes which labels are
+    # drawn, not the chain's law)
+    if not args.no_m_sweep:
+        sweep = {}
+        for Ms in (1024, 4096, 16384, 65536):
+            o0 = [B.cg_observables(sysm.h, k) for k in range(R)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            with torch.cuda.stream(st):
+                ev[0].record(st)
+                B.cg_run_async(sysm.h, HOPS_PER_STEP, Ms)
+                ev[1].record(st)
+                B.cg_refresh_async(sysm.h)
+            assert B.cg_sync(sysm.h) == B.CG_OK
+            o1 = [B.cg_observables(sysm.h, k) for k in range(R)]
+            dt = ev[0].elapsed_time(ev[1]) * 1e-3
+            d = {f: sum(b[f] - a[f] for a, b in zip(o0, o1)) for f in ("hops", "attempts",
+                                                                          "evaluated")}
+            sweep[str(Ms)] = {"hops_per_s": d["hops"] / dt, "attempts_per_s": d["attempts"] / dt,
+                              "labels_evaluated_per_s": d["evaluated"] / dt}
+        result["m_sweep"] = sweep
     # the relaxed batch state, the starting point of the end-to-end measurement
     snapshot = None if args.no_e2e else {
         g: sysm.read_group(g) for g in range(B.cg_num_groups(sysm.h))}
@@ -475,6 +499,10 @@ def run_ours(args):
     # workload): throughput of their own launch paths
     if not args.no_other_configs and rank == 0:
         result["other_configs"] = other_configs(args, B, local)
+
+    # sigma(t) relaxation at L=256: binary32 form against the binary64 form
+    if args.sigma_hops > 0 and not args.no_other_configs and rank == 0:
+        result["sigma_L256_fp32_vs_fp64"] = sigma_l256(B, local, args.sigma_hops)
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, run one step, read the state back
@@ -597,6 +625,45 @@ def other_configs(args, B, local):
             out[name]["pair_hops_share"] = pair_share(B, s, reps, wl.M)
         s.close()
     return out
+
+
+def sigma_l256(B, local, hops, R=16, points_per_decade=5.0, first_time=1e-3):
+    """sigma(t) relaxation curves (Eq. 3) of the L=256 workload in the binary32
+    form (cluster kernel, refresh every 4096 hops) against the binary64 form
+    (8-CTA clusters), same seeds: each replica's trace records P at the
+    log-spaced times t_k (point k of both runs belongs to t_k), so the window
+    sigma_k = (P_{k+1} - P_k) / (N E (t_{k+1} - t_k)) pairs across the forms
+    and the paired differences over the replicas give one z per window."""
+    import numpy as np
+    from paper_1407_5026_gb300 import workloads as W
+    wl = W.l256(R=R)
+    reps = [r.as_dict() for r in wl.replicas]
+    N, E = 256 * 256, wl.replicas[0].E
+    cap = 128
+    sig, tmid, shape = {}, {}, {}
+    for name, prec in (("fp32", B.CG_FP32), ("fp64", B.CG_FP64)):
+        s = B.System(reps, precision=prec, device=local,
+                     refresh_every=wl.refresh_every if prec == B.CG_FP32 else 0)
+        B.cg_set_trace(s.h, first_time=first_time, points_per_decade=points_per_decade,
+                       capacity=cap)
+        assert s.run(hops, wl.M) == B.CG_OK
+        tr = [B.cg_read_trace(s.h, k, cap) for k in range(R)]
+        K = min(len(t) for t in tr)
+        t = np.array([x["time"][:K] for x in tr], dtype=np.float64)
+        Pk = np.array([x["P"][:K] for x in tr], dtype=np.float64)
+        sig[name] = np.diff(Pk, axis=1) / (N * E * np.diff(t, axis=1))
+        tmid[name] = 0.5 * (t[:, 1:] + t[:, :-1]).mean(axis=0)
+        shape[name] = B.cg_group_shape(s.h, 0)["cluster"]
+        s.close()
+    K = min(sig["fp32"].shape[1], sig["fp64"].shape[1])
+    d = sig["fp32"][:, :K] - sig["fp64"][:, :K]
+    se = d.std(axis=0, ddof=1) / np.sqrt(R)
+    z = np.where(se > 0, d.mean(axis=0) / np.where(se > 0, se, 1.0), 0.0)
+    return {"replicas": R, "hops_per_replica": hops, "windows": int(K),
+            "clusters": shape, "t": tmid["fp64"][:K].round(6).tolist(),
+            "sigma_fp32": sig["fp32"][:, :K].mean(axis=0).round(6).tolist(),
+            "sigma_fp64": sig["fp64"][:, :K].mean(axis=0).round(6).tolist(),
+            "max_abs_z": float(np.abs(z).max()), "rms_z": float(np.sqrt((z ** 2).mean()))}
 
 
 def pair_share(B, s, reps, M, hops=64):
