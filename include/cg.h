@@ -121,8 +121,8 @@ typedef struct {
                                    conclusions as an extension): a label is a
                                    pair proposal iff its fourth Philox word is
                                    below floor(p2 2^32).  0 = single hops only.
-                                   Square lattices on one CTA with the
-                                   deterministic time only (else CG_EINVAL);
+                                   Square lattices on one CTA only (else
+                                   CG_EINVAL);
                                    Gamma becomes N Z / (1 - floor(p2 2^32) 2^-32) */
 } cg_opts;
 

@@ -142,12 +142,18 @@ cudaError_t launch_pr_persistent3(int precision, const DevReplica *d_reps, const
                                   cudaStream_t st, int L);
 cudaError_t set_pr3_smem_limit(int precision, int bytes);
 // The two-electron-hop instances (cg_pr_kernel_pair.cu): square lattice, one
-// CTA per replica, deterministic time.
+// CTA per replica.
 cudaError_t launch_pr_persistent_pair(int precision, const DevReplica *d_reps,
                                       const int *d_index, int n_ctas, int threads,
                                       int smem_bytes, const RunArgs &args, cudaStream_t st,
                                       int L);
 cudaError_t set_pr_pair_smem_limit(int precision, int bytes);
+// ... and with the stochastic clock (cg_pr_kernel_pair_time.cu).
+cudaError_t launch_pr_persistent_pair_time(int precision, const DevReplica *d_reps,
+                                           const int *d_index, int n_ctas, int threads,
+                                           int smem_bytes, const RunArgs &args, cudaStream_t st,
+                                           int L);
+cudaError_t set_pr_pair_time_smem_limit(int precision, int bytes);
 // The same chain over a thread-block cluster of `cluster` CTAs per replica
 // (eps split by rows, or by z-planes on the cubic lattice, dim = 3);
 // grid = n_reps * cluster CTAs.

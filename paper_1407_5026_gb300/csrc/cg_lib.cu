@@ -628,9 +628,8 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         return nullptr;
     }
     if (o.pair_frac > 0.0) {
-        if (o.time_mode != CG_TIME_DETERMINISTIC || o.cluster_size > 1) {
-            fail(CG_EINVAL, "two-electron hops run on one CTA per replica with the "
-                            "deterministic time");
+        if (o.cluster_size > 1) {
+            fail(CG_EINVAL, "two-electron hops run on one CTA per replica");
             return nullptr;
         }
         for (int k = 0; k < R; ++k)

@@ -1,6 +1,7 @@
 // cg_pr_kernel_pair.cu -- launches of the persistent parallel-rejection kernel
 // (cg_pr_persistent.cuh) with two-electron hops on the L x L square lattice,
-// L known at run time (a power of two or any even L), deterministic time.
+// L known at run time (a power of two or any even L), deterministic clock
+// (the stochastic-clock instances are in cg_pr_kernel_pair_time.cu).
 #include "cg_pr_persistent.cuh"
 
 namespace cg {
@@ -9,6 +10,9 @@ template <typename Real, int kThreads>
 static cudaError_t launch_pair_t(const DevReplica *d_reps, const int *d_index, int n_ctas,
                                  int smem_bytes, const RunArgs &args, cudaStream_t st, int L)
 {
+    if (args.time_mode)
+        return launch_pr_persistent_pair_time(sizeof(Real) == 8 ? CG_FP64 : CG_FP32, d_reps,
+                                              d_index, n_ctas, kThreads, smem_bytes, args, st, L);
     if ((L & (L - 1)) == 0)
         pr_persistent<Real, kThreads, 0, false, 2, true>
             <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
@@ -33,7 +37,8 @@ static cudaError_t set_pair_one(int bytes)
 
 cudaError_t set_pr_pair_smem_limit(int precision, int bytes)
 {
-    cudaError_t e;
+    cudaError_t e = set_pr_pair_time_smem_limit(precision, bytes);
+    if (e) return e;
     if (precision == CG_FP64) {
         if ((e = set_pair_one<double, 1024>(bytes)) || (e = set_pair_one<double, 512>(bytes)) ||
             (e = set_pair_one<double, 384>(bytes)) || (e = set_pair_one<double, 256>(bytes)))
@@ -51,7 +56,6 @@ cudaError_t launch_pr_persistent_pair(int precision, const DevReplica *d_reps,
                                       int smem_bytes, const RunArgs &args, cudaStream_t st,
                                       int L)
 {
-    if (args.time_mode) return cudaErrorInvalidValue;   // refused on the host first
     if (precision == CG_FP64) {
         switch (threads) {
         case 1024: return launch_pair_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);

@@ -153,3 +153,23 @@ def test_binary32_pair_runs(B):
     finally:
         s32.close()
         s64.close()
+
+
+def test_binary64_pair_stochastic_clock_bit_exact(B):
+    p = dict(L=16, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.3, E=0.02, seed=8, replica=1)
+    s = B.System([p], precision=B.CG_FP64, pair_frac=0.3, pair_rmax=3,
+                 time_mode=B.CG_TIME_GAUSSIAN)
+    try:
+        rc, log = s.run_logged(1200, 256)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p, 0.3, 3)
+        ch.set_time_mode(1)
+        _, olog = ch.run(1200, 256, log=True)
+        for f in FIELDS:
+            np.testing.assert_array_equal(log[0][f], olog[f], err_msg=f)
+        assert (log[0]["k"] != 0xFFFFFFFF).sum() >= 10
+        cnt = s.state(0)[3]
+        assert cnt["time"] == ch.counters()["time"]
+        assert s.observables(0)["time"] == ch.counters()["time"]
+    finally:
+        s.close()
