@@ -160,6 +160,10 @@ cudaError_t set_pr_pair_time_smem_limit(int precision, int bytes);
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
                               int n_reps, int cluster, int threads, int smem_bytes,
                               const RunArgs &args, cudaStream_t st, int L, int dim);
+// Its two-electron-hop instances (cg_pr_cluster_pair.cu; square lattice).
+cudaError_t launch_pr_cluster_pair(int precision, const DevReplica *d_reps, const int *d_index,
+                                   int n_reps, int cluster, int threads, int smem_bytes,
+                                   const RunArgs &args, cudaStream_t st, int L);
 cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int tab_entries, int words,
                             int precision, cudaStream_t st);
 cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int tab_entries, int words,

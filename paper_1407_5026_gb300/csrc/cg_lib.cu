@@ -389,9 +389,9 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
 // fits.  0 when nothing fits.
 int choose_cluster(const cg_opts &o, const Rep &r, int optin)
 {
-    const int budget = optin - 2048;     // room for the kernels' static shared memory
-    if (o.pair_frac > 0.0)               // two-electron hops: one CTA
-        return persistent_smem(r, o.precision, 1) <= budget ? 1 : 0;
+    // room for the kernels' static shared memory (the pair-hop cluster
+    // kernel's exchange slots take it past 2 KiB)
+    const int budget = optin - (o.pair_frac > 0.0 ? 3072 : 2048);
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
         if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
@@ -628,10 +628,6 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         return nullptr;
     }
     if (o.pair_frac > 0.0) {
-        if (o.cluster_size > 1) {
-            fail(CG_EINVAL, "two-electron hops run on one CTA per replica");
-            return nullptr;
-        }
         for (int k = 0; k < R; ++k)
             if (dim_of(reps[k]) != 2 || o.pair_rmax < 1 || 2 * o.pair_rmax >= reps[k].L) {
                 fail(CG_EINVAL, "two-electron hops need square lattices and "

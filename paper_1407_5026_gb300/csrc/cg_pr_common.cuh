@@ -359,13 +359,12 @@ __device__ __forceinline__ bool metropolis64(double dE, uint32_t x2, double T, f
 // the widened energies and the binary64 table when |dH| < 1e-5 (dE_out is
 // then the binary64 value, else 0: the executed pair is widened once).
 template <typename Real, bool kPow2>
-__device__ __forceinline__ bool accept_pair(const Shared &S, const DevReplica &Rg, const Prop &p,
-                                            const PairProp &q, double T, float invTf,
-                                            double &dE_out, int L, int log2L, unsigned magic,
-                                            int H1)
+__device__ __forceinline__ bool accept_pair_vals(Real ei, Real ej, Real ek, Real el,
+                                                 const Shared &S, const DevReplica &Rg,
+                                                 const Prop &p, const PairProp &q, double T,
+                                                 float invTf, double &dE_out, int L, int log2L,
+                                                 unsigned magic, int H1)
 {
-    const Real *eps = reinterpret_cast<const Real *>(S.eps);
-    const Real ei = eps[p.i], ej = eps[p.j], ek = eps[q.k], el = eps[q.l];
     if (sizeof(Real) == 8) {
         const double dE = pair_dE64<kPow2>(S, reinterpret_cast<const double *>(S.tinv),
                                            (double)ei, (double)ej, (double)ek, (double)el, p, q,
@@ -393,17 +392,38 @@ __device__ __forceinline__ bool accept_pair(const Shared &S, const DevReplica &R
     return (float)(p.x2 >> 9) < __fmaf_rn(__expf(-dEf * invTf), 0x1p23f, -0.5f);
 }
 
+template <typename Real, bool kPow2>
+__device__ __forceinline__ bool accept_pair(const Shared &S, const DevReplica &Rg, const Prop &p,
+                                            const PairProp &q, double T, float invTf,
+                                            double &dE_out, int L, int log2L, unsigned magic,
+                                            int H1)
+{
+    const Real *eps = reinterpret_cast<const Real *>(S.eps);
+    return accept_pair_vals<Real, kPow2>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q, T,
+                                         invTf, dE_out, L, log2L, magic, H1);
+}
+
 // dH of an executed pair in binary64 (binary32 form: from the widened
 // energies and the binary64 table, once per hop).
+template <typename Real, bool kPow2>
+__device__ __forceinline__ double pair_hop_dE_vals(Real ei, Real ej, Real ek, Real el,
+                                                   const Shared &S, const DevReplica &Rg,
+                                                   const Prop &p, const PairProp &q, double dE,
+                                                   int L, int log2L, unsigned magic, int H1)
+{
+    if (sizeof(Real) == 8 || dE != 0.0) return dE;
+    return pair_dE64<kPow2>(S, Rg.tinv64, (double)ei, (double)ej, (double)ek, (double)el, p, q,
+                            L, log2L, magic, H1);
+}
+
 template <typename Real, bool kPow2>
 __device__ __forceinline__ double pair_hop_dE(const Shared &S, const DevReplica &Rg,
                                               const Prop &p, const PairProp &q, double dE,
                                               int L, int log2L, unsigned magic, int H1)
 {
-    if (sizeof(Real) == 8 || dE != 0.0) return dE;
-    const float *eps = reinterpret_cast<const float *>(S.eps);
-    return pair_dE64<kPow2>(S, Rg.tinv64, (double)eps[p.i], (double)eps[p.j], (double)eps[q.k],
-                            (double)eps[q.l], p, q, L, log2L, magic, H1);
+    const Real *eps = reinterpret_cast<const Real *>(S.eps);
+    return pair_hop_dE_vals<Real, kPow2>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q,
+                                         dE, L, log2L, magic, H1);
 }
 
 template <typename Real>

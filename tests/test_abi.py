@@ -89,8 +89,7 @@ def test_create_rejects_bad_parameters_on_host(libcg, bad, msg):
                                      (dict(pair_frac=-0.1, pair_rmax=2), "pair_frac"),
                                      (dict(pair_frac=0.1, pair_rmax=0), "pair_rmax"),
                                      (dict(pair_frac=0.1, pair_rmax=8), "pair_rmax"),
-                                     (dict(pair_frac=0.1, pair_rmax=2, cluster_size=2),
-                                      "one CTA")])
+                                     ])
 def test_create_batch_rejects_bad_options_on_host(libcg, bad, msg):
     from paper_1407_5026_gb300 import binding as B
     with pytest.raises(B.CgError) as ei:

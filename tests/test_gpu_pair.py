@@ -173,3 +173,45 @@ def test_binary64_pair_stochastic_clock_bit_exact(B):
         assert s.observables(0)["time"] == ch.counters()["time"]
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("L,cluster", [(32, 2), (48, 4), (64, 8)])
+def test_binary64_pair_cluster_bit_exact(B, L, cluster):
+    # the pair data crosses the cluster: four energies through distributed
+    # shared memory, the second electron in its own exchange slot
+    p = dict(L=L, nu=0.5, W=1.0, xi=1.0, r_max=5, T=0.3, E=0.02, seed=13, replica=2)
+    s = B.System([p], precision=B.CG_FP64, pair_frac=0.3, pair_rmax=4, cluster_size=cluster)
+    try:
+        assert B.cg_group_shape(s.h, 0)["cluster"] == cluster
+        rc, log = s.run_logged(1200, 512)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p, 0.3, 4)
+        _, olog = ch.run(1200, 512, log=True)
+        for f in FIELDS:
+            np.testing.assert_array_equal(log[0][f], olog[f], err_msg=f)
+        np.testing.assert_array_equal(_bits(log[0]["dE"]), _bits(olog["dE"]))
+        assert (log[0]["k"] != 0xFFFFFFFF).sum() >= 10
+        n, eps, _, cnt = s.state(0)
+        on, oeps, _ = ch.state()
+        np.testing.assert_array_equal(n, on)
+        np.testing.assert_array_equal(_bits(eps), _bits(oeps))
+        assert cnt["P"] == ch.counters()["P"]
+    finally:
+        s.close()
+
+
+def test_binary32_pairs_beyond_one_cta(B):
+    # L=256 in binary32 needs a 2-CTA cluster
+    reps = [dict(L=256, nu=0.5, W=1.0, xi=1.5, r_max=10, T=0.05, E=0.005, seed=s, replica=s)
+            for s in range(2)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=2048, pair_frac=0.2, pair_rmax=4)
+    try:
+        assert B.cg_group_shape(s.h, 0)["cluster"] >= 2
+        rc, log = s.run_logged(4500, 4096)
+        assert rc == B.CG_OK
+        assert (log["k"] != 0xFFFFFFFF).sum() >= 5
+        for k in range(2):
+            o = s.observables(k)
+            assert o["refreshes"] == 2 and o["max_eps_err_last_refresh"] <= 1e-4
+    finally:
+        s.close()
