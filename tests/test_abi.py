@@ -113,3 +113,37 @@ def test_workspace_plan_counts_every_buffer(libcg):
     # eps shrinks by 4 bytes per site in binary32 (each buffer 256-aligned)
     assert b64 - b32 == 2 * 256 * 4 + 1024 * 4
     assert b64 % 256 == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # a fresh process whose library path points nowhere: every entry point
+    # goes through load(), which raises instead of falling back to anything
+    import subprocess
+    import sys
+    code = ("from paper_1407_5026_gb300 import binding as B\n"
+            f"B.LIB_PATH = {str(tmp_path / 'libcg.so')!r}\n"
+            "try:\n"
+            "    B.cg_create(16, 0.5, 1.0, 1.0, 4, 0.05, 0.0, 0)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root,
+                         timeout=120)
+    assert "raised: libcg.so not built" in out.stdout, out.stdout + out.stderr
+
+
+def test_product_package_has_no_cpu_path():
+    # the package never imports the oracle, and no module of it computes the
+    # chain in Python: the binding marshals arguments only
+    import ast
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1407_5026_gb300")
+    for name in os.listdir(pkg):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert all(not a.name.startswith("oracle") for a in node.names), name
+            if isinstance(node, ast.ImportFrom):
+                assert not (node.module or "").startswith("oracle"), name
