@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-m-sweep", action="store_true")
+    ap.add_argument("--config", default=None,
+                    help="run only the named other configuration (e.g. cubic_L32_T0.05_R152) "
+                         "and print its result as one JSON line")
     ap.add_argument("--sigma-hops", type=int, default=200_000,
                     help="hops per replica of the L=256 sigma(t) comparison (0 skips it)")
     ap.add_argument("--clocks-dir", default=None,
@@ -265,6 +268,12 @@ def run_ours(args):
     B.load()
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA device")
+    if args.config:
+        # one of the other configurations alone (profiling runs)
+        torch.cuda.set_device(local)
+        print(json.dumps({"config": args.config,
+                          "result": other_configs(args, B, local, only=args.config)}))
+        return
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -574,7 +583,7 @@ def shape_of(B, h, g, tuned):
     return sh
 
 
-def other_configs(args, B, local):
+def other_configs(args, B, local, only=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
     replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
@@ -595,6 +604,8 @@ def other_configs(args, B, local):
             ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False)):
+        if only is not None and name != only:
+            continue
         reps = [r.as_dict() for r in wl.replicas]
         pair = {k: wl.extra[k] for k in ("pair_frac", "pair_rmax") if wl.extra.get("pair_frac")}
         s = B.System(reps, precision=B.CG_FP32, refresh_every=wl.refresh_every,

@@ -87,7 +87,8 @@ cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps, const 
                                  int n_ctas, int threads, int smem_bytes, const RunArgs &args,
                                  cudaStream_t st, int L, int dim)
 {
-    if (threads < L / 2) return cudaErrorInvalidValue;     // the update needs L/2 columns
+    // the square lattice's update needs L/2 columns, the cubic one's L
+    if (threads < L / 2 || (dim == 3 && threads < L)) return cudaErrorInvalidValue;
     if (dim == 3)
         return launch_pr_persistent3(precision, d_reps, d_index, n_ctas, threads, smem_bytes,
                                      args, st, L);

@@ -396,12 +396,17 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                             oi[cz][cy] = ((cz ? Lh - fzi : fzi) * H1 + (cy ? Lh - fyi : fyi)) * H1;
                         }
                     Real *e = eps + (bz * L + by) * L + bx;
+                    // odd base rows take the two x-images in swapped order, so
+                    // the half-warps of consecutive rows (L/2 = 16) touch
+                    // opposite halves of the banks at each access
+                    const int sw = p0 & 1;
 #pragma unroll
                     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
                         for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
-                            for (int cx = 0; cx < 2; ++cx) {
+                            for (int c = 0; c < 2; ++c) {
+                                const int cx = c ^ sw;
                                 const Real ta = (cx ? cj1 : cj0)[oj[cz][cy]];
                                 const Real tb = (cx ? ci1 : ci0)[oi[cz][cy]];
                                 Real *ep = e + cz * Lh * LL + cy * Lh * L + cx * Lh;
