@@ -43,7 +43,10 @@ Parity status of each oracle function (what pins it, in ``tests/``):
                         oracle's own labels against that kernel's row
                         (chi-square); attempt-weighted Boltzmann visits;
                         incremental eps, energy and dipole against scratch;
-                        p2 = 0 equal to the single-hop chain
+                        p2 = 0 equal to the single-hop chain; on the cubic
+                        lattice the pair dH against numpy Eq. 1, detailed
+                        balance of two electrons on a 4^3 torus, and the
+                        labels of a 16-electron state against its kernel row
                         (tests/test_oracle_pair.py).
 """
 from __future__ import annotations
@@ -115,9 +118,9 @@ class Label(ctypes.Structure):
                 ("theta", ctypes.c_int32), ("dE", ctypes.c_double),
                 ("u", ctypes.c_double), ("x", ctypes.c_uint32 * 4),
                 ("pair", ctypes.c_int32), ("vec2", ctypes.c_int32),
-                ("ex", ctypes.c_int32), ("ey", ctypes.c_int32),
+                ("ex", ctypes.c_int32), ("ey", ctypes.c_int32), ("ez", ctypes.c_int32),
                 ("k", ctypes.c_uint32), ("l", ctypes.c_uint32),
-                ("dx2", ctypes.c_int32), ("dy2", ctypes.c_int32),
+                ("dx2", ctypes.c_int32), ("dy2", ctypes.c_int32), ("dz2", ctypes.c_int32),
                 ("y", ctypes.c_uint32 * 4)]
 
 

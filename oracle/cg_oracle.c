@@ -77,8 +77,9 @@
  *       extension, optional; square lattice).  A label is a pair proposal
  *       iff its fourth Philox word x3 < T_p = floor(p2 2^32).  A second
  *       Philox block of counter (k, r lo, r hi | 2^31, c) gives y0 -> ex,
- *       y2 -> ey, each floor(y (2R+1) / 2^32) - R (an offset e uniform on
- *       the square [-R, R]^2), and y1 -> a second tower vector d2.  The
+ *       y2 -> ey (and y3 -> ez on the cubic lattice), each
+ *       floor(y (2R+1) / 2^32) - R (an offset e uniform on the square
+ *       [-R, R]^2 or the cube [-R, R]^3), and y1 -> a second tower vector d2.  The
  *       second electron moves k = i + e -> l = k + d2.  The pair passes
  *       theta iff n_i = n_k = 1, n_j = n_l = 0, 0 < |e|^2 <= R^2 and
  *       0 < |e'|^2 <= R^2 with e' = e + d2 - d1 (the reverse move's offset),
@@ -545,11 +546,12 @@ double orc_Gamma(const orc_chain *c)
 }
 
 /* R15: pair proposals with probability p2 (0 <= p2 < 1) and offset radius R
- * (1 <= R, 2R < Lx, Ly; square lattice only). */
+ * (1 <= R, 2R below every side of the torus; square or cubic lattice). */
 int orc_set_pair(orc_chain *c, double p2, int R)
 {
     if (!(p2 >= 0.0 && p2 < 1.0)) return ORC_EINVAL;
-    if (p2 > 0.0 && (c->Lz != 1 || c->Ly == 1 || R < 1 || 2 * R >= c->Lx || 2 * R >= c->Ly))
+    if (p2 > 0.0 && (c->Ly == 1 || R < 1 || 2 * R >= c->Lx || 2 * R >= c->Ly ||
+                     (c->Lz > 1 && 2 * R >= c->Lz)))
         return ORC_EINVAL;
     c->pair_T = (uint32_t)floor(p2 * 4294967296.0);
     c->pair_R = p2 > 0.0 ? R : 0;
@@ -657,9 +659,9 @@ typedef struct {
     uint32_t x[4];        /* raw Philox words */
     int32_t pair;         /* 1: a pair proposal (x3 < T_p, R15) */
     int32_t vec2;         /* its second vector, -1 for a null proposal */
-    int32_t ex, ey;       /* its offset e */
+    int32_t ex, ey, ez;   /* its offset e (ez = 0 on the square lattice) */
     uint32_t k, l;        /* its second electron's origin and destination */
-    int32_t dx2, dy2;
+    int32_t dx2, dy2, dz2;
     uint32_t y[4];        /* raw words of its second Philox block */
 } orc_label;
 
@@ -720,27 +722,33 @@ void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *o
     out->l = 0xFFFFFFFFu;
     if (out->pair) {
         /* R15: a pair proposal */
-        int R = c->pair_R, W = 2 * c->pair_R + 1, xk, yk, xl, yl, fx, fy;
+        int R = c->pair_R, W = 2 * c->pair_R + 1, xk, yk, zk, xl, yl, zl, fx, fy, fz, e2, f2;
         ctr[2] = (uint32_t)(round >> 32) | 0x80000000u;
         orc_philox(ctr, key, out->y);
         out->ex = (int)(((uint64_t)out->y[0] * (uint64_t)W) >> 32) - R;
         out->ey = (int)(((uint64_t)out->y[2] * (uint64_t)W) >> 32) - R;
+        /* on the cubic lattice the offset's z comes from the fourth word */
+        out->ez = c->Lz > 1 ? (int)(((uint64_t)out->y[3] * (uint64_t)W) >> 32) - R : 0;
         out->vec2 = tower_sample(c, out->y[1]);
         if (out->vec2 < 0) { out->theta = 0; out->accepted = 0; return; }
         out->dx2 = c->vdx[out->vec2];
         out->dy2 = c->vdy[out->vec2];
+        out->dz2 = c->vdz[out->vec2];
         xk = (xi + out->ex + c->Lx) % c->Lx;
         yk = (yi + out->ey + c->Ly) % c->Ly;
+        zk = (zi + out->ez + c->Lz) % c->Lz;
         xl = (xk + out->dx2 + c->Lx) % c->Lx;
         yl = (yk + out->dy2 + c->Ly) % c->Ly;
-        out->k = (uint32_t)(yk * c->Lx + xk);
-        out->l = (uint32_t)(yl * c->Lx + xl);
+        zl = (zk + out->dz2 + c->Lz) % c->Lz;
+        out->k = (uint32_t)((zk * c->Ly + yk) * c->Lx + xk);
+        out->l = (uint32_t)((zl * c->Ly + yl) * c->Lx + xl);
         fx = out->ex + out->dx2 - out->dx;          /* e' = l - j */
         fy = out->ey + out->dy2 - out->dy;
+        fz = out->ez + out->dz2 - out->dz;
+        e2 = out->ex * out->ex + out->ey * out->ey + out->ez * out->ez;
+        f2 = fx * fx + fy * fy + fz * fz;
         out->theta = out->theta && c->n[out->k] == 1 && c->n[out->l] == 0 &&
-                     out->ex * out->ex + out->ey * out->ey > 0 &&
-                     out->ex * out->ex + out->ey * out->ey <= R * R &&
-                     fx * fx + fy * fy > 0 && fx * fx + fy * fy <= R * R;
+                     e2 > 0 && e2 <= R * R && f2 > 0 && f2 <= R * R;
         if (!out->theta) { out->accepted = 0; return; }
         out->dE = orc_delta_e_pair(c, (int)out->i, (int)out->j, (int)out->k, (int)out->l,
                                    out->dx, out->dx2);

@@ -282,4 +282,179 @@ def test_gamma_counts_the_pair_attempts():
     with pytest.raises(ValueError):
         c.set_pair(0.1, 8)          # 2R must stay below L
     with pytest.raises(ValueError):
-        oracle.Chain(8, dim=3, r_max=2, pair_frac=0.1, pair_rmax=2)
+        oracle.Chain(8, 1, r_max=2, pair_frac=0.1, pair_rmax=2)      # a ring has no pairs
+
+
+
+# ---------------------------------------------------------------------------
+# the cubic lattice: the offset's z is the fourth word of the pair block
+# ---------------------------------------------------------------------------
+
+def _pair_moves3(c, n, R):
+    """Every 3D pair proposal with its probability given a pair label (offset
+    uniform on the cube [-R, R]^3, kept with both offsets inside the ball):
+    yields (prob, i, j, k, l, dx1, dx2)."""
+    L, N = c.Lx, c.N
+    dxs, dys, Wi, _ = c.vectors()
+    dzs = c.vectors_z()
+    pd = Wi.astype(np.float64) / 2.0 ** 32
+    W = 2 * R + 1
+
+    def site(x, y, z):
+        return ((z % L) * L + (y % L)) * L + (x % L)
+    for i in np.nonzero(n)[0]:
+        xi, yi, zi = i % L, (i // L) % L, i // (L * L)
+        for v1 in range(len(dxs)):
+            j = site(xi + dxs[v1], yi + dys[v1], zi + dzs[v1])
+            if n[j]:
+                continue
+            for ex, ey, ez in itertools.product(range(-R, R + 1), repeat=3):
+                if not 0 < ex * ex + ey * ey + ez * ez <= R * R:
+                    continue
+                k = site(xi + ex, yi + ey, zi + ez)
+                if not n[k]:
+                    continue
+                xk, yk, zk = k % L, (k // L) % L, k // (L * L)
+                for v2 in range(len(dxs)):
+                    l = site(xk + dxs[v2], yk + dys[v2], zk + dzs[v2])
+                    if n[l]:
+                        continue
+                    f = (ex + dxs[v2] - dxs[v1], ey + dys[v2] - dys[v1], ez + dzs[v2] - dzs[v1])
+                    f2 = f[0] ** 2 + f[1] ** 2 + f[2] ** 2
+                    if not 0 < f2 <= R * R:
+                        continue
+                    yield ((1.0 / N) * pd[v1] * pd[v2] / W ** 3,
+                           int(i), int(j), int(k), int(l), int(dxs[v1]), int(dxs[v2]))
+
+
+def _kernel_row3(c, n, R, p2q, index):
+    L, N = c.Lx, c.N
+    dxs, dys, Wi, _ = c.vectors()
+    dzs = c.vectors_z()
+    pd = Wi.astype(np.float64) / 2.0 ** 32
+    row = {}
+    c.set_state(n)
+    for i in np.nonzero(n)[0]:
+        xi, yi, zi = i % L, (i // L) % L, i // (L * L)
+        for v in range(len(dxs)):
+            j = (((zi + dzs[v]) % L) * L + (yi + dys[v]) % L) * L + (xi + dxs[v]) % L
+            if n[j]:
+                continue
+            acc = min(1.0, math.exp(-c.delta_e(i, j, int(dxs[v])) / c.T))
+            n2 = n.copy()
+            n2[i], n2[j] = 0, 1
+            b = index[n2.tobytes()] if index is not None else n2.tobytes()
+            row[b] = row.get(b, 0.0) + (1.0 - p2q) * (1.0 / N) * pd[v] * acc
+    for prob, i, j, k, l, dx1, dx2 in _pair_moves3(c, n, R):
+        acc = min(1.0, math.exp(-c.delta_e_pair(i, j, k, l, dx1, dx2) / c.T))
+        n2 = n.copy()
+        n2[i], n2[j], n2[k], n2[l] = 0, 1, 0, 1
+        b = index[n2.tobytes()] if index is not None else n2.tobytes()
+        row[b] = row.get(b, 0.0) + p2q * prob * acc
+    return row
+
+
+@pytest.mark.parametrize("E", [0.0, 0.05])
+def test_pair_delta_e_on_the_cube(E):
+    L = 6
+    N = L ** 3
+    c = oracle.Chain(L, dim=3, r_max=2, T=0.1, E=E, seed=2, pair_frac=0.3, pair_rmax=2)
+    G = ref.coupling_matrix3(L, L, L)
+    rng = np.random.default_rng(9)
+    n = workloads.random_occupation(N, N // 2, seed=41)
+    phi = workloads.random_phi(N, 1.0, seed=51)
+    c.set_state(n, phi)
+    H0 = ref.interaction_energy(n, phi, 0.5, G)
+    moves = list(_pair_moves3(c, n, 2))
+    for m in rng.choice(len(moves), 120, replace=False):
+        _, i, j, k, l, dx1, dx2 = moves[m]
+        n2 = n.copy()
+        n2[i], n2[j], n2[k], n2[l] = 0, 1, 0, 1
+        want = (ref.interaction_energy(n2, phi, 0.5, G) - H0) - E * (dx1 + dx2)
+        assert abs(c.delta_e_pair(i, j, k, l, dx1, dx2) - want) <= 1e-12 * (1 + abs(H0) / N)
+
+
+def test_pair_detailed_balance_on_the_cube():
+    L, ne = 4, 2
+    N = L ** 3
+    c = oracle.Chain(L, dim=3, nu=ne / N, r_max=1, T=0.4, E=0.0, seed=6, pair_frac=0.4,
+                     pair_rmax=1)
+    _, _, phi = c.state()
+    states = _states(N, ne)
+    index = {s.tobytes(): a for a, s in enumerate(states)}
+    G = ref.coupling_matrix3(L, L, L)
+    H = ref.interaction_energy_batch(states, phi, ne / N, G)
+    pi = np.exp(-(H - H.min()) / c.T)
+    pi /= pi.sum()
+    p2q = c.pair_threshold * 2.0 ** -32
+    K = np.zeros((len(states), len(states)))
+    for a, n in enumerate(states):
+        for b, v in _kernel_row3(c, n, 1, p2q, index).items():
+            K[a, b] += v
+    K[np.diag_indices_from(K)] += 1.0 - K.sum(axis=1)
+    F = pi[:, None] * K
+    assert np.abs(F - F.T).max() <= 1e-14 * np.abs(F).max()
+    four = sum(1 for a, n in enumerate(states) for b in np.nonzero(K[a])[0]
+               if np.abs(states[b].astype(int) - n).sum() == 4)
+    assert four > 100          # pair moves are part of the kernel
+
+
+def test_oracle_labels_follow_the_kernel_row_on_the_cube():
+    # 16 electrons filling the 2 x 2 x 4 block x, y < 2 of a 4^3 torus: many
+    # neighbouring pairs, including pairs along z (their offsets need ez)
+    L = 4
+    N = L ** 3
+    c = oracle.Chain(L, dim=3, nu=16 / N, r_max=1, T=1.0, E=0.0, seed=4, pair_frac=0.9,
+                     pair_rmax=1)
+    n = np.zeros(N, np.uint8)
+    for z in range(L):
+        for y in range(2):
+            for x in range(2):
+                n[(z * L + y) * L + x] = 1
+    c.set_state(n)
+    row = _kernel_row3(c, n, 1, c.pair_threshold * 2.0 ** -32, None)
+    n_labels = 400_000
+    counts = {}
+    for t in range(n_labels):
+        lab = c.eval_label(t // 64, t % 64)
+        if lab.accepted:
+            n2 = n.copy()
+            n2[lab.i], n2[lab.j] = 0, 1
+            if lab.pair:
+                n2[lab.k], n2[lab.l] = 0, 1
+            b = n2.tobytes()
+            counts[b] = counts.get(b, 0) + 1
+    assert set(counts) <= set(row)
+    is_pair = {b: int(np.abs(np.frombuffer(b, np.uint8).astype(int) - n).sum() == 4)
+               for b in row}
+    # all pair moves together: a binomial count
+    p_pair = sum(pb for b, pb in row.items() if is_pair[b])
+    got = sum(v for b, v in counts.items() if is_pair[b])
+    assert abs(got - p_pair * n_labels) < 5 * math.sqrt(n_labels * p_pair), (got, p_pair)
+    assert got > 200
+    # every target with at least 5 expected hits
+    chi2, dof, pair_bins = 0.0, 0, 0
+    for b, pb in row.items():
+        e = pb * n_labels
+        if e >= 5:
+            chi2 += (counts.get(b, 0) - e) ** 2 / e
+            dof += 1
+            pair_bins += is_pair[b]
+    assert dof >= 10 and pair_bins >= 20, (dof, pair_bins)
+    assert chi2 < dof + 5 * math.sqrt(2 * dof), (chi2, dof)
+
+
+def test_pair_run_on_the_cube_keeps_eps_energy_and_dipole():
+    L = 8
+    c = oracle.Chain(L, dim=3, r_max=2, T=0.5, E=0.02, seed=3, pair_frac=0.6, pair_rmax=2)
+    P0 = c.counters()["P"]
+    rc, log = c.run(3000, 128, log=True)
+    assert rc == oracle.ORC_OK
+    assert (log["k"] != 0xFFFFFFFF).sum() > 10
+    n, eps, phi = c.state()
+    assert np.abs(eps - c.eps_scratch()).max() <= 1e-11
+    cnt = c.counters()
+    assert cnt["P"] - P0 == int(log["dx"].sum() + log["dx2"].sum())
+    G = ref.coupling_matrix3(L, L, L)
+    H = ref.interaction_energy(n, phi, 0.5, G)
+    assert abs(cnt["energy"] - (H - c.E * cnt["P"])) <= 1e-9 * max(1.0, abs(H))
