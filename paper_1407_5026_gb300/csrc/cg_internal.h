@@ -141,6 +141,12 @@ cudaError_t launch_pr_persistent3(int precision, const DevReplica *d_reps, const
                                   int n_ctas, int threads, int smem_bytes, const RunArgs &args,
                                   cudaStream_t st, int L);
 cudaError_t set_pr3_smem_limit(int precision, int bytes);
+// The cubic lattice with two-electron hops (cg_pr_kernel3d_pair.cu).
+cudaError_t launch_pr_persistent3_pair(int precision, const DevReplica *d_reps,
+                                       const int *d_index, int n_ctas, int threads,
+                                       int smem_bytes, const RunArgs &args, cudaStream_t st,
+                                       int L);
+cudaError_t set_pr3_pair_smem_limit(int precision, int bytes);
 // The two-electron-hop instances (cg_pr_kernel_pair.cu): square lattice, one
 // CTA per replica.
 cudaError_t launch_pr_persistent_pair(int precision, const DevReplica *d_reps,
@@ -160,10 +166,10 @@ cudaError_t set_pr_pair_time_smem_limit(int precision, int bytes);
 cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int *d_index,
                               int n_reps, int cluster, int threads, int smem_bytes,
                               const RunArgs &args, cudaStream_t st, int L, int dim);
-// Its two-electron-hop instances (cg_pr_cluster_pair.cu; square lattice).
+// Its two-electron-hop instances (cg_pr_cluster_pair.cu).
 cudaError_t launch_pr_cluster_pair(int precision, const DevReplica *d_reps, const int *d_index,
                                    int n_reps, int cluster, int threads, int smem_bytes,
-                                   const RunArgs &args, cudaStream_t st, int L);
+                                   const RunArgs &args, cudaStream_t st, int L, int dim);
 cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int tab_entries, int words,
                             int precision, cudaStream_t st);
 cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int tab_entries, int words,

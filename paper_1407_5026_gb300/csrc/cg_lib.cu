@@ -629,9 +629,8 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     }
     if (o.pair_frac > 0.0) {
         for (int k = 0; k < R; ++k)
-            if (dim_of(reps[k]) != 2 || o.pair_rmax < 1 || 2 * o.pair_rmax >= reps[k].L) {
-                fail(CG_EINVAL, "two-electron hops need square lattices and "
-                                "1 <= pair_rmax < L/2");
+            if (o.pair_rmax < 1 || 2 * o.pair_rmax >= reps[k].L) {
+                fail(CG_EINVAL, "two-electron hops need 1 <= pair_rmax < L/2");
                 return nullptr;
             }
     }

@@ -64,9 +64,8 @@ cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int
     if (cluster < 2 || cluster > 8 || (L % cluster) != 0 || threads < L)
         return cudaErrorInvalidValue;
     if (args.pair)
-        return dim == 2 ? launch_pr_cluster_pair(precision, d_reps, d_index, n_reps, cluster,
-                                                 threads, smem_bytes, args, st, L)
-                        : cudaErrorInvalidValue;
+        return launch_pr_cluster_pair(precision, d_reps, d_index, n_reps, cluster, threads,
+                                      smem_bytes, args, st, L, dim);
     const bool pow2 = (L & (L - 1)) == 0;
     return precision == CG_FP64
                ? launch_cluster_p<double>(d_reps, d_index, n_reps, cluster, threads, smem_bytes,

@@ -208,9 +208,9 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                                                thr_last, mine && k1 < M);
                 PairProp q0{}, q1{};
                 if (kPair && !a.toy) {
-                    q0 = pair_extend<kPow2>(S, p0, k0, PP2, key0, key1, L, log2L, magic, thr_last,
+                    q0 = pair_extend<kPow2, kDim>(S, p0, k0, PP2, key0, key1, L, log2L, magic, thr_last,
                                             Rg.pair_T, Rg.pair_R);
-                    q1 = pair_extend<kPow2>(S, p1, k1, PP2, key0, key1, L, log2L, magic, thr_last,
+                    q1 = pair_extend<kPow2, kDim>(S, p1, k1, PP2, key0, key1, L, log2L, magic, thr_last,
                                             Rg.pair_T, Rg.pair_R);
                 }
                 double dE0 = 0.0, dE1 = 0.0;
@@ -229,7 +229,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                         if (kPair && q0.pair) {
                             ek0 = cluster_eps<Real, kDim>(cl, eps, q0.k, rows_local, log2L, L, magic, kPow2, rank);
                             el0 = cluster_eps<Real, kDim>(cl, eps, q0.l, rows_local, log2L, L, magic, kPow2, rank);
-                            acc0 = accept_pair_vals<Real, kPow2>(ei0, ej0, ek0, el0, S, Rg, p0, q0, T,
+                            acc0 = accept_pair_vals<Real, kPow2, kDim>(ei0, ej0, ek0, el0, S, Rg, p0, q0, T,
                                                                  invTf, dE0, L, log2L, magic, H1);
                         } else {
                             acc0 = accept_vals<Real>(ei0, ej0, S, p0, T, invTf, dE0);
@@ -241,7 +241,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                         if (kPair && q1.pair) {
                             ek1 = cluster_eps<Real, kDim>(cl, eps, q1.k, rows_local, log2L, L, magic, kPow2, rank);
                             el1 = cluster_eps<Real, kDim>(cl, eps, q1.l, rows_local, log2L, L, magic, kPow2, rank);
-                            acc1 = accept_pair_vals<Real, kPow2>(ei1, ej1, ek1, el1, S, Rg, p1, q1, T,
+                            acc1 = accept_pair_vals<Real, kPow2, kDim>(ei1, ej1, ek1, el1, S, Rg, p1, q1, T,
                                                                  invTf, dE1, L, log2L, magic, H1);
                         } else {
                             acc1 = accept_vals<Real>(ei1, ej1, S, p1, T, invTf, dE1);
@@ -264,7 +264,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                             s_cand[warp].dE =
                                 a.toy ? 0.0
                                 : (kPair && q0.pair)
-                                    ? pair_hop_dE_vals<Real, kPow2>(ei0, ej0, ek0, el0, S, Rg, p0,
+                                    ? pair_hop_dE_vals<Real, kPow2, kDim>(ei0, ej0, ek0, el0, S, Rg, p0,
                                                                     q0, dE0, L, log2L, magic, H1)
                                     : hop_dE_vals<Real>(ei0, ej0, S, p0, dE0);
                             if (kPair) s_pcand[warp] = q0;
@@ -279,7 +279,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                             s_cand[warp].dE =
                                 a.toy ? 0.0
                                 : (kPair && q1.pair)
-                                    ? pair_hop_dE_vals<Real, kPow2>(ei1, ej1, ek1, el1, S, Rg, p1,
+                                    ? pair_hop_dE_vals<Real, kPow2, kDim>(ei1, ej1, ek1, el1, S, Rg, p1,
                                                                     q1, dE1, L, log2L, magic, H1)
                                     : hop_dE_vals<Real>(ei1, ej1, S, p1, dE1);
                             if (kPair) s_pcand[warp] = q1;
@@ -351,8 +351,8 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         const int cdx = kDim == 3 ? (win.dxy << 22) >> 22 : (int)(short)(win.dxy & 0xffff);
         const int cdy = kDim == 3 ? (win.dxy << 12) >> 22 : win.dxy >> 16;
         const bool cpair = kPair && !a.toy && wpq.pair;
-        const int cdx2 = cpair ? (int)(short)(wpq.dxy2 & 0xffff) : 0;
-        const int cdy2 = cpair ? wpq.dxy2 >> 16 : 0;
+        const int cdx2 = !cpair ? 0 : kDim == 3 ? (wpq.dxy2 << 22) >> 22 : (int)(short)(wpq.dxy2 & 0xffff);
+        const int cdy2 = !cpair ? 0 : kDim == 3 ? (wpq.dxy2 << 12) >> 22 : wpq.dxy2 >> 16;
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
@@ -395,17 +395,22 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
         // ---- local-energy update of this CTA's rows (step 3b) ----
         if (kDim == 3 && !a.toy && tid < active) {
             // thread -> column x = ux of the (z, y) rows uy0, uy0 + rows_per_pass,
-            // ... of this CTA's planes (row r = zl L + y, site r L + x)
+            // ... of this CTA's planes (row r = zl L + y, site r L + x); an
+            // executed pair applies the second electron's update after the
+            // first one's
+#pragma unroll 1
+            for (int pass = 0; pass < (cpair ? 2 : 1); ++pass) {
+            const unsigned ui = pass ? wpq.k : ci, uj = pass ? wpq.l : cj;
             int xi, yi, zi, xj, yj, zj;
             if (kPow2) {
                 const int m = L - 1;
-                xi = (int)ci & m; yi = (int)(ci >> log2L) & m; zi = (int)(ci >> (2 * log2L));
-                xj = (int)cj & m; yj = (int)(cj >> log2L) & m; zj = (int)(cj >> (2 * log2L));
+                xi = (int)ui & m; yi = (int)(ui >> log2L) & m; zi = (int)(ui >> (2 * log2L));
+                xj = (int)uj & m; yj = (int)(uj >> log2L) & m; zj = (int)(uj >> (2 * log2L));
             } else {
-                const unsigned qi = __umulhi(ci, magic), qj = __umulhi(cj, magic);
-                xi = (int)(ci - qi * (unsigned)L); zi = (int)__umulhi(qi, magic);
+                const unsigned qi = __umulhi(ui, magic), qj = __umulhi(uj, magic);
+                xi = (int)(ui - qi * (unsigned)L); zi = (int)__umulhi(qi, magic);
                 yi = (int)qi - zi * L;
-                xj = (int)(cj - qj * (unsigned)L); zj = (int)__umulhi(qj, magic);
+                xj = (int)(uj - qj * (unsigned)L); zj = (int)__umulhi(qj, magic);
                 yj = (int)qj - zj * L;
             }
             const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
@@ -416,6 +421,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 const int oi = (fold_axis(z - zi, L) * H1 + fold_axis(y - yi, L)) * H1 + fxi;
                 Real *e = eps + r * L + ux;
                 *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[oj], tinv[oi]));
+            }
             }
         } else if (!a.toy && tid < active) {
             // an executed pair applies the second electron's update after the

@@ -262,6 +262,24 @@ __device__ __forceinline__ void site_xy(unsigned s, int L, int log2L, unsigned m
     x = (int)s - y * L;
 }
 
+// x, y, z of site s = (z L + y) L + x of the cubic lattice
+template <bool kPow2>
+__device__ __forceinline__ void site_xyz(unsigned s, int L, int log2L, unsigned magic, int &x,
+                                         int &y, int &z)
+{
+    if (kPow2) {
+        const int m = L - 1;
+        x = (int)s & m;
+        y = (int)(s >> log2L) & m;
+        z = (int)(s >> (2 * log2L));
+    } else {
+        const unsigned q = __umulhi(s, magic);      // s / L
+        x = (int)(s - q * (unsigned)L);
+        z = (int)__umulhi(q, magic);                 // s / L^2
+        y = (int)q - z * L;
+    }
+}
+
 __device__ __forceinline__ int wrap_axis(int c, int L)
 {
     c += (c < 0) ? L : 0;
@@ -269,7 +287,9 @@ __device__ __forceinline__ int wrap_axis(int c, int L)
     return c;
 }
 
-template <bool kPow2>
+// kDim = 3: vectors are 10-bit packed, the offset's z comes from y3 and
+// sites are (z L + y) L + x.
+template <bool kPow2, int kDim = 2>
 __device__ __forceinline__ PairProp pair_extend(const Shared &S, Prop &p, unsigned k,
                                                 const PhiloxPrefix &P2, uint32_t key0,
                                                 uint32_t key1, int L, int log2L, unsigned magic,
@@ -285,18 +305,36 @@ __device__ __forceinline__ PairProp pair_extend(const Shared &S, Prop &p, unsign
     philox_finish(k, P2, key0, key1, y);
     const unsigned W = (unsigned)(2 * R + 1);
     const int ex = (int)__umulhi(y[0], W) - R, ey = (int)__umulhi(y[2], W) - R;
+    const int ez = kDim == 3 ? (int)__umulhi(y[3], W) - R : 0;
     const bool live2 = y[1] <= thr_last;
     const int v2 = tower_lookup(S.guide, S.thr, min(y[1], thr_last));
     const int dxy2 = S.disp[v2];
-    const int dx2 = (int)(short)(dxy2 & 0xffff), dy2 = dxy2 >> 16;
-    const int dx1 = (int)(short)(p.dxy & 0xffff), dy1 = p.dxy >> 16;
-    int xi, yi;
-    site_xy<kPow2>(p.i, L, log2L, magic, xi, yi);
+    int dx2, dy2, dz2 = 0, dx1, dy1, dz1 = 0;
+    if (kDim == 3) {
+        dx2 = (dxy2 << 22) >> 22; dy2 = (dxy2 << 12) >> 22; dz2 = dxy2 >> 20;
+        dx1 = (p.dxy << 22) >> 22; dy1 = (p.dxy << 12) >> 22; dz1 = p.dxy >> 20;
+    } else {
+        dx2 = (int)(short)(dxy2 & 0xffff); dy2 = dxy2 >> 16;
+        dx1 = (int)(short)(p.dxy & 0xffff); dy1 = p.dxy >> 16;
+    }
+    int xi, yi, zi = 0;
+    if (kDim == 3)
+        site_xyz<kPow2>(p.i, L, log2L, magic, xi, yi, zi);
+    else
+        site_xy<kPow2>(p.i, L, log2L, magic, xi, yi);
     const int xk = wrap_axis(xi + ex, L), yk = wrap_axis(yi + ey, L);
     const int xl = wrap_axis(xk + dx2, L), yl = wrap_axis(yk + dy2, L);
-    const unsigned ks = (unsigned)(yk * L + xk), ls = (unsigned)(yl * L + xl);
-    const int fx = ex + dx2 - dx1, fy = ey + dy2 - dy1;
-    const int e2 = ex * ex + ey * ey, f2 = fx * fx + fy * fy, R2 = R * R;
+    unsigned ks, ls;
+    if (kDim == 3) {
+        const int zk = wrap_axis(zi + ez, L), zl = wrap_axis(zk + dz2, L);
+        ks = (unsigned)((zk * L + yk) * L + xk);
+        ls = (unsigned)((zl * L + yl) * L + xl);
+    } else {
+        ks = (unsigned)(yk * L + xk);
+        ls = (unsigned)(yl * L + xl);
+    }
+    const int fx = ex + dx2 - dx1, fy = ey + dy2 - dy1, fz = ez + dz2 - dz1;
+    const int e2 = ex * ex + ey * ey + ez * ez, f2 = fx * fx + fy * fy + fz * fz, R2 = R * R;
     const unsigned wk = S.occ[ks >> 5], wl = S.occ[ls >> 5];
     const bool ok = live2 && e2 > 0 && e2 <= R2 && f2 > 0 && f2 <= R2 &&
                     ((wk >> (ks & 31)) & 1u) && !((wl >> (ls & 31)) & 1u);
@@ -308,11 +346,19 @@ __device__ __forceinline__ PairProp pair_extend(const Shared &S, Prop &p, unsign
     return q;
 }
 
-// 1/r between sites a and b from a folded table [fy * H1 + fx].
-template <typename T, bool kPow2>
+// 1/r between sites a and b from a folded table [fy * H1 + fx], or
+// [(fz * H1 + fy) * H1 + fx] on the cubic lattice.
+template <typename T, bool kPow2, int kDim = 2>
 __device__ __forceinline__ T tinv_sites(const T *tab, unsigned a, unsigned b, int L, int log2L,
                                         unsigned magic, int H1)
 {
+    if (kDim == 3) {
+        int xa, ya, za, xb, yb, zb;
+        site_xyz<kPow2>(a, L, log2L, magic, xa, ya, za);
+        site_xyz<kPow2>(b, L, log2L, magic, xb, yb, zb);
+        return tab[(fold_axis(za - zb, L) * H1 + fold_axis(ya - yb, L)) * H1 +
+                   fold_axis(xa - xb, L)];
+    }
     int xa, ya, xb, yb;
     site_xy<kPow2>(a, L, log2L, magic, xa, ya);
     site_xy<kPow2>(b, L, log2L, magic, xb, yb);
@@ -321,7 +367,7 @@ __device__ __forceinline__ T tinv_sites(const T *tab, unsigned a, unsigned b, in
 
 // dH of the pair i -> j, k -> l in binary64, in the serial chain's order:
 // (dH1 + dH2) + ((1/r_lj - 1/r_li) - (1/r_kj - 1/r_ki)), each dH as R9.
-template <bool kPow2>
+template <bool kPow2, int kDim = 2>
 __device__ __forceinline__ double pair_dE64(const Shared &S, const double *tab64, double ei,
                                             double ej, double ek, double el, const Prop &p,
                                             const PairProp &q, int L, int log2L,
@@ -329,10 +375,10 @@ __device__ __forceinline__ double pair_dE64(const Shared &S, const double *tab64
 {
     const double d1 = d_sub(d_sub(d_sub(ej, ei), S.vr64[p.v]), S.edx64[p.v]);
     const double d2 = d_sub(d_sub(d_sub(el, ek), S.vr64[q.v2]), S.edx64[q.v2]);
-    const double tlj = tinv_sites<double, kPow2>(tab64, q.l, p.j, L, log2L, magic, H1);
-    const double tli = tinv_sites<double, kPow2>(tab64, q.l, p.i, L, log2L, magic, H1);
-    const double tkj = tinv_sites<double, kPow2>(tab64, q.k, p.j, L, log2L, magic, H1);
-    const double tki = tinv_sites<double, kPow2>(tab64, q.k, p.i, L, log2L, magic, H1);
+    const double tlj = tinv_sites<double, kPow2, kDim>(tab64, q.l, p.j, L, log2L, magic, H1);
+    const double tli = tinv_sites<double, kPow2, kDim>(tab64, q.l, p.i, L, log2L, magic, H1);
+    const double tkj = tinv_sites<double, kPow2, kDim>(tab64, q.k, p.j, L, log2L, magic, H1);
+    const double tki = tinv_sites<double, kPow2, kDim>(tab64, q.k, p.i, L, log2L, magic, H1);
     return d_add(d_add(d1, d2), d_sub(d_sub(tlj, tli), d_sub(tkj, tki)));
 }
 
@@ -358,7 +404,7 @@ __device__ __forceinline__ bool metropolis64(double dE, uint32_t x2, double T, f
 // same sum in binary32 from the binary32 table, re-decided in binary64 from
 // the widened energies and the binary64 table when |dH| < 1e-5 (dE_out is
 // then the binary64 value, else 0: the executed pair is widened once).
-template <typename Real, bool kPow2>
+template <typename Real, bool kPow2, int kDim = 2>
 __device__ __forceinline__ bool accept_pair_vals(Real ei, Real ej, Real ek, Real el,
                                                  const Shared &S, const DevReplica &Rg,
                                                  const Prop &p, const PairProp &q, double T,
@@ -366,9 +412,9 @@ __device__ __forceinline__ bool accept_pair_vals(Real ei, Real ej, Real ek, Real
                                                  unsigned magic, int H1)
 {
     if (sizeof(Real) == 8) {
-        const double dE = pair_dE64<kPow2>(S, reinterpret_cast<const double *>(S.tinv),
-                                           (double)ei, (double)ej, (double)ek, (double)el, p, q,
-                                           L, log2L, magic, H1);
+        const double dE = pair_dE64<kPow2, kDim>(S, reinterpret_cast<const double *>(S.tinv),
+                                                 (double)ei, (double)ej, (double)ek, (double)el,
+                                                 p, q, L, log2L, magic, H1);
         dE_out = dE;
         return metropolis64(dE, p.x2, T, invTf);
     }
@@ -376,14 +422,14 @@ __device__ __forceinline__ bool accept_pair_vals(Real ei, Real ej, Real ek, Real
     const float d1 = __fsub_rn(__fsub_rn((float)ej, (float)ei), S.cv32[p.v]);
     const float d2 = __fsub_rn(__fsub_rn((float)el, (float)ek), S.cv32[q.v2]);
     const float cr = __fsub_rn(
-        __fsub_rn(tinv_sites<float, kPow2>(t32, q.l, p.j, L, log2L, magic, H1),
-                  tinv_sites<float, kPow2>(t32, q.l, p.i, L, log2L, magic, H1)),
-        __fsub_rn(tinv_sites<float, kPow2>(t32, q.k, p.j, L, log2L, magic, H1),
-                  tinv_sites<float, kPow2>(t32, q.k, p.i, L, log2L, magic, H1)));
+        __fsub_rn(tinv_sites<float, kPow2, kDim>(t32, q.l, p.j, L, log2L, magic, H1),
+                  tinv_sites<float, kPow2, kDim>(t32, q.l, p.i, L, log2L, magic, H1)),
+        __fsub_rn(tinv_sites<float, kPow2, kDim>(t32, q.k, p.j, L, log2L, magic, H1),
+                  tinv_sites<float, kPow2, kDim>(t32, q.k, p.i, L, log2L, magic, H1)));
     const float dEf = __fadd_rn(__fadd_rn(d1, d2), cr);
     if (fabsf(dEf) < 1e-5f) {
-        const double dE = pair_dE64<kPow2>(S, Rg.tinv64, (double)ei, (double)ej, (double)ek,
-                                           (double)el, p, q, L, log2L, magic, H1);
+        const double dE = pair_dE64<kPow2, kDim>(S, Rg.tinv64, (double)ei, (double)ej,
+                                                 (double)ek, (double)el, p, q, L, log2L, magic, H1);
         dE_out = dE;
         return metropolis64(dE, p.x2, T, invTf);
     }
@@ -392,37 +438,37 @@ __device__ __forceinline__ bool accept_pair_vals(Real ei, Real ej, Real ek, Real
     return (float)(p.x2 >> 9) < __fmaf_rn(__expf(-dEf * invTf), 0x1p23f, -0.5f);
 }
 
-template <typename Real, bool kPow2>
+template <typename Real, bool kPow2, int kDim = 2>
 __device__ __forceinline__ bool accept_pair(const Shared &S, const DevReplica &Rg, const Prop &p,
                                             const PairProp &q, double T, float invTf,
                                             double &dE_out, int L, int log2L, unsigned magic,
                                             int H1)
 {
     const Real *eps = reinterpret_cast<const Real *>(S.eps);
-    return accept_pair_vals<Real, kPow2>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q, T,
+    return accept_pair_vals<Real, kPow2, kDim>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q, T,
                                          invTf, dE_out, L, log2L, magic, H1);
 }
 
 // dH of an executed pair in binary64 (binary32 form: from the widened
 // energies and the binary64 table, once per hop).
-template <typename Real, bool kPow2>
+template <typename Real, bool kPow2, int kDim = 2>
 __device__ __forceinline__ double pair_hop_dE_vals(Real ei, Real ej, Real ek, Real el,
                                                    const Shared &S, const DevReplica &Rg,
                                                    const Prop &p, const PairProp &q, double dE,
                                                    int L, int log2L, unsigned magic, int H1)
 {
     if (sizeof(Real) == 8 || dE != 0.0) return dE;
-    return pair_dE64<kPow2>(S, Rg.tinv64, (double)ei, (double)ej, (double)ek, (double)el, p, q,
-                            L, log2L, magic, H1);
+    return pair_dE64<kPow2, kDim>(S, Rg.tinv64, (double)ei, (double)ej, (double)ek, (double)el, p,
+                                  q, L, log2L, magic, H1);
 }
 
-template <typename Real, bool kPow2>
+template <typename Real, bool kPow2, int kDim = 2>
 __device__ __forceinline__ double pair_hop_dE(const Shared &S, const DevReplica &Rg,
                                               const Prop &p, const PairProp &q, double dE,
                                               int L, int log2L, unsigned magic, int H1)
 {
     const Real *eps = reinterpret_cast<const Real *>(S.eps);
-    return pair_hop_dE_vals<Real, kPow2>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q,
+    return pair_hop_dE_vals<Real, kPow2, kDim>(eps[p.i], eps[p.j], eps[q.k], eps[q.l], S, Rg, p, q,
                                          dE, L, log2L, magic, H1);
 }
 

@@ -45,7 +45,8 @@ static cudaError_t set3_one(int bytes)
 
 cudaError_t set_pr3_smem_limit(int precision, int bytes)
 {
-    cudaError_t e;
+    cudaError_t e = set_pr3_pair_smem_limit(precision, bytes);
+    if (e) return e;
     if (precision == CG_FP64) {
         if ((e = set3_one<double, 1024>(bytes)) || (e = set3_one<double, 512>(bytes)) ||
             (e = set3_one<double, 384>(bytes)) || (e = set3_one<double, 256>(bytes)))
@@ -62,6 +63,9 @@ cudaError_t launch_pr_persistent3(int precision, const DevReplica *d_reps, const
                                   int n_ctas, int threads, int smem_bytes, const RunArgs &args,
                                   cudaStream_t st, int L)
 {
+    if (args.pair)
+        return launch_pr_persistent3_pair(precision, d_reps, d_index, n_ctas, threads, smem_bytes,
+                                          args, st, L);
     if (precision == CG_FP64) {
         switch (threads) {
         case 1024: return launch3_t<double, 1024>(d_reps, d_index, n_ctas, smem_bytes, args, st, L);

@@ -202,10 +202,10 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                         p1 = propose<kPow2, kDim>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
                                             thr_last, v1);
                     if (kPair && !a.toy) {
-                        q0 = pair_extend<kPow2>(S, p0, k0, PP2, key0, key1, L, log2L, magic,
+                        q0 = pair_extend<kPow2, kDim>(S, p0, k0, PP2, key0, key1, L, log2L, magic,
                                                 thr_last, Rg.pair_T, Rg.pair_R);
                         if (two)
-                            q1 = pair_extend<kPow2>(S, p1, k1, PP2, key0, key1, L, log2L, magic,
+                            q1 = pair_extend<kPow2, kDim>(S, p1, k1, PP2, key0, key1, L, log2L, magic,
                                                     thr_last, Rg.pair_T, Rg.pair_R);
                     }
                     if (a.toy) {
@@ -215,11 +215,11 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                         acc1 = v1 && u1 < a.toy_A0;
                     } else if (kPair) {
                         if (p0.theta)
-                            acc0 = q0.pair ? accept_pair<Real, kPow2>(S, Rg, p0, q0, T, invTf, dE0,
+                            acc0 = q0.pair ? accept_pair<Real, kPow2, kDim>(S, Rg, p0, q0, T, invTf, dE0,
                                                                      L, log2L, magic, H1)
                                            : accept<Real>(S, p0, T, invTf, dE0);
                         if (p1.theta)
-                            acc1 = q1.pair ? accept_pair<Real, kPow2>(S, Rg, p1, q1, T, invTf, dE1,
+                            acc1 = q1.pair ? accept_pair<Real, kPow2, kDim>(S, Rg, p1, q1, T, invTf, dE1,
                                                                      L, log2L, magic, H1)
                                            : accept<Real>(S, p1, T, invTf, dE1);
                     } else if (sizeof(Real) == 4 && two) {
@@ -245,7 +245,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                                 s_pcand[warp] = q0;
                                 s_cand[warp].dE =
                                     a.toy ? 0.0
-                                    : q0.pair ? pair_hop_dE<Real, kPow2>(S, Rg, p0, q0, dE0, L,
+                                    : q0.pair ? pair_hop_dE<Real, kPow2, kDim>(S, Rg, p0, q0, dE0, L,
                                                                          log2L, magic, H1)
                                               : hop_dE<Real>(S, p0, dE0);
                             } else {
@@ -263,7 +263,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                                 s_pcand[warp] = q1;
                                 s_cand[warp].dE =
                                     a.toy ? 0.0
-                                    : q1.pair ? pair_hop_dE<Real, kPow2>(S, Rg, p1, q1, dE1, L,
+                                    : q1.pair ? pair_hop_dE<Real, kPow2, kDim>(S, Rg, p1, q1, dE1, L,
                                                                          log2L, magic, H1)
                                               : hop_dE<Real>(S, p1, dE1);
                             } else {
@@ -315,8 +315,8 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
         PairProp cq{};
         if (kPair) cq = s_pcand[win];
         const bool cpair = kPair && !a.toy && cq.pair;
-        const int cdx2 = cpair ? (int)(short)(cq.dxy2 & 0xffff) : 0;
-        const int cdy2 = cpair ? cq.dxy2 >> 16 : 0;
+        const int cdx2 = !cpair ? 0 : kDim == 3 ? (cq.dxy2 << 22) >> 22 : (int)(short)(cq.dxy2 & 0xffff);
+        const int cdy2 = !cpair ? 0 : kDim == 3 ? (cq.dxy2 << 12) >> 22 : cq.dxy2 >> 16;
         long long t1 = 0;
         if (tid == 0) {
             const unsigned long long m_hop = (p - 1) * (unsigned long long)M + q;
@@ -363,18 +363,24 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             // (x + a L/2, y + b L/2, z + c L/2), a, b, c in {0, 1}
             const int Lh = L >> 1;
             const int rpp = kThreads / Lh;
+            // an executed pair applies the second electron's update after the
+            // first one's (each site rounds twice, in the serial order)
+            const int passes3 = (kPair && cpair) ? 2 : 1;
+#pragma unroll 1
+            for (int pass = 0; pass < passes3; ++pass)
             if (!a.toy && tid < rpp * Lh) {
+                const unsigned ui = pass ? cq.k : ci, uj = pass ? cq.l : cj;
                 const int bx = tid % Lh, p0 = tid / Lh;
                 int xi, yi, zi, xj, yj, zj;
                 if (kPow2) {
                     const int m = L - 1;
-                    xi = (int)ci & m; yi = (int)(ci >> log2L) & m; zi = (int)(ci >> (2 * log2L));
-                    xj = (int)cj & m; yj = (int)(cj >> log2L) & m; zj = (int)(cj >> (2 * log2L));
+                    xi = (int)ui & m; yi = (int)(ui >> log2L) & m; zi = (int)(ui >> (2 * log2L));
+                    xj = (int)uj & m; yj = (int)(uj >> log2L) & m; zj = (int)(uj >> (2 * log2L));
                 } else {
-                    const unsigned qi = __umulhi(ci, magic), qj = __umulhi(cj, magic);
-                    xi = (int)(ci - qi * (unsigned)L); zi = (int)__umulhi(qi, magic);
+                    const unsigned qi = __umulhi(ui, magic), qj = __umulhi(uj, magic);
+                    xi = (int)(ui - qi * (unsigned)L); zi = (int)__umulhi(qi, magic);
                     yi = (int)qi - zi * L;
-                    xj = (int)(cj - qj * (unsigned)L); zj = (int)__umulhi(qj, magic);
+                    xj = (int)(uj - qj * (unsigned)L); zj = (int)__umulhi(qj, magic);
                     yj = (int)qj - zj * L;
                 }
                 const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);

@@ -97,12 +97,12 @@ def test_create_batch_rejects_bad_options_on_host(libcg, bad, msg):
     assert msg in str(ei.value)
 
 
-def test_pair_hops_refuse_the_cubic_lattice_on_host(libcg):
+def test_pair_offsets_must_fit_every_lattice_on_host(libcg):
     from paper_1407_5026_gb300 import binding as B
     with pytest.raises(B.CgError) as ei:
-        B.cg_create_batch([B.desc(L=16), B.desc(L=8, r_max=2, dim=3)],
-                          B.opts(pair_frac=0.2, pair_rmax=2))
-    assert "square lattices" in str(ei.value)
+        B.cg_create_batch([B.desc(L=16), B.desc(L=6, r_max=2, dim=3)],
+                          B.opts(pair_frac=0.2, pair_rmax=3))
+    assert "pair_rmax" in str(ei.value)
 
 
 def test_workspace_plan_counts_every_buffer(libcg):

@@ -215,3 +215,63 @@ def test_binary32_pairs_beyond_one_cta(B):
             assert o["refreshes"] == 2 and o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()
+
+
+def _cubic_oracle(p, pf, R, mode=0):
+    ch = oracle.Chain(p["L"], dim=3, nu=p["nu"], W=p["W"], xi=p["xi"], r_max=p["r_max"],
+                      T=p["T"], E=p["E"], seed=p["seed"], replica=p.get("replica", 0),
+                      pair_frac=pf, pair_rmax=R)
+    ch.set_time_mode(mode)
+    return ch
+
+
+@pytest.mark.parametrize("L,R,pf,M,cluster", [(8, 2, 0.5, 256, 0), (6, 2, 0.6, 128, 0),
+                                              (10, 3, 0.5, 300, 0), (16, 2, 0.5, 512, 2),
+                                              (16, 2, 0.5, 512, 4)])
+def test_binary64_cubic_pair_trajectory_bit_exact(B, L, R, pf, M, cluster):
+    p = dict(L=L, nu=0.5, W=1.0, xi=1.0, r_max=2, T=0.5, E=0.02, seed=12, replica=1, dim=3)
+    s = B.System([p], precision=B.CG_FP64, pair_frac=pf, pair_rmax=R, cluster_size=cluster)
+    try:
+        if cluster:
+            assert B.cg_group_shape(s.h, 0)["cluster"] == cluster
+        rc, log = s.run_logged(1500, M)
+        assert rc == B.CG_OK
+        ch = _cubic_oracle(p, pf, R)
+        _, olog = ch.run(1500, M, log=True)
+        for f in FIELDS:
+            np.testing.assert_array_equal(log[0][f], olog[f], err_msg=f)
+        np.testing.assert_array_equal(_bits(log[0]["dE"]), _bits(olog["dE"]))
+        assert (log[0]["k"] != 0xFFFFFFFF).sum() >= 10
+        n, eps, _, cnt = s.state(0)
+        on, oeps, _ = ch.state()
+        np.testing.assert_array_equal(n, on)
+        np.testing.assert_array_equal(_bits(eps), _bits(oeps))
+        assert cnt["P"] == ch.counters()["P"]
+    finally:
+        s.close()
+
+
+def test_cubic_pair_stochastic_clock_and_binary32(B):
+    p = dict(L=8, nu=0.5, W=1.0, xi=1.0, r_max=2, T=0.5, E=0.02, seed=12, replica=1, dim=3)
+    s = B.System([p], precision=B.CG_FP64, pair_frac=0.5, pair_rmax=2,
+                 time_mode=B.CG_TIME_GAUSSIAN)
+    try:
+        s.run(1200, 256)
+        ch = _cubic_oracle(p, 0.5, 2, mode=1)
+        ch.run(1200, 256)
+        assert s.state(0)[3]["time"] == ch.counters()["time"]
+    finally:
+        s.close()
+    reps = [dict(p, seed=k, replica=k, L=16) for k in range(8)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=256, pair_frac=0.4, pair_rmax=2)
+    try:
+        rc, log = s.run_logged(1500, 512)
+        assert rc == B.CG_OK
+        assert (log["k"] != 0xFFFFFFFF).sum() >= 20
+        for k in (0, 7):
+            n, eps, phi, _ = s.state(k)
+            ch = _cubic_oracle(reps[k], 0.4, 2)
+            ch.set_state(n, phi)
+            assert np.abs(eps - ch.state()[1]).max() <= 1e-4
+    finally:
+        s.close()
