@@ -104,7 +104,8 @@ typedef struct {
                                    the replica fits its shared memory, else the
                                    smallest of 2, 4, 8 that fits); 2, 4 or 8
                                    force a thread-block cluster that splits
-                                   eps by rows                                 */
+                                   eps by rows (z-planes on the cubic
+                                   lattice)                                    */
     int32_t time_mode;          /* CG_TIME_DETERMINISTIC (0): t = attempts/Gamma;
                                    CG_TIME_GAUSSIAN: each executed hop adds a
                                    Gaussian dt of mean m/Gamma and standard
@@ -121,9 +122,9 @@ typedef struct {
                                    conclusions as an extension): a label is a
                                    pair proposal iff its fourth Philox word is
                                    below floor(p2 2^32).  0 = single hops only.
-                                   Square lattices on one CTA only (else
-                                   CG_EINVAL);
-                                   Gamma becomes N Z / (1 - floor(p2 2^32) 2^-32) */
+                                   Square and cubic lattices, one CTA or a
+                                   cluster, both clocks; Gamma becomes
+                                   N Z / (1 - floor(p2 2^32) 2^-32)            */
 } cg_opts;
 
 /* Counters of one replica (step 3 of the mixed PR algorithm). */
