@@ -115,6 +115,24 @@ def test_workspace_plan_counts_every_buffer(libcg):
     assert b64 % 256 == 0
 
 
+def test_workspace_plan_counts_the_cubic_tensor_core_scratch(libcg):
+    # 16 replicas of the 16^3 lattice in binary32: the tensor-core refresh adds
+    # the +-1 image (2 N R_pad bytes), the K-split partials (k R_pad N x 4
+    # bytes, k the smallest divisor of the N/64 K-blocks leaving at most 16 per
+    # partial on the cubic lattice) and its 256-byte error word
+    from paper_1407_5026_gb300 import binding as B
+    reps = [B.desc(L=16, r_max=3, seed=s, replica=s, dim=3) for s in range(16)]
+    tc = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32,
+                                           refresh_kind=B.CG_REFRESH_BF16X2))
+    plain = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32,
+                                              refresh_kind=B.CG_REFRESH_FP64))
+    N, R_pad, kblocks = 16 ** 3, 16, 16 ** 3 // 64
+    k = next(d for d in range(1, kblocks + 1) if kblocks % d == 0 and kblocks // d <= 16)
+    img = 2 * N * R_pad
+    scratch = ((img + 255) // 256) * 256 + k * R_pad * N * 4
+    assert tc - plain == ((scratch + 255) // 256) * 256 + 256
+
+
 def test_missing_library_fails_loudly(tmp_path):
     # a fresh process whose library path points nowhere: every entry point
     # goes through load(), which raises instead of falling back to anything
