@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # workload (304 replicas x 1024 hops), from the ncu capture summarised in
 # profiles/pr_persistent_fp32_L128_R304_relaxed.md; valid only while the
 # kernel sources hash to the captured version.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "a386e38758326dd3", "bytes_per_launch": 20.722e6,
+TRAFFIC_CAPTURE = {"sources_sha256_16": "1d8a753ca8aefab9", "bytes_per_launch": 20.718e6,
                    "replicas": 304, "hops_per_replica": 1024}
 
 

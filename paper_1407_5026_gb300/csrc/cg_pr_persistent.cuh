@@ -387,10 +387,24 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                 const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
                 const Real *ci0 = tinv + fxi, *ci1 = tinv + (Lh - fxi);
                 const int LL = L * L;
+#pragma unroll 2
                 for (int pz = p0; pz < Lh * Lh; pz += rpp) {
-                    const int by = pz % Lh, bz = pz / Lh;
-                    const int fyj = fold_axis(by - yj, L), fyi = fold_axis(by - yi, L);
-                    const int fzj = fold_axis(bz - zj, L), fzi = fold_axis(bz - zi, L);
+                    int by, bz, fyj, fyi, fzj, fzi;
+                    if (kPow2) {
+                        // power-of-two L: shifts, masks and a min for the folds
+                        by = pz & (Lh - 1);
+                        bz = pz >> (log2L - 1);
+                        const int m = L - 1;
+                        const int dyj = (by - yj) & m, dyi = (by - yi) & m;
+                        const int dzj = (bz - zj) & m, dzi = (bz - zi) & m;
+                        fyj = min(dyj, L - dyj); fyi = min(dyi, L - dyi);
+                        fzj = min(dzj, L - dzj); fzi = min(dzi, L - dzi);
+                    } else {
+                        by = pz % Lh;
+                        bz = pz / Lh;
+                        fyj = fold_axis(by - yj, L); fyi = fold_axis(by - yi, L);
+                        fzj = fold_axis(bz - zj, L); fzi = fold_axis(bz - zi, L);
+                    }
                     // rows (fz H1 + fy) H1 of the folded table for the four
                     // (z, y) images of the base site, relative to j and to i
                     int oj[2][2], oi[2][2];
