@@ -48,6 +48,12 @@ Parity status of each oracle function (what pins it, in ``tests/``):
                         balance of two electrons on a 4^3 torus, and the
                         labels of a 16-electron state against its kernel row
                         (tests/test_oracle_pair.py).
+* random sites          pinned: positions against the Philox definition;
+  (``random_sites``)     partner lists, 1/r and dx against a numpy brute force;
+                        symmetric integer weights; eps and dH against numpy
+                        Eq. 1; exact detailed balance over every half-filled
+                        state of 16 sites; labels against the kernel row;
+                        eps and energy after a run (tests/test_oracle_random.py).
 """
 from __future__ import annotations
 
@@ -150,6 +156,18 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                ctypes.c_uint32]
         L.orc_new3.restype = ctypes.c_void_p
+        L.orc_new_random.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32]
+        L.orc_new_random.restype = ctypes.c_void_p
+        L.orc_get_positions.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_get_positions.restype = None
+        L.orc_num_pairs.argtypes = [ctypes.c_void_p]
+        L.orc_num_pairs.restype = ctypes.c_int
+        L.orc_get_pairs.argtypes = [ctypes.c_void_p, i32p, u32p, u64p, dp, dp]
+        L.orc_get_pairs.restype = None
+        L.orc_Zmax.argtypes = [ctypes.c_void_p]
+        L.orc_Zmax.restype = ctypes.c_double
         L.orc_get_vectors_z.argtypes = [ctypes.c_void_p, i32p]
         L.orc_get_vectors_z.restype = None
         L.orc_tinv_of3.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -262,16 +280,23 @@ class Chain:
     """One replica of the serial mixed-rejection chain on an Lx x Ly torus."""
 
     def __init__(self, Lx, Ly=None, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05,
-                 E=0.0, seed=0, replica=0, Lz=1, dim=None, pair_frac=0.0, pair_rmax=0):
+                 E=0.0, seed=0, replica=0, Lz=1, dim=None, pair_frac=0.0, pair_rmax=0,
+                 random_sites=False):
         """Lx x Ly x Lz torus; dim=3 makes the cubic lattice Lx = Ly = Lz;
-        pair_frac > 0 adds two-electron hops (reading R15)."""
+        pair_frac > 0 adds two-electron hops (reading R15); random_sites puts
+        N = Lx^2 sites at random positions in the Lx x Lx box (reading R16)."""
         Ly = Lx if Ly is None else Ly
         if dim == 3:
             Ly = Lz = Lx
         self._lib = lib()
-        self._h = self._lib.orc_new3(int(Lx), int(Ly), int(Lz), float(nu), float(W),
-                                     float(xi), int(r_max), float(T), float(E),
-                                     int(seed), int(replica))
+        if random_sites:
+            self._h = self._lib.orc_new_random(int(Lx), float(nu), float(W), float(xi),
+                                               int(r_max), float(T), float(E), int(seed),
+                                               int(replica))
+        else:
+            self._h = self._lib.orc_new3(int(Lx), int(Ly), int(Lz), float(nu), float(W),
+                                         float(xi), int(r_max), float(T), float(E),
+                                         int(seed), int(replica))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
         if pair_frac:
@@ -331,6 +356,31 @@ class Chain:
 
     def tinv(self, dx, dy, dz=0):
         return self._lib.orc_tinv_of3(self._h, int(dx), int(dy), int(dz))
+
+    def positions(self):
+        """Random sites (R16): the x and y positions."""
+        x = np.zeros(self.N, np.float64)
+        y = np.zeros(self.N, np.float64)
+        self._lib.orc_get_positions(self._h, _ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double))
+        return x, y
+
+    def pairs(self):
+        """Random sites (R16): partner-list offsets (N + 1), partners, running
+        integer weights, 1/r and the minimum-image dx of every pair."""
+        M = self._lib.orc_num_pairs(self._h)
+        off = np.zeros(self.N + 1, np.int32)
+        j = np.zeros(max(M, 1), np.uint32)
+        C = np.zeros(max(M, 1), np.uint64)
+        g = np.zeros(max(M, 1), np.float64)
+        dx = np.zeros(max(M, 1), np.float64)
+        self._lib.orc_get_pairs(self._h, _ptr(off, ctypes.c_int32), _ptr(j, ctypes.c_uint32),
+                                _ptr(C, ctypes.c_uint64), _ptr(g, ctypes.c_double),
+                                _ptr(dx, ctypes.c_double))
+        return off, j[:M], C[:M], g[:M], dx[:M]
+
+    @property
+    def Zmax(self):
+        return self._lib.orc_Zmax(self._h)
 
     def vectors_z(self):
         dz = np.zeros(self.V, np.int32)

@@ -88,6 +88,18 @@
  *       dH1 = ((eps_j - eps_i) - 1/r_ij) - E dx1, dH2 likewise for k -> l:
  *       the exact change of Eq. 1.  The commit applies the two single-hop
  *       eps updates in turn; P gains dx1 + dx2; Gamma = N Z / (1 - T_p 2^-32).
+ *   R16 Random sites (the random-site Coulomb glass, optional): N = L^2 sites
+ *       at x = L (x0 + 1/2) 2^-32, y = L (x1 + 1/2) 2^-32 from the Philox
+ *       block of counter (s, 3, 0xFFFFFFFF, c) in the L x L periodic box;
+ *       1/r with the minimum-image displacement (dx = x_t - x_s, shifted by
+ *       -L or +L when beyond L/2).  The hop partners of i are the j != i with
+ *       r_ij <= r_max in ascending j, weights w = exp(-2 r / xi), Z_i their sum,
+ *       Zmax = max_i Z_i and integer weights floor(2^32 w / Zmax): a label
+ *       draws i = floor(x0 N / 2^32) and the smallest partner k with
+ *       x1 < C_k (C the running sums over i's list; none: a null proposal).
+ *       The proposal probability W_ij 2^-32 / N is symmetric exactly, and
+ *       Gamma = N Zmax.  dH = ((eps_j - eps_i) - 1/r_ij) - E dx_ij with the
+ *       real minimum-image dx_ij; the dipole is not accumulated.
  *
  * Geometry is a general Lx x Ly x Lz torus (Ly = Lz = 1 gives a ring, Lz = 1
  * the square lattice, Lx = Ly = Lz the cubic lattice of the 3D extension) so
@@ -324,6 +336,14 @@ typedef struct orc_chain {
     int time_mode;            /* 0: t = attempts / Gamma (R4); 1: Gaussian dt (R13) */
     uint32_t pair_T;          /* R15: pair proposal iff x3 < pair_T (0: single hops only) */
     int pair_R;               /* R15: pair offsets inside the disk |e| <= pair_R */
+    /* R16: random sites */
+    int random;               /* 1: sites at random positions (Lz = 1, Ly = Lx) */
+    double *px, *py;          /* positions */
+    int *roff;                /* N + 1 offsets of each site's partner list */
+    uint32_t *rj;             /* partners */
+    uint64_t *rC;             /* running integer weights within each list */
+    double *rg, *rdx;         /* 1/r and the minimum-image x displacement of each pair */
+    double Zmax;
 } orc_chain;
 
 static int fold(int d, int L)
@@ -345,12 +365,32 @@ double orc_tinv_of(const orc_chain *c, int dx, int dy)
     return orc_tinv_of3(c, dx, dy, 0);
 }
 
+/* R16: minimum-image displacement component from a to b in a box of side L */
+static double min_image(double d, double L)
+{
+    if (d > 0.5 * L) d = d - L;
+    else if (d < -0.5 * L) d = d + L;
+    return d;
+}
+
+static double tinv_random(const orc_chain *c, int a, int b)
+{
+    double dx, dy;
+    if (a == b) return 0.0;
+    dx = min_image(c->px[b] - c->px[a], (double)c->Lx);
+    dy = min_image(c->py[b] - c->py[a], (double)c->Lx);
+    return 1.0 / sqrt(dx * dx + dy * dy);
+}
+
 /* site s = (z Ly + y) Lx + x */
 static double tinv_sites(const orc_chain *c, int a, int b)
 {
+    if (c->random) return tinv_random(c, a, b);
+    {
     int xa = a % c->Lx, ya = (a / c->Lx) % c->Ly, za = a / (c->Lx * c->Ly);
     int xb = b % c->Lx, yb = (b / c->Lx) % c->Ly, zb = b / (c->Lx * c->Ly);
     return orc_tinv_of3(c, xa - xb, ya - yb, za - zb);
+    }
 }
 
 void orc_free(orc_chain *c)
@@ -358,6 +398,7 @@ void orc_free(orc_chain *c)
     if (!c) return;
     free(c->tinv); free(c->vdx); free(c->vdy); free(c->vdz); free(c->w); free(c->Wint);
     free(c->C); free(c->n); free(c->phi); free(c->eps);
+    free(c->px); free(c->py); free(c->roff); free(c->rj); free(c->rC); free(c->rg); free(c->rdx);
     free(c);
 }
 
@@ -386,7 +427,8 @@ double orc_energy_scratch(const orc_chain *c)
     int s, t;
     for (s = 0; s < c->N; ++s) {
         h1 = h1 + c->phi[s] * (double)c->n[s];
-        h3 = h3 + (double)c->n[s] * (double)(s % c->Lx);
+        /* the x position: the lattice column, or the random site's x (R16) */
+        h3 = h3 + (double)c->n[s] * (c->random ? c->px[s] : (double)(s % c->Lx));
     }
     for (s = 0; s < c->N; ++s) {
         double ss = (double)c->n[s] - c->nu;
@@ -530,6 +572,103 @@ orc_chain *orc_new(int Lx, int Ly, double nu, double W, double xi, int r_max,
     return orc_new3(Lx, Ly, 1, nu, W, xi, r_max, T, E, seed, replica);
 }
 
+/* R16: N = L^2 sites at random positions in the L x L periodic box.  The
+ * lattice parts (disorder, initial state) are those of the L x L square
+ * lattice; positions, partner lists and the tower follow the reading. */
+orc_chain *orc_new_random(int L, double nu, double W, double xi, int r_max, double T,
+                          double E, uint64_t seed, uint32_t replica)
+{
+    orc_chain *c = orc_new3(L, L, 1, nu, W, xi, r_max, T, E, seed, replica);
+    int s, t, m, cnt;
+    double *Z, *w;
+    if (!c) return NULL;
+    c->random = 1;
+    c->px = (double *)malloc(sizeof(double) * c->N);
+    c->py = (double *)malloc(sizeof(double) * c->N);
+    for (s = 0; s < c->N; ++s) {
+        uint32_t o[4];
+        philox_setup_word(c, (uint32_t)s, 3u, o);
+        c->px[s] = (double)L * (((double)o[0] + 0.5) * 0x1p-32);
+        c->py[s] = (double)L * (((double)o[1] + 0.5) * 0x1p-32);
+    }
+    /* partner lists: count, then fill (ascending partner) */
+    c->roff = (int *)calloc((size_t)c->N + 1, sizeof(int));
+    cnt = 0;
+    for (s = 0; s < c->N; ++s) {
+        c->roff[s] = cnt;
+        for (t = 0; t < c->N; ++t) {
+            double dx, dy, r;
+            if (t == s) continue;
+            dx = min_image(c->px[t] - c->px[s], (double)L);
+            dy = min_image(c->py[t] - c->py[s], (double)L);
+            r = sqrt(dx * dx + dy * dy);
+            if (r == 0.0) { orc_free(c); return NULL; }       /* coincident sites */
+            if (r <= (double)r_max) ++cnt;
+        }
+    }
+    c->roff[c->N] = cnt;
+    c->rj = (uint32_t *)malloc(sizeof(uint32_t) * (cnt ? cnt : 1));
+    c->rC = (uint64_t *)malloc(sizeof(uint64_t) * (cnt ? cnt : 1));
+    c->rg = (double *)malloc(sizeof(double) * (cnt ? cnt : 1));
+    c->rdx = (double *)malloc(sizeof(double) * (cnt ? cnt : 1));
+    Z = (double *)calloc((size_t)c->N, sizeof(double));
+    w = (double *)malloc(sizeof(double) * (cnt ? cnt : 1));
+    m = 0;
+    for (s = 0; s < c->N; ++s)
+        for (t = 0; t < c->N; ++t) {
+            double dx, dy, r;
+            if (t == s) continue;
+            dx = min_image(c->px[t] - c->px[s], (double)L);
+            dy = min_image(c->py[t] - c->py[s], (double)L);
+            r = sqrt(dx * dx + dy * dy);
+            if (r > (double)r_max) continue;
+            c->rj[m] = (uint32_t)t;
+            c->rg[m] = 1.0 / r;
+            c->rdx[m] = dx;
+            w[m] = orc_exp_core(-2.0 * r / xi);
+            Z[s] = Z[s] + w[m];
+            ++m;
+        }
+    c->Zmax = 0.0;
+    for (s = 0; s < c->N; ++s) if (Z[s] > c->Zmax) c->Zmax = Z[s];
+    for (s = 0; s < c->N; ++s) {
+        uint64_t run = 0;
+        for (m = c->roff[s]; m < c->roff[s + 1]; ++m) {
+            uint64_t Wm = (uint64_t)floor((w[m] / c->Zmax) * 4294967296.0);
+            if (Wm > 0xFFFFFFFFull) Wm = 0xFFFFFFFFull;
+            run += Wm;
+            c->rC[m] = run;
+        }
+    }
+    free(Z);
+    free(w);
+    /* eps, energy and the (untracked) dipole from scratch on the new geometry */
+    orc_eps_scratch(c, c->eps);
+    c->cnt.energy = orc_energy_scratch(c);
+    c->cnt.P = 0;
+    return c;
+}
+
+void orc_get_positions(const orc_chain *c, double *x, double *y)
+{
+    int s;
+    for (s = 0; s < c->N; ++s) { x[s] = c->px[s]; y[s] = c->py[s]; }
+}
+
+int orc_num_pairs(const orc_chain *c) { return c->random ? c->roff[c->N] : 0; }
+
+void orc_get_pairs(const orc_chain *c, int32_t *off, uint32_t *j, uint64_t *C, double *g,
+                   double *dx)
+{
+    int s, m;
+    for (s = 0; s <= c->N; ++s) off[s] = c->roff[s];
+    for (m = 0; m < c->roff[c->N]; ++m) {
+        j[m] = c->rj[m]; C[m] = c->rC[m]; g[m] = c->rg[m]; dx[m] = c->rdx[m];
+    }
+}
+
+double orc_Zmax(const orc_chain *c) { return c->Zmax; }
+
 /* ------------------------------------------------------------------------ */
 /* Accessors                                                                 */
 /* ------------------------------------------------------------------------ */
@@ -541,7 +680,7 @@ double orc_Gamma(const orc_chain *c)
 {
     /* R4; with pair proposals (R15) a fraction T_p 2^-32 of the attempts is
        spent on them, so the single-hop attempts keep their rate */
-    const double g = (double)c->N * c->Z;
+    const double g = (double)c->N * (c->random ? c->Zmax : c->Z);
     return c->pair_T ? g / (1.0 - (double)c->pair_T * 0x1p-32) : g;
 }
 
@@ -550,7 +689,7 @@ double orc_Gamma(const orc_chain *c)
 int orc_set_pair(orc_chain *c, double p2, int R)
 {
     if (!(p2 >= 0.0 && p2 < 1.0)) return ORC_EINVAL;
-    if (p2 > 0.0 && (c->Ly == 1 || R < 1 || 2 * R >= c->Lx || 2 * R >= c->Ly ||
+    if (p2 > 0.0 && (c->random || c->Ly == 1 || R < 1 || 2 * R >= c->Lx || 2 * R >= c->Ly ||
                      (c->Lz > 1 && 2 * R >= c->Lz)))
         return ORC_EINVAL;
     c->pair_T = (uint32_t)floor(p2 * 4294967296.0);
@@ -700,6 +839,22 @@ void orc_eval_label(const orc_chain *c, uint64_t round, uint32_t k, orc_label *o
     out->i = (uint32_t)(((uint64_t)out->x[0] * (uint64_t)c->N) >> 32);
     out->u = ((double)out->x[2] + 0.5) * 0x1p-32;
     out->pair = out->x[3] < c->pair_T;       /* R15 */
+    if (c->random && !c->toy) {
+        /* R16: the partner of i by the integer tower of i's list */
+        int m, lo = c->roff[out->i], hi = c->roff[out->i + 1];
+        out->vec = -1;
+        for (m = lo; m < hi; ++m)
+            if ((uint64_t)out->x[1] < c->rC[m]) { out->vec = m; break; }
+        if (out->vec < 0) { out->accepted = 0; return; }
+        out->j = c->rj[out->vec];
+        out->theta = (c->n[out->i] == 1) && (c->n[out->j] == 0);
+        if (!out->theta) { out->accepted = 0; return; }
+        out->dE = ((c->eps[out->j] - c->eps[out->i]) - c->rg[out->vec]) -
+                  c->E * c->rdx[out->vec];
+        if (out->dE <= 0.0) { out->accepted = 1; return; }
+        out->accepted = out->u < orc_cg_exp((-out->dE) / c->T);
+        return;
+    }
     v = tower_sample(c, out->x[1]);
     out->vec = v;
     if (c->toy) {                        /* test-only: constant acceptance */
@@ -771,7 +926,7 @@ static void commit_hop(orc_chain *c, const orc_label *lab)
     if (c->toy) return;                  /* toy mode moves no electron */
     c->n[i] = 0;
     c->n[j] = 1;
-    c->cnt.P += lab->dx;
+    if (!c->random) c->cnt.P += lab->dx;        /* R16: no dipole on random sites */
     c->cnt.energy = c->cnt.energy + lab->dE;
     for (l = 0; l < c->N; ++l) {
         double delta = tinv_sites(c, l, (int)j) - tinv_sites(c, l, (int)i);
