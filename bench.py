@@ -591,9 +591,11 @@ def other_configs(args, B, local, only=None):
     L=256 whose eps is split over a thread-block cluster (refresh every 4096
     hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
     tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
-    4-CTA clusters (eps split by z-planes), and 304 replicas of L=64 with and
-    without two-electron hops (a fifth of the labels proposing a pair).  Each is timed with CUDA events over hops that
-    follow a relaxation from the random start."""
+    4-CTA clusters (eps split by z-planes), 304 replicas of L=64 with and
+    without two-electron hops (a fifth of the labels proposing a pair), and
+    152 binary64 replicas of L=64 with sites at random positions against the
+    same replicas on the lattice.  Each is timed with CUDA events over hops
+    that follow a relaxation from the random start."""
     import torch
     from paper_1407_5026_gb300 import workloads as W
     out = {}
@@ -603,12 +605,15 @@ def other_configs(args, B, local, only=None):
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
             ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
-            ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False)):
+            ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False),
+            ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False),
+            ("lattice_L64_T0.05_R152_fp64", W.random_sites(lattice=True), 2048, 2048, 0, False)):
         if only is not None and name != only:
             continue
         reps = [r.as_dict() for r in wl.replicas]
         pair = {k: wl.extra[k] for k in ("pair_frac", "pair_rmax") if wl.extra.get("pair_frac")}
-        s = B.System(reps, precision=B.CG_FP32, refresh_every=wl.refresh_every,
+        prec = B.CG_FP64 if wl.precision == "fp64" else B.CG_FP32
+        s = B.System(reps, precision=prec, refresh_every=wl.refresh_every,
                      use_graph=graph, device=local, **pair)
         s.run(relax, wl.M)
         if tune:

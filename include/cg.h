@@ -75,7 +75,17 @@ typedef struct cg_handle cg_handle;
  *          one CTA per replica or, when eps does not fit one, a cluster
  *          of 2, 4 or 8 CTAs splitting it by z-planes; binary32 refreshed
  *          on the tensor cores when L^3 is a multiple of 128, else in
- *          binary64)                                                    */
+ *          binary64)
+ *   sites  CG_SITES_LATTICE (0), or CG_SITES_RANDOM: the random-site
+ *          Coulomb glass, N = L^2 sites at Philox positions in the L x L
+ *          periodic box (counter (s, 3, 0xFFFFFFFF, replica): x = L (x0 +
+ *          1/2) 2^-32, y = L (x1 + 1/2) 2^-32), minimum-image 1/r, hop
+ *          partners j != i with r_ij <= r_max drawn by an integer tower of
+ *          weights floor(2^32 exp(-2 r / xi) / Zmax) (Zmax the largest
+ *          per-site sum), Gamma = N Zmax, the real minimum-image dx in the
+ *          field term and no dipole counter (P stays 0).  Binary64, one CTA
+ *          per replica, single hops, deterministic time (else CG_EINVAL); the
+ *          N x N coupling matrix lives in device memory.                */
 typedef struct {
     int32_t L;
     int32_t r_max;
@@ -83,7 +93,12 @@ typedef struct {
     uint64_t seed;
     uint32_t replica;
     int32_t dim;
+    int32_t sites;
+    int32_t reserved_;   /* 0 */
 } cg_replica_desc;
+
+#define CG_SITES_LATTICE 0
+#define CG_SITES_RANDOM 1
 
 /* Options of a handle.  Zero-initialised means: FP64, no refresh, automatic
  * launch shape, 2^32 rounds per hop before CG_ESTUCK, a 10 s limit per hop,
@@ -361,7 +376,7 @@ int cg_write_group_state(cg_handle *h, int group, const uint32_t *occ_words_host
 
 /* Test-only constant-acceptance mode: every label accepts iff u < A0, the
  * configuration is never changed, the counters advance.  A0 < 0 turns the
- * mode off. */
+ * mode off.  CG_EINVAL on a handle with random-site replicas. */
 int cg_set_toy_acceptance(cg_handle *h, double A0);
 
 /* Exported device helpers for tests: evaluate Philox-4x32-10 and the
@@ -382,8 +397,9 @@ int cg_debug_gauss(const uint64_t *seed_host, const uint32_t *replica_host,
  * vector by tower sampling) on the GPU for n 32-bit words x1 (host arrays).
  * v_host[k] = the smallest vector index v with x1 < C_v, C the integer
  * cumulative weights in the table's order, or -1 for a null proposal
- * (x1 >= C_{V-1}).  Returns CG_EINVAL for bad arguments, CG_ECUDA on a CUDA
- * error; allocates and frees device memory internally. */
+ * (x1 >= C_{V-1}).  Returns CG_EINVAL for bad arguments or a random-site
+ * replica (it draws from its partner lists), CG_ECUDA on a CUDA error;
+ * allocates and frees device memory internally. */
 int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *v_host, int n);
 
 /* Density of states of the local energies: the histogram g(eps) whose

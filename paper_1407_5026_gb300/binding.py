@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcg.so")
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_ESTUCK, CG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 CG_FP64, CG_FP32 = 0, 1
 CG_TIME_DETERMINISTIC, CG_TIME_GAUSSIAN = 0, 1
+CG_SITES_LATTICE, CG_SITES_RANDOM = 0, 1
 CG_REFRESH_AUTO, CG_REFRESH_FP64, CG_REFRESH_BF16X2 = 0, 1, 2
 
 EXPORTED = [
@@ -48,7 +49,8 @@ class cg_replica_desc(ctypes.Structure):
                 ("nu", ctypes.c_double), ("W", ctypes.c_double),
                 ("xi", ctypes.c_double), ("T", ctypes.c_double),
                 ("E", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("replica", ctypes.c_uint32), ("dim", ctypes.c_int32)]
+                ("replica", ctypes.c_uint32), ("dim", ctypes.c_int32),
+                ("sites", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class cg_opts(ctypes.Structure):
@@ -186,9 +188,10 @@ def _ptr(a, ctype):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0, dim=0):
+def desc(L, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=0, replica=0, dim=0,
+         sites=0):
     return cg_replica_desc(L=L, r_max=r_max, nu=nu, W=W, xi=xi, T=T, E=E, seed=seed,
-                           replica=replica, dim=dim)
+                           replica=replica, dim=dim, sites=sites)
 
 
 def opts(precision=CG_FP64, refresh_every=0, refresh_kind=CG_REFRESH_AUTO, block_threads=0,

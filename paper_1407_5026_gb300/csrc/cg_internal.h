@@ -69,6 +69,13 @@ struct alignas(16) DevReplica {
     DevCounters *ctr;
     cg_hop *log;              // NULL, or n_hops entries for this replica
     cg_trace_point *trace;    // NULL, or ctr->trace_cap points
+    // random-site geometry (CG_SITES_RANDOM; null otherwise)
+    const double *G;          // N x N minimum-image 1/r, 0 on the diagonal
+    const int *roff;          // N + 1 offsets of the partner lists
+    const unsigned int *rj;   // partners, ascending within each list
+    const unsigned long long *rC; // running integer weights within each list
+    const double *rg;         // 1/r of each pair
+    const double *redx;       // E dx of each pair (minimum-image dx, binary64)
 };
 
 // Thread 0 at commit: record trace points whose attempt threshold the
@@ -129,6 +136,19 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int tab_entries, int V,
     s.off_cv32 = o;  o = cg_align16(o + V * 4);
     s.total = o;
     return s;
+}
+
+// Random sites (cg_pr_random.cu): the coupling matrix from the positions,
+// eps from its definition, and the persistent binary64 PR kernel.
+cudaError_t launch_g_build(const double *px, const double *py, int L, int N, double *G,
+                           cudaStream_t st);
+cudaError_t launch_eps_init_random(const DevReplica *d_rep, int N, cudaStream_t st);
+cudaError_t launch_pr_random(const DevReplica *d_reps, const int *d_index, int n_ctas,
+                             int threads, int smem_bytes, const RunArgs &args, cudaStream_t st);
+cudaError_t set_pr_random_smem_limit(int bytes);
+inline int random_smem_bytes(int N)
+{
+    return cg_align16(N * 8) + cg_align16(((N + 31) / 32) * 4);
 }
 
 // Launchers (defined in the .cu files).

@@ -228,11 +228,24 @@ struct Rep {
     unsigned *d_occ = nullptr;
     double *d_phi = nullptr;
     DevCounters *d_ctr = nullptr;
+    // random sites: positions, partner lists (ascending partner) with their
+    // running integer weights, 1/r and E dx, and the N x N coupling matrix
+    bool random = false;
+    std::vector<double> px, py, rg, redx;
+    std::vector<int> roff;
+    std::vector<unsigned> rj;
+    std::vector<unsigned long long> rC;
+    double Zmax = 0.0;
+    double *d_px = nullptr, *d_py = nullptr, *d_G = nullptr, *d_rg = nullptr, *d_redx = nullptr;
+    int *d_roff = nullptr;
+    unsigned *d_rj = nullptr;
+    unsigned long long *d_rC = nullptr;
 };
 
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
     int dim = 2;                     // 2: square lattice, 3: cubic lattice
+    bool random = false;             // random-site replicas (pr_random)
     int cluster = 1;                 // CTAs per replica
     unsigned M = 4096;               // labels per round when cg_run is given M = 0
     bool tuned = false;
@@ -346,6 +359,10 @@ int sites_of(const cg_replica_desc &d)
 int check_desc(const cg_replica_desc &d)
 {
     if (d.dim != 0 && d.dim != 2 && d.dim != 3) return fail(CG_EINVAL, "dim must be 0, 2 or 3");
+    if (d.sites != CG_SITES_LATTICE && d.sites != CG_SITES_RANDOM)
+        return fail(CG_EINVAL, "sites must be CG_SITES_LATTICE or CG_SITES_RANDOM");
+    if (d.sites == CG_SITES_RANDOM && d.dim == 3)
+        return fail(CG_EINVAL, "random sites live in the two-dimensional box");
     if (d.L < 4 || d.L > 1024 || (d.L & 1))
         return fail(CG_EINVAL, "L must be even and in [4, 1024]");
     if (d.dim == 3 && d.L > 64) return fail(CG_EINVAL, "a cubic lattice needs L <= 64");
@@ -372,13 +389,14 @@ unsigned pair_threshold(const cg_opts &o)
 // so that the single-hop attempts keep their rate.
 double gamma_of(const Rep &r, const cg_opts &o)
 {
-    const double g = (double)r.N * r.tab->Z;
+    const double g = (double)r.N * (r.random ? r.Zmax : r.tab->Z);
     const unsigned Tp = pair_threshold(o);
     return Tp ? g / (1.0 - (double)Tp * 0x1p-32) : g;
 }
 
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
+    if (r.random) return random_smem_bytes(r.N);
     const int rb = precision == CG_FP64 ? 8 : 4;
     return smem_layout(r.N / cluster, (int)r.tab->t64.size(), r.tab->V, r.words, rb).total;
 }
@@ -392,6 +410,7 @@ int choose_cluster(const cg_opts &o, const Rep &r, int optin)
     // room for the kernels' static shared memory (the pair-hop cluster
     // kernel's exchange slots take it past 2 KiB)
     const int budget = optin - (o.pair_frac > 0.0 ? 3072 : 2048);
+    if (r.random) return (o.cluster_size <= 1 && persistent_smem(r, o.precision) <= budget) ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
         if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
@@ -438,6 +457,73 @@ void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
     dr.C0 = t.C0;
     dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
     dr.log = log;
+    dr.G = r.d_G; dr.roff = r.d_roff; dr.rj = r.d_rj; dr.rC = r.d_rC;
+    dr.rg = r.d_rg; dr.redx = r.d_redx;
+}
+
+// Random sites: positions from Philox counter (s, 3, 0xFFFFFFFF, replica),
+// x = L (x0 + 1/2) 2^-32 and y = L (x1 + 1/2) 2^-32; the partners of s are
+// the t != s with r_st <= r_max (minimum image), in ascending t; weight
+// w = exp(-2 r / xi), Zmax the largest per-site sum, integer weights
+// floor(2^32 w / Zmax) (at most 2^32 - 1) and their running sums per list.
+// Coincident sites are refused.
+int build_random(Rep &r)
+{
+    const int L = r.d.L, N = r.N, R = r.d.r_max;
+    const uint32_t k0 = (uint32_t)r.d.seed, k1 = (uint32_t)(r.d.seed >> 32);
+    const double Ld = (double)L;
+    r.px.resize(N);
+    r.py.resize(N);
+    for (int s = 0; s < N; ++s) {
+        uint32_t x[4];
+        philox4x32_10((uint32_t)s, 3u, 0xFFFFFFFFu, r.d.replica, k0, k1, x);
+        r.px[s] = Ld * (((double)x[0] + 0.5) * 0x1p-32);
+        r.py[s] = Ld * (((double)x[1] + 0.5) * 0x1p-32);
+    }
+    auto mi = [&](double d) {
+        if (d > 0.5 * Ld) return d - Ld;
+        if (d < -0.5 * Ld) return d + Ld;
+        return d;
+    };
+    r.roff.assign(N + 1, 0);
+    r.rj.clear(); r.rg.clear(); r.redx.clear(); r.rC.clear();
+    std::vector<double> w, Z(N, 0.0), dxs;
+    for (int s = 0; s < N; ++s) {
+        r.roff[s] = (int)r.rj.size();
+        for (int t = 0; t < N; ++t) {
+            if (t == s) continue;
+            const double dx = mi(r.px[t] - r.px[s]);
+            // |dx| well beyond r_max: never a partner (cheap pre-test)
+            if (dx > R + 1.0 || dx < -(R + 1.0)) continue;
+            const double dy = mi(r.py[t] - r.py[s]);
+            const double rr = std::sqrt(dx * dx + dy * dy);
+            if (rr == 0.0) return fail(CG_EINVAL, "random sites: two sites coincide");
+            if (rr > (double)R) continue;
+            r.rj.push_back((unsigned)t);
+            r.rg.push_back(1.0 / rr);
+            dxs.push_back(dx);
+            const double ws = host_exp(-2.0 * rr / r.d.xi);
+            w.push_back(ws);
+            Z[s] = Z[s] + ws;
+        }
+    }
+    r.roff[N] = (int)r.rj.size();
+    r.Zmax = 0.0;
+    for (int s = 0; s < N; ++s) if (Z[s] > r.Zmax) r.Zmax = Z[s];
+    if (!(r.Zmax > 0.0)) return fail(CG_EINVAL, "random sites: no site has a partner within r_max");
+    r.rC.resize(r.rj.size());
+    r.redx.resize(r.rj.size());
+    for (int s = 0; s < N; ++s) {
+        unsigned long long run = 0;
+        for (int m = r.roff[s]; m < r.roff[s + 1]; ++m) {
+            unsigned long long Wm = (unsigned long long)std::floor((w[m] / r.Zmax) * 4294967296.0);
+            if (Wm > 0xFFFFFFFFull) Wm = 0xFFFFFFFFull;
+            run += Wm;
+            r.rC[m] = run;
+            r.redx[m] = r.d.E * dxs[m];
+        }
+    }
+    return CG_OK;
 }
 
 void host_setup_state(const cg_replica_desc &d, std::vector<double> &phi,
@@ -479,15 +565,21 @@ int replica_index_ok(const cg_handle *h, int r)
 // Energy of Eq. 1 (field term with x in [0, L)) from eps:
 // H = sum n phi + 1/2 sum (n - nu)(eps - phi) - E sum n x.
 double energy_from_eps(const cg_replica_desc &d, const unsigned char *n, const double *eps,
-                       const double *phi, long long *P_out)
+                       const double *phi, long long *P_out, const double *px = nullptr)
 {
     const int N = sites_of(d);
-    double h1 = 0.0, h2 = 0.0;
+    double h1 = 0.0, h2 = 0.0, X = 0.0;
     long long P = 0;
     for (int s = 0; s < N; ++s) {
         h1 += n[s] ? phi[s] : 0.0;
         h2 += ((double)n[s] - d.nu) * (eps[s] - phi[s]);
         if (n[s]) P += s % d.L;
+        if (n[s] && px) X += px[s];
+    }
+    if (px) {
+        // random sites: the field term with the real x; no dipole counter
+        *P_out = 0;
+        return h1 + 0.5 * h2 - d.E * X;
     }
     *P_out = P;
     return h1 + 0.5 * h2 - d.E * (double)P;
@@ -528,6 +620,8 @@ int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
                                     h->st));
             CG_CUDA(cudaStreamSynchronize(h->st));
         }
+    } else if (r.random) {
+        CG_CUDA(launch_eps_init_random(h->d_reps + ri, r.N, h->st));
     } else {
         CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, (int)r.tab->t64.size(), r.words,
                                 h->opts.precision, h->st));
@@ -546,7 +640,8 @@ int load_state(cg_handle *h, int ri, const unsigned char *n, const double *eps,
                                 h->st));
         CG_CUDA(cudaStreamSynchronize(h->st));
         long long P = 0;
-        dc.energy = energy_from_eps(r.d, n, e.data(), ph.data(), &P);
+        dc.energy = energy_from_eps(r.d, n, e.data(), ph.data(), &P,
+                                    r.random ? r.px.data() : nullptr);
         dc.P = P;
     }
     CG_CUDA(cudaMemcpyAsync(r.d_ctr, &dc, sizeof(dc), cudaMemcpyHostToDevice, h->st));
@@ -581,6 +676,17 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
         const size_t N = (size_t)sites_of(d), words = (N + 31) / 32;
         total += up(N * (precision == CG_FP64 ? 8 : 4)) + up(words * 4) + up(N * 8) +
                  up(sizeof(DevCounters));
+        if (d.sites == CG_SITES_RANDOM) {
+            // positions, G, and the partner lists (their length needs the
+            // geometry itself)
+            Rep tmp;
+            tmp.d = d;
+            tmp.N = (int)N;
+            const size_t cnt = build_random(tmp) == CG_OK ? tmp.rj.size() : 0;
+            const size_t c1 = cnt ? cnt : 1;
+            total += 2 * up(N * 8) + up(N * N * 8) + up((N + 1) * 4) + up(c1 * 4) +
+                     3 * up(c1 * 8);
+        }
         auto key = std::make_tuple(d.L, d.r_max, d.xi, dim_of(d));
         if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
             seen.push_back(key);
@@ -627,6 +733,14 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         fail(CG_EINVAL, "pair_frac must be in [0, 1)");
         return nullptr;
     }
+    for (int k = 0; k < R; ++k)
+        if (reps[k].sites == CG_SITES_RANDOM &&
+            (o.precision != CG_FP64 || o.pair_frac > 0.0 || o.time_mode != CG_TIME_DETERMINISTIC ||
+             o.cluster_size > 1)) {
+            fail(CG_EINVAL, "random sites run in binary64, one CTA per replica, single hops and "
+                            "deterministic time");
+            return nullptr;
+        }
     if (o.pair_frac > 0.0) {
         for (int k = 0; k < R; ++k)
             if (o.pair_rmax < 1 || 2 * o.pair_rmax >= reps[k].L) {
@@ -674,6 +788,11 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         r.d = reps[k];
         r.N = sites_of(r.d);
         r.words = (r.N + 31) / 32;
+        r.random = r.d.sites == CG_SITES_RANDOM;
+        if (r.random && build_random(r) != CG_OK) {
+            destroy_partial();
+            return nullptr;
+        }
         for (auto &t : h->tables)
             if (t->L == r.d.L && t->r_max == r.d.r_max && t->xi == r.d.xi && t->dim == dim_of(r.d))
                 r.tab = t.get();
@@ -713,10 +832,44 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         cudaMemcpyAsync(t->d_tinvd, t->tinvd.data(), t->tinvd.size() * 8, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_guide, t->guide.data(), t->guide.size() * 2, cudaMemcpyHostToDevice, h->st);
     }
+    for (Rep &r : h->reps) {
+        if (!r.random) continue;
+        const size_t N = (size_t)r.N, cnt = std::max<size_t>(r.rj.size(), 1);
+        if (dalloc(h.get(), (void **)&r.d_px, N * 8) || dalloc(h.get(), (void **)&r.d_py, N * 8) ||
+            dalloc(h.get(), (void **)&r.d_G, N * N * 8) ||
+            dalloc(h.get(), (void **)&r.d_roff, (N + 1) * 4) ||
+            dalloc(h.get(), (void **)&r.d_rj, cnt * 4) ||
+            dalloc(h.get(), (void **)&r.d_rC, cnt * 8) ||
+            dalloc(h.get(), (void **)&r.d_rg, cnt * 8) ||
+            dalloc(h.get(), (void **)&r.d_redx, cnt * 8)) { destroy_partial(); return nullptr; }
+        const size_t m = r.rj.size();
+        cudaMemcpyAsync(r.d_px, r.px.data(), N * 8, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(r.d_py, r.py.data(), N * 8, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(r.d_roff, r.roff.data(), (N + 1) * 4, cudaMemcpyHostToDevice, h->st);
+        if (m) {
+            cudaMemcpyAsync(r.d_rj, r.rj.data(), m * 4, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_rC, r.rC.data(), m * 8, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_rg, r.rg.data(), m * 8, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_redx, r.redx.data(), m * 8, cudaMemcpyHostToDevice, h->st);
+        }
+        if (launch_g_build(r.d_px, r.d_py, r.d.L, r.N, r.d_G, h->st) != cudaSuccess) {
+            fail(CG_ECUDA, "coupling-matrix build failed to launch");
+            destroy_partial();
+            return nullptr;
+        }
+        // the host copies served the uploads (pageable: wait before they go)
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+            fail(CG_ECUDA, "random-site geometry upload failed");
+            destroy_partial();
+            return nullptr;
+        }
+    }
     const int rb = o.precision == CG_FP64 ? 8 : 4;
-    // groups of equal (dimension, L) (one launch each), replica order kept
-    // inside a group
-    auto gkey = [&](int k) { return dim_of(h->reps[k].d) * 4096 + h->reps[k].d.L; };
+    // groups of equal (sites kind, dimension, L) (one launch each), replica
+    // order kept inside a group
+    auto gkey = [&](int k) {
+        return (h->reps[k].random ? 1 << 20 : 0) + dim_of(h->reps[k].d) * 4096 + h->reps[k].d.L;
+    };
     std::vector<int> order(R);
     for (int k = 0; k < R; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gkey(a) < gkey(b); });
@@ -749,6 +902,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         Group g;
         g.L = h->reps[order[k]].d.L;
         g.dim = dim_of(h->reps[order[k]].d);
+        g.random = h->reps[order[k]].random;
         g.first = k;
         const int key = gkey(order[k]);
         int smem = 0, cluster = 1;
@@ -802,7 +956,8 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         destroy_partial();
         return nullptr;
     }
-    if (set_pr_smem_limit(o.precision, optin - 2048) != cudaSuccess) {
+    if (set_pr_smem_limit(o.precision, optin - 2048) != cudaSuccess ||
+        set_pr_random_smem_limit(optin - 2048) != cudaSuccess) {
         fail(CG_ECUDA, "cudaFuncSetAttribute(max dynamic shared memory) failed");
         destroy_partial();
         return nullptr;
@@ -839,6 +994,10 @@ int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
         for (int k = g.first; k < g.first + g.count; ++k) {
             const int ri = h->order[k];
             const Rep &r = h->reps[ri];
+            if (r.random) {
+                CG_CUDA(launch_eps_init_random(h->d_reps + ri, r.N, st));
+                continue;
+            }
             CG_CUDA(launch_eps_init(h->d_reps + ri, r.N, (int)r.tab->t64.size(), r.words, CG_FP64,
                                     st));
         }
@@ -889,7 +1048,10 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.toy_A0 = h->toy_A0;
     a.time_mode = h->opts.time_mode;
     a.pair = h->opts.pair_frac > 0.0 ? 1 : 0;
-    if (g.cluster > 1)
+    if (g.random)
+        CG_CUDA(launch_pr_random(h->d_reps, h->d_index + g.first, g.count, g.threads, g.smem, a,
+                                 st));
+    else if (g.cluster > 1)
         CG_CUDA(launch_pr_cluster(h->opts.precision, h->d_reps, h->d_index + g.first, g.count,
                                   g.cluster, g.threads, g.smem, a, st, g.L, g.dim));
     else
@@ -1548,6 +1710,8 @@ int cg_set_toy_acceptance(cg_handle *h, double A0)
     if (!h) return fail(CG_EINVAL, "null handle");
     if (A0 < 0) { h->toy = 0; h->toy_A0 = 0; return CG_OK; }
     if (!(A0 <= 1.0)) return fail(CG_EINVAL, "A0 must be in [0, 1]");
+    for (const Rep &r : h->reps)
+        if (r.random) return fail(CG_EINVAL, "random sites have no constant-acceptance mode");
     h->toy = 1;
     h->toy_A0 = A0;
     return CG_OK;
@@ -1625,6 +1789,8 @@ int cg_debug_tower(cg_handle *h, int replica, const uint32_t *x1_host, int32_t *
     if (!h || n <= 0 || !x1_host || !v_host) return fail(CG_EINVAL, "bad arguments");
     if (replica < 0 || replica >= (int)h->reps.size()) return fail(CG_EINVAL, "replica out of range");
     if (cudaSetDevice(h->device) != cudaSuccess) return fail(CG_ECUDA, "cudaSetDevice failed");
+    if (h->reps[replica].random)
+        return fail(CG_EINVAL, "a random-site replica draws from its partner lists");
     const Tables &t = *h->reps[replica].tab;
     char *d = nullptr;
     CG_CUDA(cudaMalloc((void **)&d, 8 * (size_t)n));

@@ -32,6 +32,7 @@ class Replica:
     seed: int
     replica: int = 0
     dim: int = 2      # 2: L x L square lattice; 3: L x L x L cubic lattice
+    sites: int = 0    # 0: lattice sites; 1: random positions in the L x L box
 
     def as_dict(self):
         return asdict(self)
@@ -132,6 +133,21 @@ def cubic(R: int = 152, L: int = 32, hops: int = 1_000_000) -> Workload:
                          seed=s, replica=s, dim=3) for s in range(R))
     return Workload(f"cubic_L{L}_T0.05_R{R}", reps, M=4096, hops=hops,
                     precision="fp32", refresh_every=1024)
+
+
+def random_sites(R: int = 152, L: int = 64, hops: int = 1_000_000,
+                 lattice: bool = False) -> Workload:
+    """The random-site Coulomb glass (the off-lattice model of the paper's
+    introduction): N = L^2 sites at uniform random positions in the L x L
+    periodic box, nu=1/2, phi ~ U[-0.5, 0.5], xi=1, partners within
+    r_max=6, T=0.05, E=0.01, one replica per SM, binary64 (the N x N
+    coupling matrix in device memory).  lattice=True: the same replicas on
+    the square lattice, for comparison."""
+    reps = tuple(Replica(L=L, nu=0.5, W=1.0, xi=1.0, r_max=6, T=0.05, E=0.01,
+                         seed=s, replica=s, sites=0 if lattice else 1) for s in range(R))
+    kind = "lattice" if lattice else "random"
+    return Workload(f"{kind}_L{L}_T0.05_R{R}", reps, M=4096, hops=hops,
+                    precision="fp64", refresh_every=0)
 
 
 # ---------------------------------------------------------------------------

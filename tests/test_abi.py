@@ -165,3 +165,42 @@ def test_product_package_has_no_cpu_path():
                 assert all(not a.name.startswith("oracle") for a in node.names), name
             if isinstance(node, ast.ImportFrom):
                 assert not (node.module or "").startswith("oracle"), name
+
+
+@pytest.mark.parametrize("bad,msg", [(dict(precision=1), "random sites"),
+                                     (dict(pair_frac=0.1, pair_rmax=2), "random sites"),
+                                     (dict(time_mode=1), "random sites"),
+                                     (dict(cluster_size=2), "random sites")])
+def test_random_sites_refuse_unsupported_options_on_host(libcg, bad, msg):
+    from paper_1407_5026_gb300 import binding as B
+    assert B.CG_FP32 == 1 and B.CG_TIME_GAUSSIAN == 1
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create_batch([B.desc(L=16, sites=B.CG_SITES_RANDOM)], B.opts(**bad))
+    assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("kw,msg", [(dict(sites=2), "sites must"),
+                                    (dict(sites=1, dim=3), "random sites")])
+def test_random_site_descriptor_checks_on_host(libcg, kw, msg):
+    from paper_1407_5026_gb300 import binding as B
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create_batch([B.desc(L=16, **kw)], B.opts())
+    assert msg in str(ei.value)
+
+
+def test_workspace_plan_counts_the_random_site_geometry(libcg):
+    # a random-site replica adds its positions (2 N doubles), the N x N
+    # coupling matrix, the list offsets (N + 1 ints) and per pair a partner
+    # (4 bytes), a running weight, 1/r and E dx (8 bytes each); the pair count
+    # is the oracle's, so the host geometry finds the same partners
+    import oracle
+    from paper_1407_5026_gb300 import binding as B
+    up = lambda b: (b + 255) // 256 * 256
+    p = dict(L=16, r_max=3, xi=1.0, seed=5, replica=2)
+    rnd = B.cg_workspace_bytes([B.desc(sites=B.CG_SITES_RANDOM, **p)], B.opts())
+    lat = B.cg_workspace_bytes([B.desc(**p)], B.opts())
+    cnt = len(oracle.Chain(16, r_max=3, xi=1.0, seed=5, replica=2, random_sites=True).pairs()[1])
+    N = 256
+    assert cnt > 0
+    assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up((N + 1) * 4) + up(cnt * 4) + \
+        3 * up(cnt * 8)
