@@ -593,8 +593,8 @@ def other_configs(args, B, local, only=None):
     tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
     4-CTA clusters (eps split by z-planes), 304 replicas of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair), and
-    152 binary64 replicas of L=64 with sites at random positions against the
-    same replicas on the lattice.  Each is timed with CUDA events over hops
+    152 binary64 replicas of L=64 (and of L=32) with sites at random
+    positions against the L=64 replicas on the lattice.  Each is timed with CUDA events over hops
     that follow a relaxation from the random start."""
     import torch
     from paper_1407_5026_gb300 import workloads as W
@@ -607,6 +607,7 @@ def other_configs(args, B, local, only=None):
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False),
             ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False),
+            ("random_L32_T0.05_R152_fp64", W.random_sites(L=32), 2048, 2048, 0, False),
             ("lattice_L64_T0.05_R152_fp64", W.random_sites(lattice=True), 2048, 2048, 0, False)):
         if only is not None and name != only:
             continue
@@ -635,12 +636,22 @@ def other_configs(args, B, local, only=None):
                      "M": "autotuned per L" if tune else wl.M,
                      "groups": [shape_of(B, s.h, g, tune) for g in range(B.cg_num_groups(s.h))],
                      "max_eps_err": max(o["max_eps_err_last_refresh"] for o in o1),
-                     "graph": bool(graph)}
+                     "graph": bool(graph),
+                     # share of the kernels' SM cycles spent in the eps update
+                     # (the rest: label rounds), from the per-replica phase
+                     # clocks over the timed hops
+                     "update_cycle_share": update_share(o0, o1)}
         if pair:
             out[name].update(pair)
             out[name]["pair_hops_share"] = pair_share(B, s, reps, wl.M)
         s.close()
     return out
+
+
+def update_share(o0, o1):
+    upd = sum(b["cycles_update"] - a["cycles_update"] for a, b in zip(o0, o1))
+    rej = sum(b["cycles_reject"] - a["cycles_reject"] for a, b in zip(o0, o1))
+    return round(upd / max(1, upd + rej), 4)
 
 
 def sigma_l256(B, local, hops, R=16, points_per_decade=5.0, first_time=1e-3):

@@ -82,8 +82,11 @@ struct RLabel {
     bool theta;
 };
 
-// Label k's site, partner and theta (the partner by binary search over the
-// running weights of i's list: the smallest m with x1 < C_m).
+// Label k's site, partner and theta.  An empty site i has theta = 0 whatever
+// its partner, so the partner is looked up for occupied sites only: the
+// smallest m of i's list with x1 < C_m, by a four-way search (three
+// independent probes per step, so about half the dependent global loads of
+// a binary search) and a last scan of at most four entries.
 __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const unsigned *occ,
                                                  unsigned k, const PhiloxPrefix &PP,
                                                  uint32_t key0, uint32_t key1, unsigned N,
@@ -98,15 +101,37 @@ __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const uns
     philox_finish(k, PP, key0, key1, x);
     p.i = __umulhi(x[0], N);
     p.x2 = x[2];
+    if (!((occ[p.i >> 5] >> (p.i & 31)) & 1u)) return p;
+    const unsigned long long x1 = x[1];
     int lo = __ldg(Rg.roff + p.i), hi = __ldg(Rg.roff + p.i + 1);
-    if (lo == hi || (unsigned long long)x[1] >= __ldg(Rg.rC + hi - 1)) return p;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((unsigned long long)x[1] < __ldg(Rg.rC + mid)) hi = mid; else lo = mid + 1;
+    if (lo == hi || x1 >= __ldg(Rg.rC + hi - 1)) return p;
+    // the answer lies in [lo, hi)
+    while (hi - lo > 4) {
+        const int q = (hi - lo) >> 2;
+        const int m1 = lo + q, m2 = m1 + q, m3 = m2 + q;
+        const unsigned long long c1 = __ldg(Rg.rC + m1), c2 = __ldg(Rg.rC + m2),
+                                 c3 = __ldg(Rg.rC + m3);
+        if (x1 < c1) {
+            hi = m1 + 1;
+        } else if (x1 < c2) {
+            lo = m1 + 1;
+            hi = m2 + 1;
+        } else if (x1 < c3) {
+            lo = m2 + 1;
+            hi = m3 + 1;
+        } else {
+            lo = m3 + 1;
+        }
     }
-    p.m = (unsigned)lo;
-    p.j = __ldg(Rg.rj + lo);
-    p.theta = ((occ[p.i >> 5] >> (p.i & 31)) & 1u) && !((occ[p.j >> 5] >> (p.j & 31)) & 1u);
+    // the entries with x1 < C_m form a suffix of [lo, hi): walking down, the
+    // last one that holds is the smallest
+    int m = hi - 1;
+#pragma unroll
+    for (int t = 1; t <= 3; ++t)
+        if (hi - 1 - t >= lo && x1 < __ldg(Rg.rC + hi - 1 - t)) m = hi - 1 - t;
+    p.m = (unsigned)m;
+    p.j = __ldg(Rg.rj + m);
+    p.theta = !((occ[p.j >> 5] >> (p.j & 31)) & 1u);     // n_i = 1 here
     return p;
 }
 
@@ -163,21 +188,14 @@ pr_random(const DevReplica *__restrict__ reps, const int *__restrict__ index, Ru
     __syncthreads();
 
     const unsigned M = a.M;
+    // one label per thread in every chunk: a chunk costs the latency of one
+    // chain of dependent global loads (list offsets, search probes, partner,
+    // 1/r) however many labels it holds, so the widest chunk settles a hop in
+    // the fewest chunks; a second label per thread would run a second chain
+    // after the first.  C changes which labels are evaluated, never the hop.
+    const unsigned C = kThreads;
     for (unsigned long long h = 0; h < a.n_hops; ++h) {
         if (tid == 0) s_c.t0 = clock64();
-        // labels per chunk ~ sqrt(128 m) for m expected labels per hop (the
-        // lattice kernel's rule): two per thread above blockDim
-        const float want = sqrtf(128.0f * s_c.m_ema);
-        unsigned C;
-        if (want > (float)kThreads) {
-            C = 2u * kThreads;
-        } else {
-            C = 64;
-            while (C < (unsigned)kThreads && (float)C < want) C <<= 1;
-            if (C > (unsigned)kThreads) C = kThreads;
-        }
-        const bool two = C > (unsigned)kThreads;
-        const bool act = (unsigned)tid < C;
         unsigned long long p = 0;
         unsigned q = 0, win = 0, kb_hit = 0;
         bool found = false;
@@ -186,35 +204,22 @@ pr_random(const DevReplica *__restrict__ reps, const int *__restrict__ index, Ru
             const PhiloxPrefix PP =
                 philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
             for (unsigned kb = 0; kb < M; kb += C) {
-                const unsigned k0 = kb + (unsigned)tid, k1 = k0 + (unsigned)kThreads;
-                const bool v0 = act && k0 < M, v1 = act && two && k1 < M;
-                RLabel p0 = propose_random(Rg, occ, k0, PP, key0, key1, (unsigned)N, v0);
-                RLabel p1{};
-                p1.theta = false;
-                if (two) p1 = propose_random(Rg, occ, k1, PP, key0, key1, (unsigned)N, v1);
-                double dE0 = 0.0, dE1 = 0.0;
-                bool acc0 = false, acc1 = false;
+                const unsigned k0 = kb + (unsigned)tid;
+                const RLabel p0 = propose_random(Rg, occ, k0, PP, key0, key1, (unsigned)N, k0 < M);
+                double dE0 = 0.0;
+                bool acc0 = false;
                 if (p0.theta) {
                     dE0 = dE_random(Rg, eps, p0);
                     acc0 = metropolis64(dE0, p0.x2, T, invTf);
                 }
-                if (p1.theta) {
-                    dE1 = dE_random(Rg, eps, p1);
-                    acc1 = metropolis64(dE1, p1.x2, T, invTf);
-                }
-                const int any = __syncthreads_or(acc0 || acc1);
+                const int any = __syncthreads_or(acc0);
                 if (any) {
                     const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
-                    const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
                     unsigned off = 0xffffffffu;
                     if (b0) {
                         const int first = __ffs(b0) - 1;
                         off = (unsigned)(warp * 32 + first);
                         if (lane == first) s_cand[warp] = RCand{p0.i, p0.j, dE0};
-                    } else if (b1) {
-                        const int first = __ffs(b1) - 1;
-                        off = (unsigned)(kThreads + warp * 32 + first);
-                        if (lane == first) s_cand[warp] = RCand{p1.i, p1.j, dE1};
                     }
                     if (lane == 0) s_wlabel[warp] = off;
                     __syncthreads();
@@ -223,7 +228,7 @@ pr_random(const DevReplica *__restrict__ reps, const int *__restrict__ index, Ru
                     for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
                     q = kb + wl + 1;                 // 1-based label in the round
                     kb_hit = kb;
-                    win = (wl >= (unsigned)kThreads ? wl - (unsigned)kThreads : wl) >> 5;
+                    win = wl >> 5;
                     found = true;
                     break;
                 }
