@@ -71,11 +71,9 @@ struct alignas(16) DevReplica {
     cg_trace_point *trace;    // NULL, or ctr->trace_cap points
     // random-site geometry (CG_SITES_RANDOM; null otherwise)
     const double *G;          // N x N minimum-image 1/r, 0 on the diagonal
-    const int *roff;          // N + 1 offsets of the partner lists
-    const unsigned int *rj;   // partners, ascending within each list
-    const unsigned long long *rC; // running integer weights within each list
-    const double *rg;         // 1/r of each pair
-    const double *redx;       // E dx of each pair (minimum-image dx, binary64)
+    const int *rguide;        // 16 ints per site: kRandomGuide layout
+    const uint4 *rrec;        // per pair: running weight C (lo, hi words), partner j, 0
+    const double2 *rgx;       // per pair: 1/r, E dx (minimum-image dx, binary64)
 };
 
 // Thread 0 at commit: record trace points whose attempt threshold the
@@ -146,6 +144,13 @@ cudaError_t launch_eps_init_random(const DevReplica *d_rep, int N, cudaStream_t 
 cudaError_t launch_pr_random(const DevReplica *d_reps, const int *d_index, int n_ctas,
                              int threads, int smem_bytes, const RunArgs &args, cudaStream_t st);
 cudaError_t set_pr_random_smem_limit(int bytes);
+// The per-site record of a random-site partner list (16 ints, 64 bytes):
+// [0] first pair of the list, [9] one past its last; [1 + b], b = 0..7, the
+// pair that x1 = b 2^29 selects (the smallest m with b 2^29 < C_m; the last
+// pair when none); [12], [13] the list's last running weight (lo, hi words).
+// A label with x1 in bucket b = x1 >> 29 finds its pair in
+// [g[1 + b], min(g[2 + b], g[9] - 1)].
+constexpr int kRandomGuide = 16;
 inline int random_smem_bytes(int N)
 {
     return cg_align16(N * 8) + cg_align16(((N + 31) / 32) * 4);

@@ -236,10 +236,10 @@ struct Rep {
     std::vector<unsigned> rj;
     std::vector<unsigned long long> rC;
     double Zmax = 0.0;
-    double *d_px = nullptr, *d_py = nullptr, *d_G = nullptr, *d_rg = nullptr, *d_redx = nullptr;
-    int *d_roff = nullptr;
-    unsigned *d_rj = nullptr;
-    unsigned long long *d_rC = nullptr;
+    double *d_px = nullptr, *d_py = nullptr, *d_G = nullptr;
+    int *d_guide = nullptr;           // kRandomGuide ints per site
+    uint4 *d_rec = nullptr;           // running weight and partner of each pair
+    double2 *d_rgx = nullptr;         // 1/r and E dx of each pair
 };
 
 struct Group {
@@ -457,8 +457,42 @@ void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
     dr.C0 = t.C0;
     dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
     dr.log = log;
-    dr.G = r.d_G; dr.roff = r.d_roff; dr.rj = r.d_rj; dr.rC = r.d_rC;
-    dr.rg = r.d_rg; dr.redx = r.d_redx;
+    dr.G = r.d_G; dr.rguide = r.d_guide; dr.rrec = r.d_rec; dr.rgx = r.d_rgx;
+}
+
+// The device form of a random-site replica's partner lists: per site the
+// kRandomGuide record (list bounds, the pair each x1 bucket starts at, the
+// last running weight), per pair (C lo, C hi, j, 0) and (1/r, E dx).
+void pack_random(const Rep &r, std::vector<int> &guide, std::vector<uint32_t> &rec,
+                 std::vector<double> &rgx)
+{
+    const int N = r.N;
+    const size_t m = r.rj.size();
+    guide.assign((size_t)N * kRandomGuide, 0);
+    rec.assign(4 * m, 0u);
+    rgx.assign(2 * m, 0.0);
+    for (size_t k = 0; k < m; ++k) {
+        rec[4 * k] = (uint32_t)r.rC[k];
+        rec[4 * k + 1] = (uint32_t)(r.rC[k] >> 32);
+        rec[4 * k + 2] = r.rj[k];
+        rgx[2 * k] = r.rg[k];
+        rgx[2 * k + 1] = r.redx[k];
+    }
+    for (int s = 0; s < N; ++s) {
+        int *g = guide.data() + (size_t)s * kRandomGuide;
+        const int lo = r.roff[s], hi = r.roff[s + 1];
+        g[0] = lo;
+        g[9] = hi;
+        int a = lo;
+        for (int b = 0; b < 8; ++b) {
+            const unsigned long long v = (unsigned long long)b << 29;
+            while (a < hi && !(v < r.rC[a])) ++a;      // smallest a with v < C_a
+            g[1 + b] = a < hi ? a : (hi > lo ? hi - 1 : lo);
+        }
+        const unsigned long long last = hi > lo ? r.rC[hi - 1] : 0ull;
+        g[12] = (int)(uint32_t)last;
+        g[13] = (int)(uint32_t)(last >> 32);
+    }
 }
 
 // Random sites: positions from Philox counter (s, 3, 0xFFFFFFFF, replica),
@@ -684,8 +718,7 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
             tmp.N = (int)N;
             const size_t cnt = build_random(tmp) == CG_OK ? tmp.rj.size() : 0;
             const size_t c1 = cnt ? cnt : 1;
-            total += 2 * up(N * 8) + up(N * N * 8) + up((N + 1) * 4) + up(c1 * 4) +
-                     3 * up(c1 * 8);
+            total += 2 * up(N * 8) + up(N * N * 8) + up(N * kRandomGuide * 4) + 2 * up(c1 * 16);
         }
         auto key = std::make_tuple(d.L, d.r_max, d.xi, dim_of(d));
         if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
@@ -837,20 +870,21 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         const size_t N = (size_t)r.N, cnt = std::max<size_t>(r.rj.size(), 1);
         if (dalloc(h.get(), (void **)&r.d_px, N * 8) || dalloc(h.get(), (void **)&r.d_py, N * 8) ||
             dalloc(h.get(), (void **)&r.d_G, N * N * 8) ||
-            dalloc(h.get(), (void **)&r.d_roff, (N + 1) * 4) ||
-            dalloc(h.get(), (void **)&r.d_rj, cnt * 4) ||
-            dalloc(h.get(), (void **)&r.d_rC, cnt * 8) ||
-            dalloc(h.get(), (void **)&r.d_rg, cnt * 8) ||
-            dalloc(h.get(), (void **)&r.d_redx, cnt * 8)) { destroy_partial(); return nullptr; }
+            dalloc(h.get(), (void **)&r.d_guide, N * kRandomGuide * 4) ||
+            dalloc(h.get(), (void **)&r.d_rec, cnt * 16) ||
+            dalloc(h.get(), (void **)&r.d_rgx, cnt * 16)) { destroy_partial(); return nullptr; }
         const size_t m = r.rj.size();
+        std::vector<int> guide;
+        std::vector<uint32_t> rec;
+        std::vector<double> rgx;
+        pack_random(r, guide, rec, rgx);
         cudaMemcpyAsync(r.d_px, r.px.data(), N * 8, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(r.d_py, r.py.data(), N * 8, cudaMemcpyHostToDevice, h->st);
-        cudaMemcpyAsync(r.d_roff, r.roff.data(), (N + 1) * 4, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(r.d_guide, guide.data(), N * kRandomGuide * 4, cudaMemcpyHostToDevice,
+                        h->st);
         if (m) {
-            cudaMemcpyAsync(r.d_rj, r.rj.data(), m * 4, cudaMemcpyHostToDevice, h->st);
-            cudaMemcpyAsync(r.d_rC, r.rC.data(), m * 8, cudaMemcpyHostToDevice, h->st);
-            cudaMemcpyAsync(r.d_rg, r.rg.data(), m * 8, cudaMemcpyHostToDevice, h->st);
-            cudaMemcpyAsync(r.d_redx, r.redx.data(), m * 8, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_rec, rec.data(), m * 16, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_rgx, rgx.data(), m * 16, cudaMemcpyHostToDevice, h->st);
         }
         if (launch_g_build(r.d_px, r.d_py, r.d.L, r.N, r.d_G, h->st) != cudaSuccess) {
             fail(CG_ECUDA, "coupling-matrix build failed to launch");

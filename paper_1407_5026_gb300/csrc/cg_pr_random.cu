@@ -84,9 +84,12 @@ struct RLabel {
 
 // Label k's site, partner and theta.  An empty site i has theta = 0 whatever
 // its partner, so the partner is looked up for occupied sites only: the
-// smallest m of i's list with x1 < C_m, by a four-way search (three
-// independent probes per step, so about half the dependent global loads of
-// a binary search) and a last scan of at most four entries.
+// smallest m of i's list with x1 < C_m.  One 64-byte load of i's guide record
+// gives the list's bounds, its last running weight (x1 at or above it: a null
+// proposal) and the bucket of pairs x1 >> 29 can select; a four-way search
+// (three independent probes per step) narrows the bucket to at most four
+// records, and the last scan reads whole records, so the partner comes with
+// its running weight.
 __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const unsigned *occ,
                                                  unsigned k, const PhiloxPrefix &PP,
                                                  uint32_t key0, uint32_t key1, unsigned N,
@@ -103,14 +106,32 @@ __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const uns
     p.x2 = x[2];
     if (!((occ[p.i >> 5] >> (p.i & 31)) & 1u)) return p;
     const unsigned long long x1 = x[1];
-    int lo = __ldg(Rg.roff + p.i), hi = __ldg(Rg.roff + p.i + 1);
-    if (lo == hi || x1 >= __ldg(Rg.rC + hi - 1)) return p;
-    // the answer lies in [lo, hi)
+    const int4 *g4 = reinterpret_cast<const int4 *>(Rg.rguide + (size_t)p.i * kRandomGuide);
+    const int4 ga = __ldg(g4), gb = __ldg(g4 + 1), gc = __ldg(g4 + 2), gd = __ldg(g4 + 3);
+    const int first = ga.x, end = gc.y;                    // [0] and [9]
+    const unsigned long long last =
+        (unsigned long long)(uint32_t)gd.x | ((unsigned long long)(uint32_t)gd.y << 32);
+    if (first == end || x1 >= last) return p;
+    // g[1 + b] and g[2 + b] for b = x1 >> 29 (g[1..8] in ga.y .. gc.x, g[9] = end)
+    int glo, ghi;
+    switch (x[1] >> 29) {
+    case 0: glo = ga.y; ghi = ga.z; break;
+    case 1: glo = ga.z; ghi = ga.w; break;
+    case 2: glo = ga.w; ghi = gb.x; break;
+    case 3: glo = gb.x; ghi = gb.y; break;
+    case 4: glo = gb.y; ghi = gb.z; break;
+    case 5: glo = gb.z; ghi = gb.w; break;
+    case 6: glo = gb.w; ghi = gc.x; break;
+    default: glo = gc.x; ghi = gc.y; break;
+    }
+    int lo = glo, hi = min(ghi, end - 1) + 1;
+    const unsigned long long *rc = reinterpret_cast<const unsigned long long *>(Rg.rrec);
+    // the answer lies in [lo, hi); record m's running weight is rc[2 m]
     while (hi - lo > 4) {
         const int q = (hi - lo) >> 2;
         const int m1 = lo + q, m2 = m1 + q, m3 = m2 + q;
-        const unsigned long long c1 = __ldg(Rg.rC + m1), c2 = __ldg(Rg.rC + m2),
-                                 c3 = __ldg(Rg.rC + m3);
+        const unsigned long long c1 = __ldg(rc + 2 * m1), c2 = __ldg(rc + 2 * m2),
+                                 c3 = __ldg(rc + 2 * m3);
         if (x1 < c1) {
             hi = m1 + 1;
         } else if (x1 < c2) {
@@ -123,14 +144,23 @@ __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const uns
             lo = m3 + 1;
         }
     }
-    // the entries with x1 < C_m form a suffix of [lo, hi): walking down, the
+    // the records with x1 < C_m form a suffix of [lo, hi): walking down, the
     // last one that holds is the smallest
     int m = hi - 1;
+    unsigned j = __ldg(Rg.rrec + m).z;
 #pragma unroll
-    for (int t = 1; t <= 3; ++t)
-        if (hi - 1 - t >= lo && x1 < __ldg(Rg.rC + hi - 1 - t)) m = hi - 1 - t;
+    for (int t = 1; t <= 3; ++t) {
+        const int mt = hi - 1 - t;
+        if (mt >= lo) {
+            const uint4 r = __ldg(Rg.rrec + mt);
+            if (x1 < ((unsigned long long)r.x | ((unsigned long long)r.y << 32))) {
+                m = mt;
+                j = r.z;
+            }
+        }
+    }
     p.m = (unsigned)m;
-    p.j = __ldg(Rg.rj + m);
+    p.j = j;
     p.theta = !((occ[p.j >> 5] >> (p.j & 31)) & 1u);     // n_i = 1 here
     return p;
 }
@@ -138,7 +168,8 @@ __device__ __forceinline__ RLabel propose_random(const DevReplica &Rg, const uns
 __device__ __forceinline__ double dE_random(const DevReplica &Rg, const double *eps,
                                             const RLabel &p)
 {
-    return d_sub(d_sub(d_sub(eps[p.j], eps[p.i]), __ldg(Rg.rg + p.m)), __ldg(Rg.redx + p.m));
+    const double2 gx = __ldg(Rg.rgx + p.m);          // 1/r_ij, E dx_ij
+    return d_sub(d_sub(d_sub(eps[p.j], eps[p.i]), gx.x), gx.y);
 }
 
 template <int kThreads>

@@ -190,8 +190,8 @@ def test_random_site_descriptor_checks_on_host(libcg, kw, msg):
 
 def test_workspace_plan_counts_the_random_site_geometry(libcg):
     # a random-site replica adds its positions (2 N doubles), the N x N
-    # coupling matrix, the list offsets (N + 1 ints) and per pair a partner
-    # (4 bytes), a running weight, 1/r and E dx (8 bytes each); the pair count
+    # coupling matrix, a 64-byte guide record per site and per pair two
+    # 16-byte records (running weight + partner; 1/r + E dx); the pair count
     # is the oracle's, so the host geometry finds the same partners
     import oracle
     from paper_1407_5026_gb300 import binding as B
@@ -202,5 +202,4 @@ def test_workspace_plan_counts_the_random_site_geometry(libcg):
     cnt = len(oracle.Chain(16, r_max=3, xi=1.0, seed=5, replica=2, random_sites=True).pairs()[1])
     N = 256
     assert cnt > 0
-    assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up((N + 1) * 4) + up(cnt * 4) + \
-        3 * up(cnt * 8)
+    assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up(N * 64) + 2 * up(cnt * 16)
