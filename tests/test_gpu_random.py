@@ -5,7 +5,8 @@ Binary64, so every logged hop (sites, label, round, dH bit for bit), the
 final occupation, eps bit for bit and the counters equal the oracle's:
 for powers of two and other even L, with and without a field, one replica
 and a batch that mixes random-site and lattice replicas (graph replay
-included).  A refresh rebuilds eps from its definition bit for bit.
+included).  A refresh rebuilds eps from its definition bit for bit; every
+CTA size and the autotuner keep the chain; the lattice-only calls refuse.
 """
 import numpy as np
 import pytest
@@ -113,5 +114,57 @@ def test_random_site_state_round_trip(B):
         assert ch.run(200, 1024)[0] == oracle.ORC_OK
         np.testing.assert_array_equal(s.state(0)[0], ch.state()[0])
         np.testing.assert_array_equal(_bits(s.state(0)[1]), _bits(ch.eps_scratch()))
+    finally:
+        s.close()
+
+
+def _random_p(B, **kw):
+    p = dict(L=16, nu=0.5, W=1.0, xi=1.0, r_max=3, T=0.1, E=0.01, seed=8, replica=1,
+             sites=B.CG_SITES_RANDOM)
+    p.update(kw)
+    return p
+
+
+@pytest.mark.parametrize("threads", [256, 384, 512])
+def test_random_site_cta_sizes_bit_exact(B, threads):
+    # every CTA size evaluates the labels in its own chunks; the hops are
+    # the serial chain's
+    p = _random_p(B)
+    s = B.System([p], precision=B.CG_FP64, block_threads=threads)
+    try:
+        assert B.cg_group_shape(s.h, 0)["threads"] == threads
+        rc, log = s.run_logged(600, 700)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p)
+        _, olog = ch.run(600, 700, log=True)
+        _check_same(s, 0, ch, log[0], olog)
+    finally:
+        s.close()
+
+
+def test_random_site_autotune_keeps_the_chain(B):
+    # the autotuner's trial launches run on a snapshot that is restored
+    p = _random_p(B, seed=12)
+    s = B.System([p], precision=B.CG_FP64)
+    try:
+        B.cg_autotune(s.h, 64)
+        assert B.cg_group_shape(s.h, 0)["threads"] in (256, 384, 512, 1024)
+        rc, log = s.run_logged(400, 512)
+        assert rc == B.CG_OK
+        ch = _oracle_for(p)
+        _, olog = ch.run(400, 512, log=True)
+        _check_same(s, 0, ch, log[0], olog)
+    finally:
+        s.close()
+
+
+def test_random_site_handle_refuses_lattice_only_calls(B):
+    s = B.System([_random_p(B)], precision=B.CG_FP64)
+    try:
+        with pytest.raises(B.CgError, match="constant-acceptance"):
+            B.cg_set_toy_acceptance(s.h, 0.5)
+        with pytest.raises(B.CgError, match="partner lists"):
+            B.cg_debug_tower(s.h, 0, [1, 2, 3])
+        assert s.run(50, 256) == B.CG_OK
     finally:
         s.close()
