@@ -225,6 +225,14 @@ const char *cg_last_error(void);
 int cg_num_replicas(const cg_handle *h);
 int cg_num_sites(const cg_handle *h, int replica);
 
+/* Positions of a random-site replica's N sites (CG_SITES_RANDOM; the
+ * Philox positions of the descriptor's definition, in the L x L box): x into
+ * x_host[0..N), y into y_host[0..N) (caller-owned host arrays).  With the
+ * occupation from cg_read_state they give the real dipole sum n_s x_s, which
+ * the counters do not keep on random sites.  CG_EINVAL for a null handle or
+ * output, a replica out of range or a lattice replica; no device work. */
+int cg_site_positions(const cg_handle *h, int replica, double *x_host, double *y_host);
+
 /* Advance every replica by n_hops executed hops with M labels per round
  * (mixed PR algorithm, steps 1-3; 1 <= M <= 2^24, or M = 0 for each lattice
  * size's own M: 4096 unless cg_autotune chose another).  Blocks until the

@@ -34,7 +34,7 @@ EXPORTED = [
     "cg_set_toy_acceptance", "cg_debug_philox", "cg_debug_exp", "cg_debug_tower", "cg_version",
     "cg_group_replicas", "cg_read_group_state", "cg_write_group_state", "cg_debug_gauss",
     "cg_refresh_tc_noalloc", "cg_autotune", "cg_num_groups", "cg_group_shape",
-    "cg_set_trace", "cg_read_trace", "cg_eps_histogram",
+    "cg_set_trace", "cg_read_trace", "cg_eps_histogram", "cg_site_positions",
 ]
 
 
@@ -138,6 +138,8 @@ def load(path: str | None = None):
             "cg_last_error": (ctypes.c_char_p, []),
             "cg_num_replicas": (ctypes.c_int, [vp]),
             "cg_num_sites": (ctypes.c_int, [vp, ctypes.c_int]),
+            "cg_site_positions": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double)]),
             "cg_run": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32]),
             "cg_run_async": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32]),
             "cg_sync": (ctypes.c_int, [vp]),
@@ -261,6 +263,16 @@ def cg_num_replicas(h) -> int:
 
 def cg_num_sites(h, replica=0) -> int:
     return load().cg_num_sites(h, replica)
+
+
+def cg_site_positions(h, replica=0, n_sites=None):
+    """(x, y) of a random-site replica's sites (float64 arrays)."""
+    N = cg_num_sites(h, replica) if n_sites is None else int(n_sites)
+    x = np.zeros(max(N, 1), dtype=np.float64)
+    y = np.zeros(max(N, 1), dtype=np.float64)
+    _check(load().cg_site_positions(h, replica, _ptr(x, ctypes.c_double),
+                                    _ptr(y, ctypes.c_double)))
+    return x[:N], y[:N]
 
 
 def cg_run(h, n_hops, M):

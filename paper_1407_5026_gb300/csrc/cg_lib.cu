@@ -1267,6 +1267,18 @@ void cg_destroy(cg_handle *h)
 
 int cg_num_replicas(const cg_handle *h) { return h ? (int)h->reps.size() : 0; }
 
+int cg_site_positions(const cg_handle *h, int replica, double *x_host, double *y_host)
+{
+    const int rc = replica_index_ok(h, replica);
+    if (rc) return rc;
+    if (!x_host || !y_host) return fail(CG_EINVAL, "null output");
+    const Rep &r = h->reps[replica];
+    if (!r.random) return fail(CG_EINVAL, "a lattice replica's sites are its lattice points");
+    std::memcpy(x_host, r.px.data(), sizeof(double) * (size_t)r.N);
+    std::memcpy(y_host, r.py.data(), sizeof(double) * (size_t)r.N);
+    return CG_OK;
+}
+
 int cg_num_sites(const cg_handle *h, int replica)
 {
     if (!h || replica < 0 || replica >= (int)h->reps.size()) return 0;

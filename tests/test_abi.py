@@ -203,3 +203,9 @@ def test_workspace_plan_counts_the_random_site_geometry(libcg):
     N = 256
     assert cnt > 0
     assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up(N * 64) + 2 * up(cnt * 16)
+
+
+def test_site_positions_checks_its_arguments_on_host(libcg):
+    from paper_1407_5026_gb300 import binding as B
+    with pytest.raises(B.CgError, match="null handle"):
+        B.cg_site_positions(None, 0, n_sites=4)

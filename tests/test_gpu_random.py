@@ -168,3 +168,17 @@ def test_random_site_handle_refuses_lattice_only_calls(B):
         assert s.run(50, 256) == B.CG_OK
     finally:
         s.close()
+
+
+def test_site_positions_equal_the_oracle(B):
+    p = _random_p(B, L=12, seed=3, replica=5)
+    s = B.System([p, dict(p, sites=0)], precision=B.CG_FP64)
+    try:
+        x, y = B.cg_site_positions(s.h, 0)
+        ox, oy = _oracle_for(p).positions()
+        np.testing.assert_array_equal(_bits(x), _bits(ox))
+        np.testing.assert_array_equal(_bits(y), _bits(oy))
+        with pytest.raises(B.CgError, match="lattice"):
+            B.cg_site_positions(s.h, 1)
+    finally:
+        s.close()
