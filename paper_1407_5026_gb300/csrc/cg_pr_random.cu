@@ -12,10 +12,12 @@
 // the minimum-image fold maps d to -d exactly.
 //
 // pr_random: one CTA per replica, binary64; eps and the occupation bitmask in
-// shared memory, the partner lists and G in global memory (read-only path).
-// The round / chunk / lowest-accepting-label structure is that of the
-// lattice's persistent kernel (mixed PR algorithm, steps 1-3), so the
-// trajectory equals the serial chain's on the same random numbers:
+// shared memory, the partner lists (a 64-byte guide record per site, 16-byte
+// pair records) and G in global memory (read-only path).  The round and
+// lowest-accepting-label structure is that of the lattice's persistent
+// kernel (mixed PR algorithm, steps 1-3), with one label per thread in every
+// chunk, so the trajectory equals the serial chain's on the same random
+// numbers:
 //   label k of round r: Philox(ctr = (k, r lo, r hi, replica)) -> site
 //   i = floor(x0 N 2^-32), partner m = smallest in i's list with
 //   x1 < C_m (C the running integer weights; none: a null proposal),
