@@ -77,6 +77,40 @@ def test_cluster_constant_acceptance_matches_oracle(B):
         s.close()
 
 
+@pytest.mark.parametrize("cluster", [2, 4])
+def test_cluster_hop_time_limit_returns_timeout(B, cluster):
+    # a hop that never ends (no label accepts, unbounded rounds): rank 0's
+    # wall clock passes the limit, every CTA of the cluster reads that
+    # decision from rank 0's exchange slot after the same cluster barrier and
+    # the launch stores a valid state
+    p = dict(L=32, nu=0.5, W=1.0, xi=1.0, r_max=4, T=0.05, E=0.0, seed=3)
+    s = B.System([p], precision=B.CG_FP64, cluster_size=cluster, hop_timeout_ms=200)
+    try:
+        assert B.cg_group_shape(s.h, 0)["cluster"] == cluster
+        n0, e0, _, c0 = s.state(0)
+        B.cg_set_toy_acceptance(s.h, 0.0)
+        with pytest.raises(B.CgError) as ei:
+            s.run(1, 1024)
+        assert ei.value.code == B.CG_ETIMEOUT
+        n1, e1, _, c1 = s.state(0)
+        np.testing.assert_array_equal(n0, n1)
+        np.testing.assert_array_equal(_bits(e0), _bits(e1))
+        assert c1["hops"] == c0["hops"]
+        # complete failed rounds only: M attempts and one round each
+        assert c1["rounds"] > c0["rounds"]
+        assert c1["attempts"] - c0["attempts"] == 1024 * (c1["rounds"] - c0["rounds"])
+        # the handle keeps working and still follows the serial chain
+        B.cg_set_toy_acceptance(s.h, -1.0)
+        _, log = s.run_logged(50, 256)
+        ch = _oracle_for(p)
+        ch.set_counters(dict(c1))
+        _, olog = ch.run(50, 256, log=True)
+        for f in ("i", "j", "q", "p", "round"):
+            np.testing.assert_array_equal(log[0][f], olog[f], err_msg=f)
+    finally:
+        s.close()
+
+
 def test_l256_binary32_cluster_keeps_eps_within_1em4(B):
     reps = [dict(L=256, nu=0.5, W=1.0, xi=1.5, r_max=10, T=0.02, E=0.005, seed=s, replica=s)
             for s in range(2)]
