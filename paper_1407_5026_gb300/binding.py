@@ -367,18 +367,6 @@ def cg_read_trace(h, replica=0, capacity=256):
     return out[:n]
 
 
-def sigma_windows(trace, N, E, Gamma=None):
-    """Conductivity of Eq. 3, sigma = (1 / N E) dP/dt, over the windows between
-    consecutive trace points, on the time each point recorded (attempts /
-    Gamma, or the stochastic time of CG_TIME_GAUSSIAN); returns (t_mid, sigma)."""
-    t = trace["time"].astype(np.float64)
-    P = trace["P"].astype(np.float64)
-    dt = np.diff(t)
-    keep = dt > 0
-    t_mid = 0.5 * (t[1:] + t[:-1])[keep]
-    return t_mid, (np.diff(P)[keep] / dt[keep]) / (N * E)
-
-
 def cg_autotune(h, hops_per_trial=0):
     return _check(load().cg_autotune(h, hops_per_trial))
 

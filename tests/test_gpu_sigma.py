@@ -22,8 +22,8 @@ def B():
 
 
 def test_l256_sigma_binary32_matches_binary64(B):
-    import bench
-    r = bench.sigma_l256(B, 0, hops=40_000, R=8)
+    from paper_1407_5026_gb300 import sigma
+    r = sigma.compare_forms_l256(B, 0, hops=40_000, R=8)
     assert r["clusters"]["fp32"] >= 2 and r["clusters"]["fp64"] >= 2
     assert r["windows"] >= 10
     assert np.all(np.diff(r["t"]) > 0)

@@ -15,6 +15,8 @@ import pytest
 
 import oracle
 
+from paper_1407_5026_gb300.sigma import sigma_windows
+
 pytestmark = pytest.mark.gpu
 
 
@@ -97,7 +99,7 @@ def test_trace_points_carry_the_time(B):
                     t_at[h] = ch.counters()["time"]
                 for pt in tr[1:]:
                     assert pt["time"] == t_at[int(pt["hops"])]
-            t, sig = B.sigma_windows(tr, 32 * 32, 0.05)
+            t, sig = sigma_windows(tr, 32 * 32, 0.05)
             assert np.all(np.diff(t) > 0) and np.isfinite(sig).all()
         finally:
             s.close()

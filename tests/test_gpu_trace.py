@@ -12,6 +12,8 @@ import pytest
 
 import oracle
 
+from paper_1407_5026_gb300.sigma import sigma_windows
+
 pytestmark = pytest.mark.gpu
 
 
@@ -62,7 +64,7 @@ def test_trace_points_follow_the_serial_chain(B):
             h = int(tr[k]["hops"])
             assert tr[k]["attempts"] == att[h - 1]
             assert tr[k]["P"] == P[h - 1]
-        t, sig = B.sigma_windows(tr, 32 * 32, 0.05, Gamma)
+        t, sig = sigma_windows(tr, 32 * 32, 0.05)
         assert np.all(np.diff(t) > 0)
         assert sig[len(sig) // 2:].mean() > 0      # current along the field
     finally:
