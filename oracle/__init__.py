@@ -9,7 +9,10 @@ C file's header.
 
 Parity status of each oracle function (what pins it, in ``tests/``):
 
-* ``philox``            pinned: cuRAND's host-side Philox4_32_10 generator.
+* ``philox``            pinned: cuRAND's host-side Philox4_32_10 generator
+                        (counter words 0-2, both key words) and its device
+                        generator (all four counter words, on a GPU:
+                        tests/test_gpu_philox_curand.py).
 * ``cg_exp``            pinned: ``math.exp`` within 2 ulp over [-23, 0].
 * tables / tower        pinned: closed forms (Gauss circle counts, 1/sqrt 2,
                         shell symmetry, sum of weights).

@@ -67,8 +67,9 @@ def test_philox_matches_curand_host_generator(seed):
 
 
 def test_philox_counter_word3_changes_output():
-    # word 3 is not reachable through cuRAND's host generator; at least check
-    # that it is consumed (distinct replicas give distinct streams)
+    # word 3 is not reachable through cuRAND's host generator (its device
+    # generator reaches it: tests/test_gpu_philox_curand.py); here only that
+    # it is consumed (distinct replicas give distinct streams)
     key = [7, 9]
     a = oracle.philox([1, 2, 3, 0], key)
     b = oracle.philox([1, 2, 3, 1], key)
