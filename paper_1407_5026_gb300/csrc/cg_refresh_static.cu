@@ -17,6 +17,8 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>   // CUcontext / CUresult types of two driver entry points
+
 #include "cg_device.cuh"
 #include "cg_internal.h"
 
@@ -35,11 +37,44 @@ static __device__ __align__(256) unsigned char g_refresh_scratch[kStaticScratchB
 
 std::mutex g_mutex;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context id the address belongs to
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device address of the static scratch on the current device (looked up once
-// per device, with that device current).
+// Unique id of the CUDA context current on this thread (cuCtxGetCurrent +
+// cuCtxGetId through the runtime's driver entry points), 0 when there is none
+// or it cannot be read.  A device address of the static array is valid only in
+// the context it was looked up in: after cudaDeviceReset, or under another
+// context on the same ordinal, the array lives elsewhere.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx &&
+        get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of the static scratch on the current device: looked up with
+// that device current, once per device and context (again when the context
+// changed, e.g. after cudaDeviceReset).
 int scratch_address(int device, unsigned char **out)
 {
     if (device < 0 || device >= kMaxDevices) {
@@ -47,7 +82,8 @@ int scratch_address(int device, unsigned char **out)
         return CG_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[device]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_refresh_scratch);
         if (e != cudaSuccess) {
@@ -55,6 +91,8 @@ int scratch_address(int device, unsigned char **out)
             return CG_ECUDA;
         }
         g_scratch_ptr[device] = static_cast<unsigned char *>(p);
+        // the lookup makes the device's context current if none was
+        g_scratch_ctx[device] = current_context_id();
     }
     *out = g_scratch_ptr[device];
     return CG_OK;
