@@ -10,6 +10,16 @@
 
 namespace cg {
 
+// 32 x 32 -> 64-bit product as one wide multiply (both halves from one
+// instruction instead of a high and a low multiply).
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
+{
+    unsigned long long p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies, key bumped by the Weyl constants between rounds.
 __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1,
@@ -24,8 +34,9 @@ __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1,
             k1 += 0xBB67AE85u;
         }
 #ifdef __CUDA_ARCH__
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(0xD2511F53u, c0, hi0, lo0);
+        mul_wide(0xCD9E8D57u, c2, hi1, lo1);
 #else
         const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
         const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
@@ -56,13 +67,15 @@ __device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t c1, uint32_t c2, 
 {
     PhiloxPrefix P;
     // round 1: word 0 of the output and word 1 come from c1, c2 alone
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t hi1, lo1;
+    mul_wide(0xCD9E8D57u, c2, hi1, lo1);
     const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1;
     P.A = c3 ^ k1;
     // round 2 (keys bumped once): the product of word 0 is shared
     const uint32_t k0b = k0 + 0x9E3779B9u, k1b = k1 + 0xBB67AE85u;
-    P.B = __umulhi(0xD2511F53u, n0) ^ k1b;
-    P.x3 = 0xD2511F53u * n0;
+    uint32_t hb;
+    mul_wide(0xD2511F53u, n0, hb, P.x3);
+    P.B = hb ^ k1b;
     P.C = n1 ^ k0b;
     return P;
 }
@@ -71,10 +84,13 @@ __device__ __forceinline__ void philox_finish(uint32_t k, const PhiloxPrefix &P,
                                               uint32_t k1, uint32_t out[4])
 {
     // round 1, the k-dependent half
-    const uint32_t n2 = __umulhi(0xD2511F53u, k) ^ P.A, n3 = 0xD2511F53u * k;
+    uint32_t h1, n3;
+    mul_wide(0xD2511F53u, k, h1, n3);
+    const uint32_t n2 = h1 ^ P.A;
     // round 2, the n2-dependent half
-    uint32_t c0 = __umulhi(0xCD9E8D57u, n2) ^ P.C;
-    uint32_t c1 = 0xCD9E8D57u * n2;
+    uint32_t h2, c1;
+    mul_wide(0xCD9E8D57u, n2, h2, c1);
+    uint32_t c0 = h2 ^ P.C;
     uint32_t c2 = P.B ^ n3;
     uint32_t c3 = P.x3;
     k0 += 2u * 0x9E3779B9u;
@@ -85,8 +101,9 @@ __device__ __forceinline__ void philox_finish(uint32_t k, const PhiloxPrefix &P,
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(0xD2511F53u, c0, hi0, lo0);
+        mul_wide(0xCD9E8D57u, c2, hi1, lo1);
         const uint32_t n0 = hi1 ^ c1 ^ k0, nn2 = hi0 ^ c3 ^ k1;
         c0 = n0;
         c1 = lo1;

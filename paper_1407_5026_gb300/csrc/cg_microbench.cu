@@ -6,9 +6,14 @@
 //   kind 1  aggregate binary64 add rate (adds/s), which bounds the binary64
 //           eps update (two adds per site and hop);
 //   kind 2  aggregate shared-memory bandwidth (bytes/s) of the same stream with
-//           64-bit words (the binary64 eps update's pattern).
+//           64-bit words (the binary64 eps update's pattern);
+//   kind 3  aggregate Philox-4x32-10 rate (blocks/s) of the PR kernels' own
+//           label generator (per-round prefix + per-label finish, two labels
+//           per thread, 2 x 512 threads per SM), the ceiling of the rejection
+//           phase: every evaluated label costs one block.
 #include <cuda_runtime.h>
 
+#include "cg_device.cuh"
 #include "cg_internal.h"
 
 namespace cg {
@@ -45,6 +50,25 @@ __global__ void __launch_bounds__(256) dadd_kernel(int iters, double seed, doubl
     }
     const double s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
     if (s == -1.0) sink[0] = s;
+}
+
+// Labels k of rounds r = it / 4 under the CTA's key, counter (k, r, 0, CTA):
+// the blocks of every thread are XOR-folded into one word per CTA.
+__global__ void __launch_bounds__(512, 2) philox_rate_kernel(int iters, uint32_t *sink)
+{
+    const uint32_t key0 = 0x9E3779B9u * (blockIdx.x + 1), key1 = 0x85EBCA6Bu ^ blockIdx.x;
+    uint32_t acc = 0;
+    for (int it = 0; it < iters; ++it) {
+        const PhiloxPrefix P = philox_prefix((uint32_t)(it >> 2), 0u, blockIdx.x, key0, key1);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            uint32_t x[4];
+            philox_finish((uint32_t)((it & 3) * 1024 + u * 512 + threadIdx.x), P, key0, key1, x);
+            acc ^= x[0] ^ x[1] ^ x[2] ^ x[3];
+        }
+    }
+    acc = __reduce_xor_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0) atomicXor(&sink[blockIdx.x & 15], acc);
 }
 
 static double time_ms(cudaEvent_t a, cudaEvent_t b)
@@ -100,6 +124,17 @@ int microbench(int kind, int device, double *result)
             err = cudaEventSynchronize(e1);
             const double adds = 8.0 * iters * 256.0 * blocks;
             const double rate = adds / (time_ms(e0, e1) * 1e-3);
+            if (rep > 0 && rate > best) best = rate;
+        }
+    } else if (kind == 3) {
+        const int iters = 2048, blocks = 2 * sms;
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            cudaEventRecord(e0);
+            philox_rate_kernel<<<blocks, 512>>>(iters, (uint32_t *)sink);
+            cudaEventRecord(e1);
+            err = cudaEventSynchronize(e1);
+            const double labels = 2.0 * iters * 512.0 * blocks;
+            const double rate = labels / (time_ms(e0, e1) * 1e-3);
             if (rep > 0 && rate > best) best = rate;
         }
     } else {

@@ -156,6 +156,17 @@ __device__ __forceinline__ Prop propose(const Shared &S, unsigned k, const Philo
     return p;
 }
 
+// Binary32 Metropolis bound of the binary32 form: e^(-dH/T) 2^23 - 1/2, with
+// e^(-dH/T) = 2^(dH c), c = -log2(e)/T folded into one constant (the
+// multiply by it is loop-invariant), from the hardware's approximate 2^x.
+__device__ __forceinline__ float metropolis_bound_f32(float dE, float invTf)
+{
+    const float c = -invTf * 1.44269504088896341f;
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(dE * c));
+    return __fmaf_rn(e, 0x1p23f, -0.5f);
+}
+
 // Step 2 (accept test) for a proposal whose theta holds, from the two local
 // energies (read from this CTA's shared memory or a cluster peer's).
 template <typename Real>
@@ -209,7 +220,7 @@ __device__ __forceinline__ bool accept_vals<float>(float ei, float ej, const Sha
     if (dEf <= 0.0f) return true;
     // u = (m + 1/2) 2^-23 with m = x2 >> 9 (exact in binary32); u < e^(-dH/T)
     // tested as m < e 2^23 - 1/2
-    return (float)(p.x2 >> 9) < __fmaf_rn(__expf(-dEf * invTf), 0x1p23f, -0.5f);
+    return (float)(p.x2 >> 9) < metropolis_bound_f32(dEf, invTf);
 }
 
 // Step 2 for the two labels of a thread in the binary32 form, without a
@@ -224,8 +235,8 @@ __device__ __forceinline__ void accept2_f32(const Shared &S, const Prop &p0, con
     const float *eps = reinterpret_cast<const float *>(S.eps);
     const float d0 = __fsub_rn(__fsub_rn(eps[p0.j], eps[p0.i]), S.cv32[p0.v]);
     const float d1 = __fsub_rn(__fsub_rn(eps[p1.j], eps[p1.i]), S.cv32[p1.v]);
-    const float t0 = __fmaf_rn(__expf(-d0 * invTf), 0x1p23f, -0.5f);
-    const float t1 = __fmaf_rn(__expf(-d1 * invTf), 0x1p23f, -0.5f);
+    const float t0 = metropolis_bound_f32(d0, invTf);
+    const float t1 = metropolis_bound_f32(d1, invTf);
     acc0 = p0.theta && (d0 <= 0.0f || (float)(p0.x2 >> 9) < t0);
     acc1 = p1.theta && (d1 <= 0.0f || (float)(p1.x2 >> 9) < t1);
     dE0 = 0.0;
@@ -496,6 +507,17 @@ __device__ __forceinline__ double hop_dE(const Shared &S, const Prop &p, double 
 {
     const Real *eps = reinterpret_cast<const Real *>(S.eps);
     return hop_dE_vals<Real>(eps[p.i], eps[p.j], S, p, dE);
+}
+
+// dH of an accepting label in binary64, redone for the executed hop from its
+// proposal: the value the accept test computed (binary64 form; binary32 near
+// ties) or the binary32 dH widened.
+template <typename Real>
+__device__ __forceinline__ double winner_dE(const Shared &S, const Prop &p, double T, float invTf)
+{
+    double dE = 0.0;
+    accept<Real>(S, p, T, invTf, dE);
+    return hop_dE<Real>(S, p, dE);
 }
 
 }  // namespace cg

@@ -51,6 +51,9 @@ namespace cg {
 // kPair: two-electron hops (square lattice): labels whose fourth Philox word
 // is below Rg.pair_T propose a pair move (pair_extend); an executed pair
 // applies the two single-hop eps updates in turn.
+// 2 b of the chunk rule C ~ sqrt(2 m b) (b: a chunk's fixed cost in labels)
+constexpr float kChunkCost = 128.0f;
+
 template <typename Real, int kThreads, int kLog2L, bool kTime, int kDim = 2, bool kPair = false>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
@@ -161,21 +164,28 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             }
         }
         if (tid == 0) s_c.t0 = clock64();
-        // labels per chunk ~ sqrt(2 m b) for m expected labels and a barrier
-        // worth b ~ 64 labels: two per thread (C = 2 blockDim) when that
+        // labels per chunk ~ sqrt(2 m b) for m expected labels and a chunk's
+        // fixed cost (the OR barrier and the warps' imbalance before it) worth
+        // b labels: nl = 4 or 2 labels per thread (C = nl blockDim) when that
         // exceeds blockDim, else one per thread for the first C threads (C a
         // power of two >= 64); m_ema is identical in every thread, so the
-        // choice is uniform and idle warps skip the labels whole
-        const float want = sqrtf(128.0f * s_c.m_ema);
-        unsigned C;
-        if (want > (float)kThreads) {
+        // choice is uniform and idle warps skip the labels whole.  Pair
+        // instances take at most two labels per thread.
+        const float want = sqrtf(kChunkCost * s_c.m_ema);
+        unsigned C, nl;
+        if (!kPair && want > 2.0f * (float)kThreads) {
+            nl = 4;
+            C = 4u * kThreads;
+        } else if (want > (float)kThreads) {
+            nl = 2;
             C = 2u * kThreads;
         } else {
+            nl = 1;
             C = 64;
             while (C < (unsigned)kThreads && (float)C < want) C <<= 1;
             if (C > (unsigned)kThreads) C = kThreads;
         }
-        const bool two = C > (unsigned)kThreads;
+        const bool two = nl > 1;
         const bool act = (unsigned)tid < C;
         unsigned long long p = 0;
         unsigned q = 0, win = 0, kb_hit = 0;
@@ -188,6 +198,75 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
             if (kPair)
                 PP2 = philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32) | 0x80000000u, rep,
                                     key0, key1);
+            if constexpr (!kPair) {
+            for (unsigned kb = 0; kb < M; kb += C) {
+                // bit u of accm: label kb + u blockDim + tid accepts; only the
+                // decisions stay live, the winning lane redoes its proposal
+                unsigned accm = 0;
+                if (act) {
+#pragma unroll
+                    for (unsigned u = 0; u < 4; u += 2) {
+                        if (u < nl) {
+                            const unsigned ka = kb + u * (unsigned)kThreads + (unsigned)tid;
+                            const unsigned kc = ka + (unsigned)kThreads;
+                            const bool hasc = u + 1 < nl;
+                            const bool va = ka < M, vc = hasc && kc < M;
+                            const Prop pa = propose<kPow2, kDim>(S, ka, PP, key0, key1, L, log2L,
+                                                                 (unsigned)N, magic, thr_last, va);
+                            Prop pc{};
+                            if (hasc)
+                                pc = propose<kPow2, kDim>(S, kc, PP, key0, key1, L, log2L,
+                                                          (unsigned)N, magic, thr_last, vc);
+                            bool aa = false, ac = false;
+                            double da = 0.0, dc = 0.0;
+                            if (a.toy) {
+                                aa = va && d_mul(d_add((double)pa.x2, 0.5), 0x1p-32) < a.toy_A0;
+                                ac = vc && d_mul(d_add((double)pc.x2, 0.5), 0x1p-32) < a.toy_A0;
+                            } else if (sizeof(Real) == 4 && hasc) {
+                                accept2_f32(S, pa, pc, T, invTf, aa, ac, da, dc);
+                            } else {
+                                if (pa.theta) aa = accept<Real>(S, pa, T, invTf, da);
+                                if (pc.theta) ac = accept<Real>(S, pc, T, invTf, dc);
+                            }
+                            accm |= (aa ? 1u : 0u) << u;
+                            accm |= (ac ? 1u : 0u) << (u + 1);
+                        }
+                    }
+                }
+                const int any = __syncthreads_or(accm != 0u);
+                if (any) {
+                    // the warp's lowest accepting label: the first sub-chunk
+                    // u with an accept, then the lowest lane
+                    unsigned off = 0xffffffffu;
+                    for (unsigned u = 0; u < nl; ++u) {
+                        const unsigned bu = __ballot_sync(0xffffffffu, (accm >> u) & 1u);
+                        if (bu) {
+                            off = u * (unsigned)kThreads + (unsigned)(warp * 32) +
+                                  (unsigned)(__ffs(bu) - 1);
+                            break;
+                        }
+                    }
+                    if (off != 0xffffffffu && (unsigned)lane == (off & 31u)) {
+                        const Prop pw = propose<kPow2, kDim>(S, kb + off, PP, key0, key1, L, log2L,
+                                                             (unsigned)N, magic, thr_last, true);
+                        s_cand[warp].i = pw.i;
+                        s_cand[warp].j = pw.j;
+                        s_cand[warp].dxy = pw.dxy;
+                        s_cand[warp].dE = a.toy ? 0.0 : winner_dE<Real>(S, pw, T, invTf);
+                    }
+                    if (lane == 0) s_wlabel[warp] = off;
+                    __syncthreads();
+                    unsigned wl = (lane < kThreads / 32) ? s_wlabel[lane] : 0xffffffffu;
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) wl = min(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+                    q = kb + wl + 1;                 // 1-based label in the round
+                    kb_hit = kb;
+                    win = (wl % (unsigned)kThreads) >> 5;
+                    found = true;
+                    break;
+                }
+            }
+            } else {
             for (unsigned kb = 0; kb < M; kb += C) {
                 const unsigned k0 = kb + (unsigned)tid, k1 = k0 + (unsigned)kThreads;
                 const bool v0 = k0 < M, v1 = two && k1 < M;
@@ -282,6 +361,7 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
                     found = true;
                     break;
                 }
+            }
             }
             if (!found) {
                 if (tid == 0) {
