@@ -253,9 +253,18 @@ int cg_sync(cg_handle *h);
  * R * n_hops entries, replica-major. */
 int cg_run_logged(cg_handle *h, uint64_t n_hops, uint32_t M, cg_hop *log_host);
 
-/* Copy one replica's state to host buffers (NULL pointers are skipped):
- * n_host N bytes (0/1), eps_host N doubles (FP32 eps widened), phi_host N
- * doubles, c_host the counters. */
+/* Copy one replica's state to host buffers (NULL pointers are skipped): the
+ * configuration and local energies of the mixed PR algorithm (section
+ * "Hopping conduction in the Coulomb glass": occupations n_i, the site
+ * energies phi_i of Eq. 1 and eps_i = phi_i + sum_j (n_j - nu)/r_ij below
+ * Eq. 2) and the counters of step 3.
+ *   n_host    N bytes (0/1)
+ *   eps_host  N doubles (FP32 eps widened exactly)
+ *   phi_host  N doubles
+ *   c_host    the counters (rounds, hops, attempts (p-1)M + q summed over
+ *             hops, P of Eq. 3, the running energy of Eq. 1)
+ * Waits for the handle's queued work first.  CG_EINVAL for a null handle or
+ * a replica out of range, CG_ECUDA on a CUDA error. */
 int cg_read_state(cg_handle *h, int replica, uint8_t *n_host, double *eps_host,
                   double *phi_host, cg_counters *c_host);
 
@@ -268,14 +277,31 @@ int cg_write_state(cg_handle *h, int replica, const uint8_t *n_host,
                    const double *eps_host, const double *phi_host,
                    const cg_counters *c_host);
 
+/* Observables of one replica (cg_obs): its counters, the time t = attempts /
+ * Gamma of the deterministic clock (the rule behind the paper's Fig. 3) or
+ * the stochastic clock of step 3c, Gamma = N sum_d exp(-2|d|/xi) of the mixed
+ * algorithm, the acceptance hops / attempts (the A of the section "Parallel
+ * rejection algorithm"), the energy per site of Eq. 1, the last refresh's
+ * eps error and the kernels' phase clocks.  Waits for the handle's queued
+ * work first.  CG_EINVAL for a null handle or output or a replica out of
+ * range, CG_ECUDA on a CUDA error. */
 int cg_observables(cg_handle *h, int replica, cg_obs *out);
 
 /* Rebuild eps of every replica from scratch now, from its definition below
  * Eq. 2: eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st.  CG_FP64 handles
  * recompute it in the serial summation order (bit-identical to a fresh
- * start); CG_FP32 handles recompute it in binary64, record the largest
- * |eps_fp32 - eps_new| (cg_obs.max_eps_err_last_refresh) and store eps_new
- * rounded to binary32.  Blocks until done. */
+ * start).  CG_FP32 handles record the largest |eps_fp32 - eps_new|
+ * (cg_obs.max_eps_err_last_refresh) and store eps_new rounded to binary32,
+ * where eps_new comes from one of two paths:
+ *   - a group of replicas of one L whose N is a multiple of 128 (and
+ *     CG_REFRESH_AUTO or CG_REFRESH_BF16X2): the tensor-core contraction, the
+ *     1/r table split into two BF16 terms (binary16 terms of 2^10/r on the
+ *     cubic lattice), the +-1 occupations exact in that format, products
+ *     accumulated in binary32 by the tensor cores over K ranges of at most
+ *     2048 sites and the partial sums and phi added in binary64 (error below
+ *     5e-5 at L <= 128, measured against the definition);
+ *   - otherwise (or CG_REFRESH_FP64): a direct sum in binary64.
+ * Blocks until done. */
 int cg_refresh(cg_handle *h);
 
 /* cg_refresh queued on the handle's stream without waiting (cg_sync waits). */
@@ -302,11 +328,17 @@ int cg_refresh_async(cg_handle *h);
  *   stream   cudaStream_t to run on (NULL: the legacy default stream)
  * All pointers are owned by the caller.  The call allocates nothing: its
  * scratch is one static device array of 32 MiB that every GPU loading the
- * library holds until the process exits; sizes that need more scratch
- * (noalloc bytes ~ 2 N R_pad + 32 N R_pad + small tables, R_pad = R rounded
- * up to 16) return CG_EINVAL with the limit in the message.  The first call
- * on a device looks up the array's device address (once per device) and
- * should come before any stream capture.  Every call shares the array and
+ * library holds until the process exits.  A call needs (2 + 4 k) N R_pad
+ * bytes of it for the contraction (R_pad = R rounded up to a multiple of 16,
+ * k the K split: 8 at L = 32, 64, 96 and 128, 10 at L = 160, 11 at L = 176)
+ * plus 352 bytes per replica and the split 1/r table, each part rounded up
+ * to 256 bytes.  The largest accepted R is 512 up to L = 48, 240 at L = 64,
+ * 224 at L = 80, 96 at L = 96, 80 at L = 112, 48 at L = 128, 32 at L = 144
+ * and 16 at L = 160 and 176; every L from 192 up needs more than 32 MiB even
+ * for R = 1.  Larger requests return CG_EINVAL with the limit in the
+ * message.  The first call on a device (and again after the device's context
+ * changed, e.g. after cudaDeviceReset) looks up the array's device address
+ * and should come before any stream capture.  Every call shares the array and
  * leaves its contents behind: calls that overlap on the GPU (other streams,
  * other host threads, same device) race and must be serialised by the
  * caller.  The call waits for its stream before returning.
@@ -320,7 +352,12 @@ int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int *occ,
  *   kind 0: shared-memory read-modify-write bandwidth of 32-bit words, bytes/s
  *   kind 1: binary64 add throughput, adds/s
  *   kind 2: shared-memory read-modify-write bandwidth of 64-bit words, bytes/s
- * summed over all SMs; result written to *result. */
+ *   kind 3: Philox-4x32-10 blocks/s of the PR kernels' label generator (the
+ *           ceiling of the rejection phase: one block per evaluated label;
+ *           section "Parallel rejection algorithm", 3M random numbers per
+ *           round on the GPU)
+ * summed over all SMs; result written to *result.  CG_EINVAL for another
+ * kind, CG_ECUDA on a CUDA error. */
 int cg_microbench(int kind, int device, double *result);
 
 /* Log-spaced trace of the dipole moment P and the energy, from which the
@@ -338,14 +375,19 @@ int cg_set_trace(cg_handle *h, double first_time, double points_per_decade, int 
 int cg_read_trace(cg_handle *h, int replica, cg_trace_point *out_host, int cap);
 
 /* Launch-shape autotuner.  The parallel-rejection section recommends M near
- * 1/A but larger than the number of concurrent threads; the best M and CTA
- * size depend on the GPU, so for every group of replicas with one L this
- * times the persistent launch for CTA sizes 256, 512, 1024 (those that fit)
- * and M in {1024, 4096, 16384} over hops_per_trial hops (0: 256) on a copy of
- * the group's state, restores the state bit for bit, and keeps the fastest
- * (cg_run with M = 0 then uses it).  With $CG_TUNE_CACHE naming a JSON file,
- * cached shapes are reused and new ones added.  Allocates a temporary device
- * snapshot; captured graphs are dropped. */
+ * 1/A but larger than the number of concurrent threads; the best M and launch
+ * shape depend on the GPU, so for every group of replicas with one L this
+ * times the persistent launch for every cluster size (CTAs per replica: 1
+ * when eps fits one CTA, and each of 2, 4, 8 that divides L and fits; only
+ * the forced size when cg_opts.cluster_size was set, only 1 for random-site
+ * replicas), CTA sizes 256, 384, 512, 1024 (those the kernel takes) and M in
+ * {1024, 4096, 16384, 65536}, over hops_per_trial hops (0: 256) on a copy of the
+ * group's state.  A trial counts only when every replica of the group
+ * completed its hops.  The state is restored bit for bit after each trial
+ * and the fastest shape is kept (cg_run with M = 0 then uses its M).  With
+ * $CG_TUNE_CACHE naming a JSON file, cached shapes are reused and new ones
+ * added.  Allocates a temporary device snapshot; captured graphs are
+ * dropped. */
 int cg_autotune(cg_handle *h, uint32_t hops_per_trial);
 
 /* Groups of replicas sharing one L (one persistent launch each). */

@@ -375,6 +375,12 @@ int check_desc(const cg_replica_desc &d)
     if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(CG_EINVAL, "T must be > 0");
     if (!(d.W >= 0.0) || !std::isfinite(d.W)) return fail(CG_EINVAL, "W must be >= 0");
     if (!std::isfinite(d.E)) return fail(CG_EINVAL, "E must be finite");
+    // random sites keep eps (binary64) and the bitmask in one CTA's shared
+    // memory (227 KiB opt-in on sm_100-class GPUs, 2 KiB left for the
+    // kernel's static part): refuse before the O(N^2) geometry is built
+    if (d.sites == CG_SITES_RANDOM && random_smem_bytes((int)N) > 227 * 1024 - 2048)
+        return fail(CG_EINVAL, "random-site replicas need eps of N <= 28224 sites (L <= 168) "
+                               "in one CTA's shared memory");
     return CG_OK;
 }
 
@@ -1233,6 +1239,10 @@ cg_handle *cg_create_batch(int R, const cg_replica_desc *reps, const cg_opts *op
 size_t cg_workspace_bytes(int R, const cg_replica_desc *reps, const cg_opts *opts)
 {
     if (R <= 0 || !reps) return 0;
+    // invalid descriptors (a random-site replica too large for a CTA among
+    // them) give 0 before any geometry is built
+    for (int k = 0; k < R; ++k)
+        if (check_desc(reps[k]) != CG_OK) return 0;
     cg_opts o{};
     if (opts) o = *opts;
     return plan_bytes(R, reps, o);
@@ -1502,9 +1512,10 @@ int cg_refresh(cg_handle *h)
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: per lattice-size group, time the persistent launch for each CTA
-// size and M on a copy of the state, keep the fastest.  Results are cached in
-// the JSON file named by $CG_TUNE_CACHE (flat map key -> {"threads", "M"}).
+// Autotuner: per lattice-size group, time the persistent launch for each
+// cluster size (CTAs per replica), CTA size and M on a copy of the state, keep
+// the fastest.  Results are cached in the JSON file named by $CG_TUNE_CACHE
+// (flat map key -> {"threads", "M", "cluster"}).
 // ---------------------------------------------------------------------------
 
 static std::string tune_key(const cg_handle *h, const Group &g)
@@ -1513,24 +1524,57 @@ static std::string tune_key(const cg_handle *h, const Group &g)
     cudaGetDeviceProperties(&prop, h->device);
     const Rep &r = h->reps[h->order[g.first]];
     char buf[512];
-    std::snprintf(buf, sizeof(buf), "%s|L=%d|prec=%s|cluster=%d|rmax=%d|T=%.6g|R=%d", prop.name,
-                  g.L, h->opts.precision == CG_FP64 ? "fp64" : "fp32", g.cluster, r.d.r_max,
-                  r.d.T, g.count);
+    // a forced cluster size is part of the key; otherwise the tuner picks it
+    char cl[16];
+    if (h->opts.cluster_size > 1)
+        std::snprintf(cl, sizeof(cl), "%d", h->opts.cluster_size);
+    else
+        std::snprintf(cl, sizeof(cl), "auto");
+    std::snprintf(buf, sizeof(buf), "%s|L=%d|dim=%d|prec=%s|cluster=%s|rmax=%d|T=%.6g|R=%d|pair=%.6g",
+                  prop.name, g.L, g.dim, h->opts.precision == CG_FP64 ? "fp64" : "fp32", cl,
+                  r.d.r_max, r.d.T, g.count, h->opts.pair_frac);
     return std::string(buf);
 }
 
 static bool tune_cache_lookup(const std::string &text, const std::string &key, int *threads,
-                              unsigned *M)
+                              unsigned *M, int *cluster)
 {
     const std::string pat = "\"" + key + "\": {\"threads\": ";
     const size_t p = text.find(pat);
     if (p == std::string::npos) return false;
-    int t = 0;
+    int t = 0, c = 0;
     unsigned m = 0;
-    if (std::sscanf(text.c_str() + p + pat.size(), "%d, \"M\": %u", &t, &m) != 2) return false;
+    if (std::sscanf(text.c_str() + p + pat.size(), "%d, \"M\": %u, \"cluster\": %d", &t, &m,
+                    &c) != 3)
+        return false;
     *threads = t;
     *M = m;
+    *cluster = c;
     return true;
+}
+
+// Cluster sizes a group can run with (CTAs per replica): the size chosen at
+// creation when the caller forced one or the group holds random-site
+// replicas; else 1 (when eps fits one CTA) and every 2, 4, 8 that divides L
+// and whose per-CTA shared memory fits, each with that shared-memory size.
+static std::vector<std::pair<int, int>> cluster_candidates(const cg_handle *h, const Group &g)
+{
+    std::vector<std::pair<int, int>> out;
+    if (g.random || h->opts.cluster_size > 1) {
+        out.push_back({g.cluster, g.smem});
+        return out;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    const int budget = optin - (h->opts.pair_frac > 0.0 ? 3072 : 2048);
+    for (int c = 1; c <= 8; c *= 2) {
+        if (c > 1 && (g.L % c != 0 || g.L < 16)) continue;
+        int sm = 0;
+        for (int k = 0; k < g.count; ++k)
+            sm = std::max(sm, persistent_smem(h->reps[h->order[g.first + k]], h->opts.precision, c));
+        if (sm <= budget) out.push_back({c, sm});
+    }
+    return out;
 }
 
 int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
@@ -1550,20 +1594,27 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
         }
     }
     const int rb = h->opts.precision == CG_FP64 ? 8 : 4;
-    std::vector<std::pair<std::string, std::pair<int, unsigned>>> found;
+    struct Shape { int threads; unsigned M; int cluster; };
+    std::vector<std::pair<std::string, Shape>> found;
     cudaEvent_t e0, e1;
     CG_CUDA(cudaEventCreate(&e0));
     CG_CUDA(cudaEventCreate(&e1));
     int rc = CG_OK;
     for (Group &g : h->groups) {
         const std::string key = tune_key(h, g);
-        int ct = 0;
+        const std::vector<std::pair<int, int>> cands = cluster_candidates(h, g);
+        int ct = 0, cc = 0;
         unsigned cM = 0;
-        if (tune_cache_lookup(cache, key, &ct, &cM)) {
-            g.threads = ct;
-            g.M = cM;
-            g.tuned = true;
-            continue;
+        if (tune_cache_lookup(cache, key, &ct, &cM, &cc)) {
+            for (const auto &c : cands)
+                if (c.first == cc) {
+                    g.cluster = cc;
+                    g.smem = c.second;
+                    g.threads = ct;
+                    g.M = cM;
+                    g.tuned = true;
+                }
+            if (g.tuned) continue;
         }
         // snapshot of the group's state (eps, bitmask, counters per replica)
         const Rep &r0 = h->reps[h->order[g.first]];
@@ -1595,34 +1646,53 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
         };
         cudaError_t ce = copy_group(true);
         double best = -1.0;
-        int best_t = g.threads;
+        int best_t = g.threads, best_c = g.cluster, best_smem = g.smem;
         unsigned best_M = g.M;
         const int shapes[4] = {256, 384, 512, 1024};
-        const unsigned Ms[3] = {1024, 4096, 16384};
-        for (int ti = 0; ti < 4 && ce == cudaSuccess; ++ti) {
-            const int t = shapes[ti];
-            if (t < g.L / 2 || (g.cluster > 1 && (t < 512 || t < g.L))) continue;
-            for (int mi = 0; mi < 3 && ce == cudaSuccess; ++mi) {
-                Group trial = g;
-                trial.threads = t;
-                cudaEventRecord(e0, h->st);
-                int lrc = launch_group(h, trial, hops_per_trial, Ms[mi], 0, h->st);
-                cudaEventRecord(e1, h->st);
-                ce = cudaStreamSynchronize(h->st);
-                if (lrc || ce != cudaSuccess) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                DevCounters c;
-                cudaMemcpy(&c, r0.d_ctr, sizeof(c), cudaMemcpyDeviceToHost);
-                const double rate = c.status == CG_OK && ms > 0.f
-                                        ? (double)g.count * hops_per_trial / (ms * 1e-3)
-                                        : 0.0;
-                if (rate > best) {
-                    best = rate;
-                    best_t = t;
-                    best_M = Ms[mi];
+        const unsigned Ms[4] = {1024, 4096, 16384, 65536};
+        std::vector<DevCounters> cs(g.count);
+        for (const auto &cand : cands) {
+            const int c = cand.first;
+            for (int ti = 0; ti < 4 && ce == cudaSuccess; ++ti) {
+                const int t = shapes[ti];
+                // the single-CTA update needs L/2 base columns (L on the cubic
+                // lattice); the cluster kernel maps a thread to a column and
+                // is built for 512 and 1024 threads
+                if (t < g.L / 2 || (g.dim == 3 && t < g.L)) continue;
+                if (c > 1 && (t < 512 || t < g.L)) continue;
+                if (g.random && c > 1) continue;
+                for (int mi = 0; mi < 4 && ce == cudaSuccess; ++mi) {
+                    Group trial = g;
+                    trial.threads = t;
+                    trial.cluster = c;
+                    trial.smem = cand.second;
+                    cudaEventRecord(e0, h->st);
+                    int lrc = launch_group(h, trial, hops_per_trial, Ms[mi], 0, h->st);
+                    cudaEventRecord(e1, h->st);
+                    ce = cudaStreamSynchronize(h->st);
+                    if (lrc || ce != cudaSuccess) break;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    // a trial counts only when every replica of the group
+                    // completed its hops (none stuck or past its time limit)
+                    bool ok = ms > 0.f;
+                    for (int k = 0; k < g.count && ok; ++k) {
+                        const Rep &r = h->reps[h->order[g.first + k]];
+                        ce = cudaMemcpy(&cs[k], r.d_ctr, sizeof(DevCounters),
+                                        cudaMemcpyDeviceToHost);
+                        ok = ce == cudaSuccess && cs[k].status == CG_OK;
+                    }
+                    if (ce != cudaSuccess) break;
+                    const double rate = ok ? (double)g.count * hops_per_trial / (ms * 1e-3) : 0.0;
+                    if (rate > best) {
+                        best = rate;
+                        best_t = t;
+                        best_M = Ms[mi];
+                        best_c = c;
+                        best_smem = cand.second;
+                    }
+                    ce = copy_group(false);   // restore: tuning leaves the chains untouched
                 }
-                ce = copy_group(false);   // restore: tuning leaves the chains untouched
             }
         }
         cudaFree(snap);
@@ -1632,8 +1702,10 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
         }
         g.threads = best_t;
         g.M = best_M;
+        g.cluster = best_c;
+        g.smem = best_smem;
         g.tuned = true;
-        found.push_back({key, {best_t, best_M}});
+        found.push_back({key, {best_t, best_M, best_c}});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1653,8 +1725,9 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
             bool first = body.find('"') == std::string::npos;
             if (!first) std::fprintf(f, "%s", body.c_str());
             for (auto &e : found) {
-                std::fprintf(f, "%s\n  \"%s\": {\"threads\": %d, \"M\": %u}", first ? "" : ",",
-                             e.first.c_str(), e.second.first, e.second.second);
+                std::fprintf(f, "%s\n  \"%s\": {\"threads\": %d, \"M\": %u, \"cluster\": %d}",
+                             first ? "" : ",", e.first.c_str(), e.second.threads, e.second.M,
+                             e.second.cluster);
                 first = false;
             }
             std::fprintf(f, "\n}\n");
@@ -1745,7 +1818,7 @@ int cg_refresh_async(cg_handle *h)
 
 int cg_microbench(int kind, int device, double *result)
 {
-    if (!result || kind < 0 || kind > 2) return fail(CG_EINVAL, "bad microbenchmark kind");
+    if (!result || kind < 0 || kind > 3) return fail(CG_EINVAL, "bad microbenchmark kind");
     int rc = microbench(kind, device, result);
     if (rc) return fail(rc, "microbenchmark failed");
     return CG_OK;

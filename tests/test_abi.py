@@ -188,6 +188,22 @@ def test_random_site_descriptor_checks_on_host(libcg, kw, msg):
     assert msg in str(ei.value)
 
 
+def test_random_sites_too_large_for_a_cta_are_refused_at_once(libcg):
+    # eps of a random-site replica lives in one CTA's shared memory; L = 1024
+    # (N = 2^20) is refused by the descriptor check, before the O(N^2) site
+    # geometry would be built
+    import time
+    from paper_1407_5026_gb300 import binding as B
+    big = [B.desc(L=1024, r_max=6, sites=B.CG_SITES_RANDOM)]
+    t0 = time.perf_counter()
+    with pytest.raises(B.CgError) as ei:
+        B.cg_create_batch(big, B.opts())
+    assert "L <= 168" in str(ei.value)
+    assert B.cg_workspace_bytes(big, B.opts()) == 0
+    assert "L <= 168" in B.cg_last_error()
+    assert time.perf_counter() - t0 < 5.0
+
+
 def test_workspace_plan_counts_the_random_site_geometry(libcg):
     # a random-site replica adds its positions (2 N doubles), the N x N
     # coupling matrix, a 64-byte guide record per site and per pair two
