@@ -71,39 +71,41 @@ def relaxation_curves(B, device=0, temperatures=(0.02, 0.05, 0.1), seeds=range(8
                       hops=1_000_000, M=4096, precision=None, points_per_decade=4.0,
                       first_time=1.0, plateau_decades=1.0):
     """sigma(t) of the L = 64 relaxation configuration (nu = 1/2, W = 1, xi = 1,
-    r_max = 6, E = 0.01 along x) from the random start, one batch of disorder
-    seeds per temperature, and its Eq. 4 rescaling.  sigma_0 per T is the
-    plateau slope over the last `plateau_decades` decades of the run's time.
-    Returns per T: the window midpoints, the replica-mean sigma, sigma_0, the
-    acceptance, and the rescaled (x, y) = (t sigma_0 T^2, sigma / sigma_0)."""
+    r_max = 6, E = 0.01 along x) from the random start: every (temperature,
+    disorder seed) chain in one handle (one persistent launch), the disorder
+    of seed s the same at every T.  Per T: the replica-mean trace, its Eq. 3
+    windows, sigma_0 as the slope of P over the last `plateau_decades`
+    decades of the run's time, the acceptance, and the Eq. 4 variables
+    (x, y) = (t sigma_0 T^2, sigma / sigma_0)."""
     from paper_1407_5026_gb300 import workloads as W
     prec = B.CG_FP64 if precision is None else precision
+    seeds = list(seeds)
+    base = W.l64_fp64(T=temperatures[0], seed=0, hops=hops).replicas[0].as_dict()
+    reps = [dict(base, T=T, seed=s, replica=s) for T in temperatures for s in seeds]
+    s = B.System(reps, precision=prec, refresh_every=1024 if prec == B.CG_FP32 else 0,
+                 device=device)
+    try:
+        cap = 256
+        B.cg_set_trace(s.h, first_time=first_time, points_per_decade=points_per_decade,
+                       capacity=cap)
+        rc = s.run(hops, M)
+        assert rc == B.CG_OK, rc
+        tr = [B.cg_read_trace(s.h, k, cap) for k in range(len(reps))]
+        acc = [s.observables(k)["acceptance"] for k in range(len(reps))]
+    finally:
+        s.close()
+    N, E = base["L"] ** 2, base["E"]
     out = {}
-    for T in temperatures:
-        reps = [r.as_dict() for r in W.l64_fp64(T=T, seed=0, hops=hops).replicas]
-        base = reps[0]
-        reps = [dict(base, seed=s, replica=s) for s in seeds]
-        s = B.System(reps, precision=prec,
-                     refresh_every=1024 if prec == B.CG_FP32 else 0, device=device)
-        try:
-            cap = 256
-            B.cg_set_trace(s.h, first_time=first_time, points_per_decade=points_per_decade,
-                           capacity=cap)
-            rc = s.run(hops, M)
-            assert rc == B.CG_OK, rc
-            tr = [B.cg_read_trace(s.h, k, cap) for k in range(len(reps))]
-            acc = float(np.mean([s.observables(k)["acceptance"] for k in range(len(reps))]))
-        finally:
-            s.close()
-        N, E = base["L"] ** 2, base["E"]
-        m = mean_trace(tr)
+    for ti, T in enumerate(temperatures):
+        sl = slice(ti * len(seeds), (ti + 1) * len(seeds))
+        m = mean_trace(tr[sl])
         t_mid, sig = sigma_windows(m, N, E)
         t_end = float(m["time"][-1])
         s0 = sigma0_plateau(m, N, E, t_end / 10 ** plateau_decades)
         x, y = rescale(t_mid, sig, s0, T)
         out[T] = {"t": t_mid.tolist(), "sigma": sig.tolist(), "sigma0": s0,
-                  "t_end": t_end, "acceptance": acc, "replicas": len(reps), "hops": hops,
-                  "x": x.tolist(), "y": y.tolist()}
+                  "t_end": t_end, "acceptance": float(np.mean(acc[sl])),
+                  "replicas": len(seeds), "hops": hops, "x": x.tolist(), "y": y.tolist()}
     return out
 
 
