@@ -119,8 +119,11 @@ typedef struct {
                                    the replica fits its shared memory, else the
                                    smallest of 2, 4, 8 that fits); 2, 4 or 8
                                    force a thread-block cluster that splits
-                                   eps by rows (z-planes on the cubic
-                                   lattice)                                    */
+                                   eps by rows (CTA r of C holds the rows
+                                   [r L/2C, (r+1) L/2C) and the same rows
+                                   + L/2, so L must be a multiple of 2C) or
+                                   by z-planes on the cubic lattice (L a
+                                   multiple of C)                              */
     int32_t time_mode;          /* CG_TIME_DETERMINISTIC (0): t = attempts/Gamma;
                                    CG_TIME_GAUSSIAN: each executed hop adds a
                                    Gaussian dt of mean m/Gamma and standard

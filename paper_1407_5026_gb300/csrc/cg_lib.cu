@@ -407,6 +407,11 @@ int persistent_smem(const Rep &r, int precision, int cluster = 1)
     return smem_layout(r.N / cluster, (int)r.tab->t64.size(), r.tab->V, r.words, rb).total;
 }
 
+// L must be a multiple of this for a cluster of c CTAs: c on the cubic
+// lattice (whole z-planes per CTA), 2c on the square lattice (each CTA holds
+// L/(2c) base rows and their partner rows y + L/2).
+int cluster_rows_unit(const cg_replica_desc &d, int c) { return dim_of(d) == 3 ? c : 2 * c; }
+
 // CTAs per replica: 1 when the replica fits one CTA's shared memory, else the
 // smallest cluster of 2, 4 or 8 CTAs (each holding L/C rows of eps, or L/C
 // z-planes on the cubic lattice) that fits; a forced size is used when it
@@ -419,14 +424,15 @@ int choose_cluster(const cg_opts &o, const Rep &r, int optin)
     if (r.random) return (o.cluster_size <= 1 && persistent_smem(r, o.precision) <= budget) ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
-        if ((c == 2 || c == 4 || c == 8) && r.d.L % c == 0 && r.d.L >= 16 &&
+        if ((c == 2 || c == 4 || c == 8) && r.d.L % cluster_rows_unit(r.d, c) == 0 && r.d.L >= 16 &&
             persistent_smem(r, o.precision, c) <= budget)
             return c;
         return 0;
     }
     if (persistent_smem(r, o.precision, 1) <= budget) return 1;
     for (int c = 2; c <= 8; c *= 2)
-        if (r.d.L % c == 0 && persistent_smem(r, o.precision, c) <= budget) return c;
+        if (r.d.L % cluster_rows_unit(r.d, c) == 0 && persistent_smem(r, o.precision, c) <= budget)
+            return c;
     return 0;
 }
 
@@ -847,7 +853,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         if (choose_cluster(o, r, optin) == 0) {
             fail(CG_EINVAL, "replica does not fit the shared memory of one CTA or of a "
                             "cluster of up to 8 CTAs (or the forced cluster size does not "
-                            "fit / divide L)");
+                            "fit, or L is not a multiple of twice it on the square lattice)");
             destroy_partial();
             return nullptr;
         }
@@ -1568,7 +1574,7 @@ static std::vector<std::pair<int, int>> cluster_candidates(const cg_handle *h, c
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     const int budget = optin - (h->opts.pair_frac > 0.0 ? 3072 : 2048);
     for (int c = 1; c <= 8; c *= 2) {
-        if (c > 1 && (g.L % c != 0 || g.L < 16)) continue;
+        if (c > 1 && (g.L % (g.dim == 3 ? c : 2 * c) != 0 || g.L < 16)) continue;
         int sm = 0;
         for (int k = 0; k < g.count; ++k)
             sm = std::max(sm, persistent_smem(h->reps[h->order[g.first + k]], h->opts.precision, c));

@@ -61,7 +61,10 @@ cudaError_t launch_pr_cluster(int precision, const DevReplica *d_reps, const int
                               int n_reps, int cluster, int threads, int smem_bytes,
                               const RunArgs &args, cudaStream_t st, int L, int dim)
 {
-    if (cluster < 2 || cluster > 8 || (L % cluster) != 0 || threads < L)
+    // square lattice: L/(2C) base rows and their partners per CTA; cubic
+    // lattice: L/C z-planes per CTA
+    if (cluster < 2 || cluster > 8 || (L % (dim == 3 ? cluster : 2 * cluster)) != 0 ||
+        threads < L)
         return cudaErrorInvalidValue;
     if (args.pair)
         return launch_pr_cluster_pair(precision, d_reps, d_index, n_reps, cluster, threads,

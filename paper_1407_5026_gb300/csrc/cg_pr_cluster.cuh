@@ -4,8 +4,12 @@
 //
 // Same chain as cg_pr_kernel.cu (mixed PR algorithm, steps 1-3); the work of
 // a replica is spread over the cluster:
-//   * CTA `rank` owns rows [rank L/C, (rank+1) L/C) of eps in its shared
-//     memory; the 1/r table, the occupation bitmask and the tower are
+//   * on the square lattice CTA `rank` owns the base rows
+//     [rank B, (rank+1) B), B = L/(2C), and their partner rows y + L/2 of eps
+//     in its shared memory (local row yl < B is base row rank B + yl, yl >= B
+//     the partner of base row rank B + yl - B), so each CTA updates its sites
+//     four at a time with one folded offset per axis, as the single-CTA
+//     kernel does; the 1/r table, the occupation bitmask and the tower are
 //     replicated in every CTA, and every CTA applies each executed hop to its
 //     bitmask copy;
 //   * a chunk of labels is split into C contiguous sub-ranges, CTA rank
@@ -43,21 +47,43 @@ struct Slot {
     Cand cand;
 };
 
+// Square lattice: the CTA that owns row y and the row's local index there
+// (base rows of B = L/(2C) per CTA, partner rows y + L/2 after them);
+// magicB = floor(2^32 / B) + 1 divides by B for y < L <= 1024.
+__device__ __forceinline__ void cluster_row_owner(int y, int Lh, int B, unsigned magicB,
+                                                  unsigned &owner, int &yl)
+{
+    const bool upper = y >= Lh;
+    const int yb = upper ? y - Lh : y;
+    owner = __umulhi((unsigned)yb, magicB);
+    yl = yb - (int)owner * B + (upper ? B : 0);
+}
+
+// Global row of local row yl of CTA rank (square lattice).
+__device__ __forceinline__ int cluster_global_row(int yl, unsigned rank, int Lh, int B)
+{
+    return yl < B ? (int)rank * B + yl : Lh + (int)rank * B + (yl - B);
+}
+
 // eps of site s, from the CTA that owns its row (square lattice) or z-plane
-// (cubic lattice).
+// (cubic lattice: CTA rank owns planes [rank L/C, (rank+1) L/C)).
 template <typename Real, int kDim>
 __device__ __forceinline__ Real cluster_eps(coop::cluster_group &cl, Real *local, unsigned s,
                                             int rows_local, int log2L, int L, unsigned magic,
-                                            bool pow2, unsigned rank)
+                                            bool pow2, unsigned rank, unsigned magicB)
 {
-    int slow;
-    if (kDim == 3)
-        slow = pow2 ? (int)(s >> (2 * log2L)) : (int)__umulhi(__umulhi(s, magic), magic);
-    else
-        slow = pow2 ? (int)(s >> log2L) : (int)__umulhi(s, magic);
-    const unsigned owner = (unsigned)(slow / rows_local);
-    const unsigned plane = kDim == 3 ? (unsigned)(L * L) : (unsigned)L;
-    const unsigned off = s - owner * (unsigned)rows_local * plane;
+    unsigned owner, off;
+    if (kDim == 3) {
+        const int z = pow2 ? (int)(s >> (2 * log2L)) : (int)__umulhi(__umulhi(s, magic), magic);
+        owner = (unsigned)(z / rows_local);
+        off = s - owner * (unsigned)rows_local * (unsigned)(L * L);
+    } else {
+        const int y = pow2 ? (int)(s >> log2L) : (int)__umulhi(s, magic);
+        const int x = (int)s - y * L;
+        int yl;
+        cluster_row_owner(y, L >> 1, rows_local >> 1, magicB, owner, yl);
+        off = (unsigned)(yl * L + x);
+    }
     if (owner == rank) return local[off];
     Real *peer = cl.map_shared_rank(local, owner);
     return peer[off];
@@ -99,6 +125,9 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int rows_local = L / (int)C, N_local = rows_local * plane;
     const int row0 = (int)rank * rows_local;
     const int log2L = __ffs(L) - 1;
+    // square lattice: base rows per CTA and the multiplier that divides by it
+    const int Bq = rows_local >> 1;
+    const unsigned magicB = kDim == 3 ? 0u : (unsigned)(4294967296ull / (unsigned)Bq + 1ull);
     const int ntab = kDim == 3 ? H1 * H1 * H1 : H1 * H1;
 
     const SmemLayout lay = smem_layout(N_local, ntab, V, words, (int)sizeof(Real));
@@ -117,8 +146,17 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
 
     // ---- stage: own rows of eps, full tables and bitmask ----
     {
-        const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps) + (size_t)row0 * plane;
-        for (int l = tid; l < N_local; l += kThreads) eps[l] = eps_g[l];
+        if (kDim == 3) {
+            const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps) + (size_t)row0 * plane;
+            for (int l = tid; l < N_local; l += kThreads) eps[l] = eps_g[l];
+        } else {
+            const Real *eps_g = reinterpret_cast<const Real *>(Rg.eps);
+            for (int l = tid; l < N_local; l += kThreads) {
+                const int yl = kPow2 ? (l >> log2L) : (int)__umulhi((unsigned)l, magic);
+                const int x = l - yl * L;
+                eps[l] = eps_g[(size_t)cluster_global_row(yl, rank, L >> 1, Bq) * L + x];
+            }
+        }
         const Real *tab_g = (sizeof(Real) == 8)
                                 ? reinterpret_cast<const Real *>(Rg.tinv64)
                                 : reinterpret_cast<const Real *>(Rg.tinv32);
@@ -159,6 +197,9 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int rows_per_pass = kThreads / L;
     const int active = rows_per_pass * L;
     const int ux = tid % L, uy0 = tid / L;
+    // square lattice update: base rows per pass and the threads that work
+    const int qrpp = kThreads / (L >> 1);
+    const int qactive = qrpp * (L >> 1);
 
     if (tid == 0) s_zbase = ~0ull;
     __syncthreads();
@@ -177,10 +218,12 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
             s_c.t0 = clock64();
             s_c.wall0 = globaltimer_ns();
         }
-        // cluster chunk: C sub-chunks of up to 2 * blockDim labels
+        // cluster chunk: C sub-chunks of up to 2 * blockDim labels, ~ sqrt(2 m b)
+        // labels in all for m expected labels and a chunk's fixed cost b (its
+        // two CTA barriers and the cluster barrier; ~1000 labels measured)
         unsigned sub = 64;
         {
-            const float want = sqrtf(128.0f * s_c.m_ema) / (float)C;
+            const float want = sqrtf(2048.0f * s_c.m_ema) / (float)C;
             while (sub < (unsigned)(2 * kThreads) && (float)sub < want) sub <<= 1;
         }
         const unsigned chunk = sub * C, half = sub >> 1;
@@ -202,33 +245,37 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 const unsigned base = kb + rank * sub;
                 const bool mine = (unsigned)tid < half;
                 const unsigned k0 = base + (unsigned)tid, k1 = k0 + half;
-                Prop p0 = propose<kPow2, kDim>(S, k0, PP, key0, key1, L, log2L, (unsigned)N, magic,
-                                               thr_last, mine && k0 < M);
-                Prop p1 = propose<kPow2, kDim>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
-                                               thr_last, mine && k1 < M);
+                Prop p0{}, p1{};
                 PairProp q0{}, q1{};
+                double dE0 = 0.0, dE1 = 0.0;
+                bool acc0 = false, acc1 = false;
+                Real ei0 = 0, ej0 = 0, ei1 = 0, ej1 = 0;
+                Real ek0 = 0, el0 = 0, ek1 = 0, el1 = 0;
+                // the threads past the CTA's sub-chunk (whole warps: half is a
+                // multiple of 32) skip the label work
+                if (mine) {
+                p0 = propose<kPow2, kDim>(S, k0, PP, key0, key1, L, log2L, (unsigned)N, magic,
+                                          thr_last, k0 < M);
+                p1 = propose<kPow2, kDim>(S, k1, PP, key0, key1, L, log2L, (unsigned)N, magic,
+                                          thr_last, k1 < M);
                 if (kPair && !a.toy) {
                     q0 = pair_extend<kPow2, kDim>(S, p0, k0, PP2, key0, key1, L, log2L, magic, thr_last,
                                             Rg.pair_T, Rg.pair_R);
                     q1 = pair_extend<kPow2, kDim>(S, p1, k1, PP2, key0, key1, L, log2L, magic, thr_last,
                                             Rg.pair_T, Rg.pair_R);
                 }
-                double dE0 = 0.0, dE1 = 0.0;
-                bool acc0 = false, acc1 = false;
-                Real ei0 = 0, ej0 = 0, ei1 = 0, ej1 = 0;
-                Real ek0 = 0, el0 = 0, ek1 = 0, el1 = 0;
                 if (a.toy) {
                     const double u0 = d_mul(d_add((double)p0.x2, 0.5), 0x1p-32);
                     const double u1 = d_mul(d_add((double)p1.x2, 0.5), 0x1p-32);
-                    acc0 = mine && k0 < M && u0 < a.toy_A0;
-                    acc1 = mine && k1 < M && u1 < a.toy_A0;
+                    acc0 = k0 < M && u0 < a.toy_A0;
+                    acc1 = k1 < M && u1 < a.toy_A0;
                 } else {
                     if (p0.theta) {
-                        ei0 = cluster_eps<Real, kDim>(cl, eps, p0.i, rows_local, log2L, L, magic, kPow2, rank);
-                        ej0 = cluster_eps<Real, kDim>(cl, eps, p0.j, rows_local, log2L, L, magic, kPow2, rank);
+                        ei0 = cluster_eps<Real, kDim>(cl, eps, p0.i, rows_local, log2L, L, magic, kPow2, rank, magicB);
+                        ej0 = cluster_eps<Real, kDim>(cl, eps, p0.j, rows_local, log2L, L, magic, kPow2, rank, magicB);
                         if (kPair && q0.pair) {
-                            ek0 = cluster_eps<Real, kDim>(cl, eps, q0.k, rows_local, log2L, L, magic, kPow2, rank);
-                            el0 = cluster_eps<Real, kDim>(cl, eps, q0.l, rows_local, log2L, L, magic, kPow2, rank);
+                            ek0 = cluster_eps<Real, kDim>(cl, eps, q0.k, rows_local, log2L, L, magic, kPow2, rank, magicB);
+                            el0 = cluster_eps<Real, kDim>(cl, eps, q0.l, rows_local, log2L, L, magic, kPow2, rank, magicB);
                             acc0 = accept_pair_vals<Real, kPow2, kDim>(ei0, ej0, ek0, el0, S, Rg, p0, q0, T,
                                                                  invTf, dE0, L, log2L, magic, H1);
                         } else {
@@ -236,17 +283,18 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                         }
                     }
                     if (p1.theta) {
-                        ei1 = cluster_eps<Real, kDim>(cl, eps, p1.i, rows_local, log2L, L, magic, kPow2, rank);
-                        ej1 = cluster_eps<Real, kDim>(cl, eps, p1.j, rows_local, log2L, L, magic, kPow2, rank);
+                        ei1 = cluster_eps<Real, kDim>(cl, eps, p1.i, rows_local, log2L, L, magic, kPow2, rank, magicB);
+                        ej1 = cluster_eps<Real, kDim>(cl, eps, p1.j, rows_local, log2L, L, magic, kPow2, rank, magicB);
                         if (kPair && q1.pair) {
-                            ek1 = cluster_eps<Real, kDim>(cl, eps, q1.k, rows_local, log2L, L, magic, kPow2, rank);
-                            el1 = cluster_eps<Real, kDim>(cl, eps, q1.l, rows_local, log2L, L, magic, kPow2, rank);
+                            ek1 = cluster_eps<Real, kDim>(cl, eps, q1.k, rows_local, log2L, L, magic, kPow2, rank, magicB);
+                            el1 = cluster_eps<Real, kDim>(cl, eps, q1.l, rows_local, log2L, L, magic, kPow2, rank, magicB);
                             acc1 = accept_pair_vals<Real, kPow2, kDim>(ei1, ej1, ek1, el1, S, Rg, p1, q1, T,
                                                                  invTf, dE1, L, log2L, magic, H1);
                         } else {
                             acc1 = accept_vals<Real>(ei1, ej1, S, p1, T, invTf, dE1);
                         }
                     }
+                }
                 }
                 const int any = __syncthreads_or(acc0 || acc1);
                 unsigned best = 0xffffffffu;
@@ -423,10 +471,16 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[oj], tinv[oi]));
             }
             }
-        } else if (!a.toy && tid < active) {
-            // an executed pair applies the second electron's update after the
-            // first one's (each site rounds twice, in the serial order)
+        } else if (kDim == 2 && !a.toy && tid < qactive) {
+            // thread -> base column bx < L/2 and base rows yb0, yb0 + qrpp, ...
+            // of this CTA; each base site (x, y) serves the four sites
+            // (x, y), (x + L/2, y), (x, y + L/2), (x + L/2, y + L/2) (local rows
+            // yb and yb + B): on an even ring fold(d + L/2) = L/2 - fold(d).
+            // An executed pair applies the second electron's update after the
+            // first one's (each site rounds twice, in the serial order).
             const int passes = cpair ? 2 : 1;
+            const int Lh = L >> 1;
+            const int bx = tid % Lh, yb0 = tid / Lh;
 #pragma unroll 1
             for (int pass = 0; pass < passes; ++pass) {
                 const unsigned ui = pass ? wpq.k : ci, uj = pass ? wpq.l : cj;
@@ -438,14 +492,35 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                     yi = (int)__umulhi(ui, magic); xi = (int)ui - yi * L;
                     yj = (int)__umulhi(uj, magic); xj = (int)uj - yj * L;
                 }
-                const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
-                const Real *colj = tinv + fxj, *coli = tinv + fxi;
-                for (int yl = uy0; yl < rows_local; yl += rows_per_pass) {
-                    const int y = row0 + yl;
-                    const int fyj = fold_axis(y - yj, L), fyi = fold_axis(y - yi, L);
-                    const Real ta = colj[fyj * H1], tb = coli[fyi * H1];
-                    Real *e = eps + yl * L + ux;
-                    *e = Prec<Real>::add(*e, Prec<Real>::sub(ta, tb));
+                const int fxj = fold_axis(bx - xj, L), fxi = fold_axis(bx - xi, L);
+                // columns of (x, .) and (x + L/2, .) relative to j and to i
+                const Real *cj0 = tinv + fxj, *cj1 = tinv + (Lh - fxj);
+                const Real *ci0 = tinv + fxi, *ci1 = tinv + (Lh - fxi);
+                const int LhH1 = Lh * H1, BL = Bq * L;
+                Real *e = eps + yb0 * L + bx;
+#pragma unroll 4
+                for (int yb = yb0; yb < Bq; yb += qrpp, e += qrpp * L) {
+                    const int y = (int)rank * Bq + yb;
+                    int fyj, fyi;
+                    if (kPow2) {
+                        const int dj = (y - yj) & (L - 1), di = (y - yi) & (L - 1);
+                        fyj = min(dj, L - dj);
+                        fyi = min(di, L - di);
+                    } else {
+                        fyj = fold_axis(y - yj, L);
+                        fyi = fold_axis(y - yi, L);
+                    }
+                    // rows fold(y - .) and L/2 - fold(y - .) = fold(y + L/2 - .)
+                    const int oj0 = fyj * H1, oj1 = LhH1 - oj0;
+                    const int oi0 = fyi * H1, oi1 = LhH1 - oi0;
+                    const Real a00 = cj0[oj0], b00 = ci0[oi0];
+                    const Real a10 = cj1[oj0], b10 = ci1[oi0];
+                    const Real a01 = cj0[oj1], b01 = ci0[oi1];
+                    const Real a11 = cj1[oj1], b11 = ci1[oi1];
+                    e[0] = Prec<Real>::add(e[0], Prec<Real>::sub(a00, b00));
+                    e[Lh] = Prec<Real>::add(e[Lh], Prec<Real>::sub(a10, b10));
+                    e[BL] = Prec<Real>::add(e[BL], Prec<Real>::sub(a01, b01));
+                    e[BL + Lh] = Prec<Real>::add(e[BL + Lh], Prec<Real>::sub(a11, b11));
                 }
             }
         }
@@ -455,8 +530,17 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
 
     // ---- store back: own rows of eps; rank 0 the bitmask and counters ----
     {
-        Real *eps_g = reinterpret_cast<Real *>(Rg.eps) + (size_t)row0 * plane;
-        for (int l = tid; l < N_local; l += kThreads) eps_g[l] = eps[l];
+        if (kDim == 3) {
+            Real *eps_g = reinterpret_cast<Real *>(Rg.eps) + (size_t)row0 * plane;
+            for (int l = tid; l < N_local; l += kThreads) eps_g[l] = eps[l];
+        } else {
+            Real *eps_g = reinterpret_cast<Real *>(Rg.eps);
+            for (int l = tid; l < N_local; l += kThreads) {
+                const int yl = kPow2 ? (l >> log2L) : (int)__umulhi((unsigned)l, magic);
+                const int x = l - yl * L;
+                eps_g[(size_t)cluster_global_row(yl, rank, L >> 1, Bq) * L + x] = eps[l];
+            }
+        }
         if (rank == 0)
             for (int l = tid; l < words; l += kThreads) Rg.occ[l] = S.occ[l];
     }
