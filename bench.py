@@ -79,6 +79,9 @@ def parse():
                          "and print its result as one JSON line")
     ap.add_argument("--sigma-hops", type=int, default=200_000,
                     help="hops per replica of the L=256 sigma(t) comparison (0 skips it)")
+    ap.add_argument("--sigma-l64-hops", type=int, default=1_000_000,
+                    help="hops per chain of the L=64 sigma(t) relaxation and its Eq. 4 "
+                         "rescaling (3 temperatures x 8 disorder seeds; 0 skips it)")
     ap.add_argument("--clocks-dir", default=None,
                     help="folder for the raw nvidia-smi clock samples (default: the temp folder)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -564,6 +567,12 @@ def run_ours(args):
         result["fp64_form"]["update_bound_dadd_per_hop"] = 2 * N
         result["fp64_form"]["dadd_peak_per_s"] = dadd_peak
         result["fp32_batched_over_fp64_form"] = result["value"] / result["fp64_form"]["hops_per_s"]
+        result["fp32_batched_over_fp64_batched"] = (result["value"]
+                                                    / result["fp64_batched"]["hops_per_s"])
+        result["fp64_cluster8"]["over_one_cta"] = (result["fp64_cluster8"]["hops_per_s"]
+                                                   / result["fp64_form"]["hops_per_s"])
+        result["fp64_cluster8"]["roofline"] = cluster_roofline(
+            replicas_for(rank, 1), result["fp64_cluster8"]["hops_per_s"], 8, smem_peak, sms, "fp64")
 
     # binary32 form (with its binary64 refresh) against the binary64 form on
     # the same disorder samples: paired differences of the observables
@@ -573,12 +582,17 @@ def run_ours(args):
     # the mixed-L batch and the cluster-sized lattice (not the headline
     # workload): throughput of their own launch paths
     if not args.no_other_configs and rank == 0:
-        result["other_configs"] = other_configs(args, B, local)
+        result["other_configs"] = other_configs(args, B, local, smem_peak=smem_peak, sms=sms)
 
     # sigma(t) relaxation at L=256: binary32 form against the binary64 form
     if args.sigma_hops > 0 and not args.no_other_configs and rank == 0:
         from paper_1407_5026_gb300 import sigma as S
         result["sigma_L256_fp32_vs_fp64"] = S.compare_forms_l256(B, local, args.sigma_hops)
+
+    # sigma(t) relaxation of the L=64 configuration at T = 0.02, 0.05, 0.1
+    # and its Eq. 4 scaling variables (the plateau sigma_0 per T)
+    if args.sigma_l64_hops > 0 and not args.no_other_configs and rank == 0:
+        result["sigma_L64_rescaling"] = sigma_l64_summary(B, local, args.sigma_l64_hops)
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, run one step, read the state back
@@ -663,7 +677,20 @@ def shape_of(B, h, g, tuned):
     return sh
 
 
-def other_configs(args, B, local, only=None):
+def cluster_roofline(reps, hops_per_s, cluster, smem_peak, sms, precision):
+    """The eps update's algorithmic shared-memory bytes per second (16 N B
+    per hop in binary32, 32 N in binary64) against the measured
+    shared-memory peak of the SMs the launch occupies (one CTA per SM)."""
+    N = reps[0]["L"] ** 2
+    per_hop = (16 if precision == "fp32" else 32) * N
+    used = min(sms, len(reps) * cluster)
+    peak = smem_peak * used / sms
+    achieved = hops_per_s * per_hop
+    return {"bound": "smem", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+            "frac": achieved / peak, "sms_used": used, "bytes_per_hop": per_hop}
+
+
+def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
     replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
@@ -681,7 +708,7 @@ def other_configs(args, B, local, only=None):
     out = {}
     for name, wl, relax, hops, graph, tune in (
             ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
-            ("L256_T0.02_R16_cluster", W.l256(), 8192, 8192, 0, True),
+            ("L256_T0.02_R16_cluster", W.l256(), 65536, 16384, 0, True),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
             ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
@@ -721,6 +748,10 @@ def other_configs(args, B, local, only=None):
                      # (the rest: label rounds), from the per-replica phase
                      # clocks over the timed hops
                      "update_cycle_share": update_share(o0, o1)}
+        cl = max(g["cluster"] for g in out[name]["groups"])
+        if cl > 1 and smem_peak and sms:
+            out[name]["roofline"] = cluster_roofline(reps, out[name]["hops_per_s"], cl,
+                                                     smem_peak, sms, wl.precision)
         if pair:
             out[name].update(pair)
             out[name]["pair_hops_share"] = pair_share(B, s, reps, wl.M)
@@ -732,6 +763,23 @@ def update_share(o0, o1):
     upd = sum(b["cycles_update"] - a["cycles_update"] for a, b in zip(o0, o1))
     rej = sum(b["cycles_reject"] - a["cycles_reject"] for a, b in zip(o0, o1))
     return round(upd / max(1, upd + rej), 4)
+
+
+def sigma_l64_summary(B, local, hops):
+    """sigma(t) of the L=64 relaxation configuration (8 disorder seeds per T)
+    and its Eq. 4 variables: per T the acceptance, sigma_0 (slope of P over
+    the last decade of time), the run's last time, tau = 1/(sigma_0 T^2) and
+    the windows (t, x = t sigma_0 T^2, y = sigma / sigma_0)."""
+    from paper_1407_5026_gb300 import sigma as S
+    r = S.relaxation_curves(B, device=local, hops=hops)
+    out = {}
+    for T, v in r.items():
+        out[str(T)] = {"acceptance": v["acceptance"], "sigma0": v["sigma0"], "t_end": v["t_end"],
+                       "tau": 1.0 / (v["sigma0"] * T * T) if v["sigma0"] > 0 else None,
+                       "t": [round(x, 4) for x in v["t"]],
+                       "x": [float(f"{x:.4g}") for x in v["x"]],
+                       "y": [round(y, 4) for y in v["y"]]}
+    return out
 
 
 def pair_share(B, s, reps, M, hops=64):

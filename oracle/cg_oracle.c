@@ -403,7 +403,8 @@ void orc_free(orc_chain *c)
 }
 
 /* eps_s = phi_s + sum_{t != s} (n_t - nu) / r_st, summed over t = 0..N-1 in
- * increasing order, the product rounded first (reading C7 of the design). */
+ * increasing order, each product rounded before it is added (the summation
+ * order the library's initial eps follows, so both give the same bits). */
 void orc_eps_scratch(const orc_chain *c, double *out)
 {
     int s, t;
