@@ -72,7 +72,7 @@ struct alignas(16) DevReplica {
     // random-site geometry (CG_SITES_RANDOM; null otherwise)
     const double *G;          // N x N minimum-image 1/r, 0 on the diagonal
     const int *rguide;        // 16 ints per site: kRandomGuide layout
-    const uint4 *rrec;        // per pair: running weight C (lo, hi words), partner j, 0
+    const uint2 *rrec;        // per pair: C mod 2^32, partner j | (C >> 32) << 31 (C <= 2^32)
     const double2 *rgx;       // per pair: 1/r, E dx (minimum-image dx, binary64)
 };
 
@@ -145,12 +145,15 @@ cudaError_t launch_pr_random(const DevReplica *d_reps, const int *d_index, int n
                              int threads, int smem_bytes, const RunArgs &args, cudaStream_t st);
 cudaError_t set_pr_random_smem_limit(int bytes);
 // The per-site record of a random-site partner list (16 ints, 64 bytes):
-// [0] first pair of the list, [9] one past its last; [1 + b], b = 0..7, the
-// pair that x1 = b 2^29 selects (the smallest m with b 2^29 < C_m; the last
-// pair when none); [12], [13] the list's last running weight (lo, hi words).
-// A label with x1 in bucket b = x1 >> 29 finds its pair in
-// [g[1 + b], min(g[2 + b], g[9] - 1)].
+// [0] first pair of the list, [1] one past its last; [2], [3] the list's
+// last running weight (lo, hi words); [4 + b/2] holds, in its low (b even)
+// or high (b odd) 16 bits, b = 0..15, the offset from [0] of the pair that
+// x1 = b 2^28 selects (the smallest m with b 2^28 < C_m; the last pair when
+// none); [12..15] unused.  A label with x1 in bucket b = x1 >> 28 finds its
+// pair in [start(b), min(start(b + 1), [1] - 1)], start(16) = [1].
+// Lists hold at most N - 1 < 2^16 pairs (N <= 28224 on one CTA).
 constexpr int kRandomGuide = 16;
+constexpr int kRandomBuckets = 16;
 inline int random_smem_bytes(int N)
 {
     return cg_align16(N * 8) + cg_align16(((N + 31) / 32) * 4);

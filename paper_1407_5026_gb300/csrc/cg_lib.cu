@@ -238,7 +238,7 @@ struct Rep {
     double Zmax = 0.0;
     double *d_px = nullptr, *d_py = nullptr, *d_G = nullptr;
     int *d_guide = nullptr;           // kRandomGuide ints per site
-    uint4 *d_rec = nullptr;           // running weight and partner of each pair
+    uint2 *d_rec = nullptr;           // running weight and partner of each pair
     double2 *d_rgx = nullptr;         // 1/r and E dx of each pair
 };
 
@@ -474,19 +474,21 @@ void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
 
 // The device form of a random-site replica's partner lists: per site the
 // kRandomGuide record (list bounds, the pair each x1 bucket starts at, the
-// last running weight), per pair (C lo, C hi, j, 0) and (1/r, E dx).
+// last running weight), per pair (C mod 2^32, j | (C >> 32) << 31) and
+// (1/r, E dx).
 void pack_random(const Rep &r, std::vector<int> &guide, std::vector<uint32_t> &rec,
                  std::vector<double> &rgx)
 {
     const int N = r.N;
     const size_t m = r.rj.size();
     guide.assign((size_t)N * kRandomGuide, 0);
-    rec.assign(4 * m, 0u);
+    rec.assign(2 * m, 0u);
     rgx.assign(2 * m, 0.0);
     for (size_t k = 0; k < m; ++k) {
-        rec[4 * k] = (uint32_t)r.rC[k];
-        rec[4 * k + 1] = (uint32_t)(r.rC[k] >> 32);
-        rec[4 * k + 2] = r.rj[k];
+        // C_k <= 2^32 in 33 bits: the low word, and its top bit above the
+        // partner (partners < N < 2^31)
+        rec[2 * k] = (uint32_t)r.rC[k];
+        rec[2 * k + 1] = r.rj[k] | ((uint32_t)(r.rC[k] >> 32) << 31);
         rgx[2 * k] = r.rg[k];
         rgx[2 * k + 1] = r.redx[k];
     }
@@ -494,16 +496,19 @@ void pack_random(const Rep &r, std::vector<int> &guide, std::vector<uint32_t> &r
         int *g = guide.data() + (size_t)s * kRandomGuide;
         const int lo = r.roff[s], hi = r.roff[s + 1];
         g[0] = lo;
-        g[9] = hi;
+        g[1] = hi;
         int a = lo;
-        for (int b = 0; b < 8; ++b) {
-            const unsigned long long v = (unsigned long long)b << 29;
+        for (int b = 0; b < kRandomBuckets; ++b) {
+            const unsigned long long v = (unsigned long long)b << (32 - 4);
             while (a < hi && !(v < r.rC[a])) ++a;      // smallest a with v < C_a
-            g[1 + b] = a < hi ? a : (hi > lo ? hi - 1 : lo);
+            const int start = a < hi ? a : (hi > lo ? hi - 1 : lo);
+            const uint32_t off = (uint32_t)(start - lo);   // < 2^16: lists hold < N pairs
+            uint32_t &w = reinterpret_cast<uint32_t &>(g[4 + b / 2]);
+            w |= (b & 1) ? (off << 16) : off;
         }
         const unsigned long long last = hi > lo ? r.rC[hi - 1] : 0ull;
-        g[12] = (int)(uint32_t)last;
-        g[13] = (int)(uint32_t)(last >> 32);
+        g[2] = (int)(uint32_t)last;
+        g[3] = (int)(uint32_t)(last >> 32);
     }
 }
 
@@ -730,7 +735,7 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
             tmp.N = (int)N;
             const size_t cnt = build_random(tmp) == CG_OK ? tmp.rj.size() : 0;
             const size_t c1 = cnt ? cnt : 1;
-            total += 2 * up(N * 8) + up(N * N * 8) + up(N * kRandomGuide * 4) + 2 * up(c1 * 16);
+            total += 2 * up(N * 8) + up(N * N * 8) + up(N * kRandomGuide * 4) + up(c1 * 8) + up(c1 * 16);
         }
         auto key = std::make_tuple(d.L, d.r_max, d.xi, dim_of(d));
         if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
@@ -883,7 +888,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         if (dalloc(h.get(), (void **)&r.d_px, N * 8) || dalloc(h.get(), (void **)&r.d_py, N * 8) ||
             dalloc(h.get(), (void **)&r.d_G, N * N * 8) ||
             dalloc(h.get(), (void **)&r.d_guide, N * kRandomGuide * 4) ||
-            dalloc(h.get(), (void **)&r.d_rec, cnt * 16) ||
+            dalloc(h.get(), (void **)&r.d_rec, cnt * 8) ||
             dalloc(h.get(), (void **)&r.d_rgx, cnt * 16)) { destroy_partial(); return nullptr; }
         const size_t m = r.rj.size();
         std::vector<int> guide;
@@ -895,7 +900,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         cudaMemcpyAsync(r.d_guide, guide.data(), N * kRandomGuide * 4, cudaMemcpyHostToDevice,
                         h->st);
         if (m) {
-            cudaMemcpyAsync(r.d_rec, rec.data(), m * 16, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(r.d_rec, rec.data(), m * 8, cudaMemcpyHostToDevice, h->st);
             cudaMemcpyAsync(r.d_rgx, rgx.data(), m * 16, cudaMemcpyHostToDevice, h->st);
         }
         if (launch_g_build(r.d_px, r.d_py, r.d.L, r.N, r.d_G, h->st) != cudaSuccess) {

@@ -206,8 +206,9 @@ def test_random_sites_too_large_for_a_cta_are_refused_at_once(libcg):
 
 def test_workspace_plan_counts_the_random_site_geometry(libcg):
     # a random-site replica adds its positions (2 N doubles), the N x N
-    # coupling matrix, a 64-byte guide record per site and per pair two
-    # 16-byte records (running weight + partner; 1/r + E dx); the pair count
+    # coupling matrix, a 64-byte guide record per site and per pair an
+    # 8-byte record (running weight + partner) and a 16-byte one (1/r + E dx);
+    # the pair count
     # is the oracle's, so the host geometry finds the same partners
     import oracle
     from paper_1407_5026_gb300 import binding as B
@@ -218,7 +219,7 @@ def test_workspace_plan_counts_the_random_site_geometry(libcg):
     cnt = len(oracle.Chain(16, r_max=3, xi=1.0, seed=5, replica=2, random_sites=True).pairs()[1])
     N = 256
     assert cnt > 0
-    assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up(N * 64) + 2 * up(cnt * 16)
+    assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up(N * 64) + up(cnt * 8) + up(cnt * 16)
 
 
 def test_site_positions_checks_its_arguments_on_host(libcg):

@@ -98,9 +98,12 @@ def test_autotune_restores_state_and_caches(B, tmp_path, monkeypatch):
             assert before[k][3] == after[3]
         shapes = [B.cg_group_shape(s.h, g) for g in range(B.cg_num_groups(s.h))]
         for sh in shapes:
-            # single-CTA groups need one thread per base column (L/2)
+            # single-CTA groups need one thread per base column (L/2); the
+            # cluster kernel one per column (L)
             assert sh["threads"] in (256, 384, 512, 1024) and 2 * sh["threads"] >= sh["L"]
-            assert sh["M"] in (1024, 4096, 16384)
+            assert sh["M"] in (1024, 4096, 16384, 65536)
+            assert sh["cluster"] in (1, 2, 4, 8)
+            assert sh["cluster"] == 1 or (sh["threads"] >= sh["L"] and sh["L"] % (2 * sh["cluster"]) == 0)
         data = json.loads(cache.read_text())
         assert len(data) == len(shapes)
         # M = 0 runs each group with its tuned M; binary64 still matches the
