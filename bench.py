@@ -709,6 +709,9 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     for name, wl, relax, hops, graph, tune in (
             ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
             ("L256_T0.02_R16_cluster", W.l256(), 65536, 16384, 0, True),
+            # the same replicas on forced 4-CTA clusters without the
+            # autotuner's trial launches (profiling with --config only)
+            ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
             ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
@@ -718,11 +721,14 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
             ("lattice_L64_T0.05_R152_fp64", W.random_sites(lattice=True), 2048, 2048, 0, False)):
         if only is not None and name != only:
             continue
+        forced = 4 if name.endswith("_cluster4") else 0
+        if forced and only is None:
+            continue
         reps = [r.as_dict() for r in wl.replicas]
         pair = {k: wl.extra[k] for k in ("pair_frac", "pair_rmax") if wl.extra.get("pair_frac")}
         prec = B.CG_FP64 if wl.precision == "fp64" else B.CG_FP32
         s = B.System(reps, precision=prec, refresh_every=wl.refresh_every,
-                     use_graph=graph, device=local, **pair)
+                     use_graph=graph, device=local, cluster_size=forced, **pair)
         s.run(relax, wl.M)
         if tune:
             B.cg_autotune(s.h, 256)
