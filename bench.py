@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # workload (304 replicas x 1024 hops), from the ncu capture of the relaxed
 # L=128 batch kept under profiles/; valid only while the kernel sources hash
 # to the captured version.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "f5dffe00b6b3fc12", "bytes_per_launch": 20.748e6,
-                   "replicas": 304, "hops_per_replica": 1024, "M": 4096, "threads": 512,
+TRAFFIC_CAPTURE = {"sources_sha256_16": "f5dffe00b6b3fc12", "bytes_per_launch": 20.742e6,
+                   "replicas": 304, "hops_per_replica": 1024, "M": 16384, "threads": 512,
                    "cluster": 1}
 
 
