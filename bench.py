@@ -711,6 +711,20 @@ def cluster_roofline(reps, hops_per_s, cluster, smem_peak, sms, precision):
             "frac": achieved / peak, "sms_used": used, "bytes_per_hop": per_hop}
 
 
+def random_roofline(reps, hops_per_s):
+    """The random-site update's HBM roofline: a hop reads rows j and i of the
+    binary64 coupling matrix G (16 N bytes; G of a box past L ~ 32 is far
+    larger than L2), against the measured HBM copy bandwidth."""
+    N = reps[0]["L"] ** 2
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peak = float(json.load(f)["hbm_gbs"])
+    ach = hops_per_s * 16.0 * N / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_hop": 16 * N, "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+            "note": "G-row bytes of the eps update only; the labels' partner lookups add "
+                    "latency-bound gathers"}
+
+
 def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
@@ -722,34 +736,48 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     4-CTA clusters (eps split by z-planes), 304 replicas of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair), and
     152 binary64 replicas of L=64 (and of L=32) with sites at random
-    positions against the L=64 replicas on the lattice.  Each is timed with CUDA events over hops
-    that follow a relaxation from the random start."""
+    positions against the L=64 replicas on the lattice, one random-site
+    replica of L=128 on one CTA and on an 8-CTA cluster, and 16 random-site
+    replicas of L=192 (eps of 36,864 sites: past one CTA) on autotuned
+    clusters.  Each is timed with CUDA events over hops that follow a
+    relaxation from the random start."""
     import torch
     from paper_1407_5026_gb300 import workloads as W
     out = {}
-    for name, wl, relax, hops, graph, tune in (
-            ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True),
-            ("L256_T0.02_R16_cluster", W.l256(), 65536, 16384, 0, True),
+    for name, wl, relax, hops, graph, tune, forced, dflt in (
+            ("mixed_L32-96_R256_T0.03", W.mixed_batch(), 8192, 4096, 1, True, 0, True),
+            ("L256_T0.02_R16_cluster", W.l256(), 65536, 16384, 0, True, 0, True),
             # the same replicas on forced 4-CTA clusters without the
             # autotuner's trial launches (profiling with --config only)
-            ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False),
-            ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False),
-            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False),
-            ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False),
-            ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False),
-            ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False),
-            ("random_L32_T0.05_R152_fp64", W.random_sites(L=32), 2048, 2048, 0, False),
-            ("lattice_L64_T0.05_R152_fp64", W.random_sites(lattice=True), 2048, 2048, 0, False)):
+            ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False, 4, False),
+            ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False, 0, True),
+            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False, 0, True),
+            ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False, 0, True),
+            ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False, 0, True),
+            ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False, 0, True),
+            ("random_L32_T0.05_R152_fp64", W.random_sites(L=32), 2048, 2048, 0, False, 0, True),
+            ("lattice_L64_T0.05_R152_fp64", W.random_sites(lattice=True), 2048, 2048, 0, False,
+             0, True),
+            ("random_L128_T0.05_R1_fp64", W.random_sites(R=1, L=128), 4096, 4096, 0, False, 0,
+             True),
+            ("random_L128_T0.05_R1_fp64_cluster8", W.random_sites(R=1, L=128), 4096, 4096, 0,
+             False, 8, True),
+            ("random_L192_T0.05_R16_fp64_cluster", W.random_sites(R=16, L=192), 2048, 4096, 0,
+             True, 0, True)):
         if only is not None and name != only:
             continue
-        forced = 4 if name.endswith("_cluster4") else 0
-        if forced and only is None:
+        if not dflt and only is None:
             continue
         reps = [r.as_dict() for r in wl.replicas]
         pair = {k: wl.extra[k] for k in ("pair_frac", "pair_rmax") if wl.extra.get("pair_frac")}
         prec = B.CG_FP64 if wl.precision == "fp64" else B.CG_FP32
+        # a random-site box holds an 8 N^2-byte coupling matrix per replica
+        # (174 GB for 16 replicas of L=192): the library allocates it and
+        # frees it at close, outside torch's cache
+        big = any(r.get("sites") and r["L"] > 128 for r in reps)
         s = B.System(reps, precision=prec, refresh_every=wl.refresh_every,
-                     use_graph=graph, device=local, cluster_size=forced, **pair)
+                     use_graph=graph, device=local, cluster_size=forced,
+                     torch_memory=not big, **pair)
         s.run(relax, wl.M)
         if tune:
             B.cg_autotune(s.h, 256)
@@ -776,7 +804,9 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
                      # clocks over the timed hops
                      "update_cycle_share": update_share(o0, o1)}
         cl = max(g["cluster"] for g in out[name]["groups"])
-        if cl > 1 and smem_peak and sms:
+        if reps[0].get("sites"):
+            out[name]["roofline"] = random_roofline(reps, out[name]["hops_per_s"])
+        elif cl > 1 and smem_peak and sms:
             out[name]["roofline"] = cluster_roofline(reps, out[name]["hops_per_s"], cl,
                                                      smem_peak, sms, wl.precision)
         if pair:

@@ -83,9 +83,14 @@ typedef struct cg_handle cg_handle;
  *          partners j != i with r_ij <= r_max drawn by an integer tower of
  *          weights floor(2^32 exp(-2 r / xi) / Zmax) (Zmax the largest
  *          per-site sum), Gamma = N Zmax, the real minimum-image dx in the
- *          field term and no dipole counter (P stays 0).  Binary64, one CTA
- *          per replica, single hops, deterministic time (else CG_EINVAL); the
- *          N x N coupling matrix lives in device memory.                */
+ *          field term and no dipole counter (P stays 0).  Binary64, single
+ *          hops, deterministic time (else CG_EINVAL); N <= 131072 (L <= 362;
+ *          partner lists below 2^16 pairs); one CTA per replica, or, when
+ *          eps (8 N bytes) does not fit one or cluster_size forces it, a
+ *          cluster of 2, 4 or 8 CTAs, CTA r owning the eps of sites
+ *          [r Nc, (r+1) Nc), Nc = ceil(N / C) rounded up to a multiple of
+ *          32 (any even L).  The N x N coupling matrix (8 N^2 bytes) lives
+ *          in device memory (CG_ENOMEM when it does not fit).           */
 typedef struct {
     int32_t L;
     int32_t r_max;
@@ -123,7 +128,8 @@ typedef struct {
                                    [r L/2C, (r+1) L/2C) and the same rows
                                    + L/2, so L must be a multiple of 2C) or
                                    by z-planes on the cubic lattice (L a
-                                   multiple of C)                              */
+                                   multiple of C), or by site index on random
+                                   sites (any even L)                          */
     int32_t time_mode;          /* CG_TIME_DETERMINISTIC (0): t = attempts/Gamma;
                                    CG_TIME_GAUSSIAN: each executed hop adds a
                                    Gaussian dt of mean m/Gamma and standard
@@ -381,9 +387,10 @@ int cg_read_trace(cg_handle *h, int replica, cg_trace_point *out_host, int cap);
  * 1/A but larger than the number of concurrent threads; the best M and launch
  * shape depend on the GPU, so for every group of replicas with one L this
  * times the persistent launch for every cluster size (CTAs per replica: 1
- * when eps fits one CTA, and each of 2, 4, 8 that divides L and fits; only
- * the forced size when cg_opts.cluster_size was set, only 1 for random-site
- * replicas), CTA sizes 256, 384, 512, 1024 (those the kernel takes) and M in
+ * when eps fits one CTA, and each of 2, 4, 8 that fits, on lattices only
+ * those whose row or plane split divides L; only the forced size when
+ * cg_opts.cluster_size was set), CTA sizes 256, 384, 512, 1024 (those the
+ * kernel takes) and M in
  * {1024, 4096, 16384, 65536}, over hops_per_trial hops (0: 256) on a copy of the
  * group's state.  A trial counts only when every replica of the group
  * completed its hops.  The state is restored bit for bit after each trial

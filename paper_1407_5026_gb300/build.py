@@ -22,11 +22,11 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["cg_lib.cu", "cg_pr_kernel.cu", "cg_pr_kernel3d.cu", "cg_pr_kernel_pair.cu",
            "cg_pr_kernel_pair_time.cu", "cg_pr_cluster_pair.cu", "cg_pr_kernel3d_pair.cu",
-           "cg_pr_random.cu",
+           "cg_pr_random.cu", "cg_pr_random_cluster.cu",
            "cg_aux_kernels.cu",
            "cg_microbench.cu", "cg_refresh_tc.cu", "cg_refresh_static.cu", "cg_pr_cluster.cu"]
 HEADERS = ["cg_internal.h", "cg_device.cuh", "cg_pr_common.cuh", "cg_pr_persistent.cuh",
-           "cg_pr_cluster.cuh"]
+           "cg_pr_cluster.cuh", "cg_pr_random.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -151,13 +151,27 @@ cudaError_t set_pr_random_smem_limit(int bytes);
 // x1 = b 2^28 selects (the smallest m with b 2^28 < C_m; the last pair when
 // none); [12..15] unused.  A label with x1 in bucket b = x1 >> 28 finds its
 // pair in [start(b), min(start(b + 1), [1] - 1)], start(16) = [1].
-// Lists hold at most N - 1 < 2^16 pairs (N <= 28224 on one CTA).
+// The offsets are 16 bits: the library refuses lists of 2^16 or more pairs.
 constexpr int kRandomGuide = 16;
 constexpr int kRandomBuckets = 16;
-inline int random_smem_bytes(int N)
+// Sites whose eps a CTA of a C-CTA cluster owns: ceil(N / C) rounded up to a
+// multiple of 32 (CTA rank owns [rank Nc, min(N, (rank + 1) Nc))).
+__host__ __device__ inline int random_cluster_sites(int N, int C)
 {
-    return cg_align16(N * 8) + cg_align16(((N + 31) / 32) * 4);
+    return C <= 1 ? N : (((N + C - 1) / C + 31) / 32) * 32;
 }
+// Dynamic shared memory of a random-site CTA: its eps (binary64) and the
+// whole occupation bitmask.
+inline int random_smem_bytes(int N, int C = 1)
+{
+    return cg_align16(random_cluster_sites(N, C) * 8) + cg_align16(((N + 31) / 32) * 4);
+}
+// The random-site chain on clusters of `cluster` (2, 4 or 8) CTAs per replica
+// (cg_pr_random_cluster.cu); grid = n_reps * cluster CTAs of 256, 512 or 1024
+// threads.
+cudaError_t launch_pr_random_cluster(const DevReplica *d_reps, const int *d_index, int n_reps,
+                                     int cluster, int threads, int smem_bytes,
+                                     const RunArgs &args, cudaStream_t st);
 
 // Launchers (defined in the .cu files).
 cudaError_t launch_pr_persistent(int precision, const DevReplica *d_reps,

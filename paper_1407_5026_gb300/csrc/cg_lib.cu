@@ -375,12 +375,13 @@ int check_desc(const cg_replica_desc &d)
     if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(CG_EINVAL, "T must be > 0");
     if (!(d.W >= 0.0) || !std::isfinite(d.W)) return fail(CG_EINVAL, "W must be >= 0");
     if (!std::isfinite(d.E)) return fail(CG_EINVAL, "E must be finite");
-    // random sites keep eps (binary64) and the bitmask in one CTA's shared
-    // memory (227 KiB opt-in on sm_100-class GPUs, 2 KiB left for the
-    // kernel's static part): refuse before the O(N^2) geometry is built
-    if (d.sites == CG_SITES_RANDOM && random_smem_bytes((int)N) > 227 * 1024 - 2048)
-        return fail(CG_EINVAL, "random-site replicas need eps of N <= 28224 sites (L <= 168) "
-                               "in one CTA's shared memory");
+    // random sites keep eps (binary64) in the shared memory of one CTA or of
+    // a cluster of up to 8 (227 KiB opt-in per CTA on sm_100-class GPUs,
+    // 2 KiB left for the kernel's static part), and G (8 N^2 bytes) in
+    // device memory: refuse before the geometry is built
+    if (d.sites == CG_SITES_RANDOM &&
+        (N > 131072.0 || random_smem_bytes((int)N, 8) > 227 * 1024 - 2048))
+        return fail(CG_EINVAL, "random-site replicas need N <= 131072 sites (L <= 362)");
     return CG_OK;
 }
 
@@ -402,15 +403,20 @@ double gamma_of(const Rep &r, const cg_opts &o)
 
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
-    if (r.random) return random_smem_bytes(r.N);
+    if (r.random) return random_smem_bytes(r.N, cluster);
     const int rb = precision == CG_FP64 ? 8 : 4;
     return smem_layout(r.N / cluster, (int)r.tab->t64.size(), r.tab->V, r.words, rb).total;
 }
 
 // L must be a multiple of this for a cluster of c CTAs: c on the cubic
 // lattice (whole z-planes per CTA), 2c on the square lattice (each CTA holds
-// L/(2c) base rows and their partner rows y + L/2).
-int cluster_rows_unit(const cg_replica_desc &d, int c) { return dim_of(d) == 3 ? c : 2 * c; }
+// L/(2c) base rows and their partner rows y + L/2); random sites split by
+// site index, any L.
+int cluster_rows_unit(const cg_replica_desc &d, int c)
+{
+    if (d.sites == CG_SITES_RANDOM) return 2;
+    return dim_of(d) == 3 ? c : 2 * c;
+}
 
 // CTAs per replica: 1 when the replica fits one CTA's shared memory, else the
 // smallest cluster of 2, 4 or 8 CTAs (each holding L/C rows of eps, or L/C
@@ -421,11 +427,10 @@ int choose_cluster(const cg_opts &o, const Rep &r, int optin)
     // room for the kernels' static shared memory (the pair-hop cluster
     // kernel's exchange slots take it past 2 KiB)
     const int budget = optin - (o.pair_frac > 0.0 ? 3072 : 2048);
-    if (r.random) return (o.cluster_size <= 1 && persistent_smem(r, o.precision) <= budget) ? 1 : 0;
     if (o.cluster_size > 1) {
         const int c = o.cluster_size;
-        if ((c == 2 || c == 4 || c == 8) && r.d.L % cluster_rows_unit(r.d, c) == 0 && r.d.L >= 16 &&
-            persistent_smem(r, o.precision, c) <= budget)
+        if ((c == 2 || c == 4 || c == 8) && r.d.L % cluster_rows_unit(r.d, c) == 0 &&
+            (r.random || r.d.L >= 16) && persistent_smem(r, o.precision, c) <= budget)
             return c;
         return 0;
     }
@@ -536,16 +541,48 @@ int build_random(Rep &r)
         if (d < -0.5 * Ld) return d + Ld;
         return d;
     };
+    // candidate partners from a cell list: nc x nc cells of side L/nc >= R + 1,
+    // so every t within r_max of s lies in the 3 x 3 cells around s's (the
+    // margin of 1 covers the rounding of the cell index); the candidates are
+    // taken in ascending t, the order of the definition, so Z sums in the
+    // same order.  With fewer than 3 cells per axis every t is a candidate.
+    const int nc = L / (R + 1) >= 3 ? L / (R + 1) : 1;
+    auto cell_of = [&](double v) {
+        int c = (int)std::floor(v * (double)nc / Ld);
+        return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+    };
+    std::vector<int> cstart((size_t)nc * nc + 1, 0), cell(N), members(N);
+    for (int s = 0; s < N; ++s) {
+        cell[s] = cell_of(r.py[s]) * nc + cell_of(r.px[s]);
+        ++cstart[cell[s] + 1];
+    }
+    for (int c = 0; c < nc * nc; ++c) cstart[c + 1] += cstart[c];
+    {
+        std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+        for (int s = 0; s < N; ++s) members[fill[cell[s]]++] = s;   // ascending s per cell
+    }
     r.roff.assign(N + 1, 0);
     r.rj.clear(); r.rg.clear(); r.redx.clear(); r.rC.clear();
     std::vector<double> w, Z(N, 0.0), dxs;
+    std::vector<int> cand;
     for (int s = 0; s < N; ++s) {
         r.roff[s] = (int)r.rj.size();
-        for (int t = 0; t < N; ++t) {
+        cand.clear();
+        if (nc == 1) {
+            for (int t = 0; t < N; ++t) cand.push_back(t);
+        } else {
+            const int cx = cell[s] % nc, cy = cell[s] / nc;
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int c = ((cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+                    cand.insert(cand.end(), members.begin() + cstart[c],
+                                members.begin() + cstart[c + 1]);
+                }
+            std::sort(cand.begin(), cand.end());
+        }
+        for (const int t : cand) {
             if (t == s) continue;
             const double dx = mi(r.px[t] - r.px[s]);
-            // |dx| well beyond r_max: never a partner (cheap pre-test)
-            if (dx > R + 1.0 || dx < -(R + 1.0)) continue;
             const double dy = mi(r.py[t] - r.py[s]);
             const double rr = std::sqrt(dx * dx + dy * dy);
             if (rr == 0.0) return fail(CG_EINVAL, "random sites: two sites coincide");
@@ -557,6 +594,9 @@ int build_random(Rep &r)
             w.push_back(ws);
             Z[s] = Z[s] + ws;
         }
+        if ((int)r.rj.size() - r.roff[s] >= 65536)
+            return fail(CG_EINVAL, "random sites: a partner list holds 2^16 or more pairs "
+                                   "(r_max too large)");
     }
     r.roff[N] = (int)r.rj.size();
     r.Zmax = 0.0;
@@ -785,10 +825,8 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     }
     for (int k = 0; k < R; ++k)
         if (reps[k].sites == CG_SITES_RANDOM &&
-            (o.precision != CG_FP64 || o.pair_frac > 0.0 || o.time_mode != CG_TIME_DETERMINISTIC ||
-             o.cluster_size > 1)) {
-            fail(CG_EINVAL, "random sites run in binary64, one CTA per replica, single hops and "
-                            "deterministic time");
+            (o.precision != CG_FP64 || o.pair_frac > 0.0 || o.time_mode != CG_TIME_DETERMINISTIC)) {
+            fail(CG_EINVAL, "random sites run in binary64, single hops and deterministic time");
             return nullptr;
         }
     if (o.pair_frac > 0.0) {
@@ -967,7 +1005,10 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         g.smem = smem;
         g.cluster = cluster;
         g.threads = choose_threads(o, g.L, smem);
-        if (cluster > 1) {
+        if (cluster > 1 && g.random) {
+            // the random-site cluster kernel takes 256, 512 or 1024 threads
+            if (g.threads == 384) g.threads = 512;
+        } else if (cluster > 1) {
             // the cluster kernel maps a thread to a column: at least L threads
             if (g.threads < 512) g.threads = 512;
             while (g.threads < g.L && g.threads < 1024) g.threads *= 2;
@@ -1099,7 +1140,10 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.toy_A0 = h->toy_A0;
     a.time_mode = h->opts.time_mode;
     a.pair = h->opts.pair_frac > 0.0 ? 1 : 0;
-    if (g.random)
+    if (g.random && g.cluster > 1)
+        CG_CUDA(launch_pr_random_cluster(h->d_reps, h->d_index + g.first, g.count, g.cluster,
+                                         g.threads, g.smem, a, st));
+    else if (g.random)
         CG_CUDA(launch_pr_random(h->d_reps, h->d_index + g.first, g.count, g.threads, g.smem, a,
                                  st));
     else if (g.cluster > 1)
@@ -1565,13 +1609,13 @@ static bool tune_cache_lookup(const std::string &text, const std::string &key, i
 }
 
 // Cluster sizes a group can run with (CTAs per replica): the size chosen at
-// creation when the caller forced one or the group holds random-site
-// replicas; else 1 (when eps fits one CTA) and every 2, 4, 8 that divides L
-// and whose per-CTA shared memory fits, each with that shared-memory size.
+// creation when the caller forced one; else 1 (when eps fits one CTA) and
+// every 2, 4, 8 whose per-CTA shared memory fits (on lattices: that divides
+// L as the row split needs), each with that shared-memory size.
 static std::vector<std::pair<int, int>> cluster_candidates(const cg_handle *h, const Group &g)
 {
     std::vector<std::pair<int, int>> out;
-    if (g.random || h->opts.cluster_size > 1) {
+    if (h->opts.cluster_size > 1) {
         out.push_back({g.cluster, g.smem});
         return out;
     }
@@ -1579,7 +1623,7 @@ static std::vector<std::pair<int, int>> cluster_candidates(const cg_handle *h, c
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     const int budget = optin - (h->opts.pair_frac > 0.0 ? 3072 : 2048);
     for (int c = 1; c <= 8; c *= 2) {
-        if (c > 1 && (g.L % (g.dim == 3 ? c : 2 * c) != 0 || g.L < 16)) continue;
+        if (c > 1 && !g.random && (g.L % (g.dim == 3 ? c : 2 * c) != 0 || g.L < 16)) continue;
         int sm = 0;
         for (int k = 0; k < g.count; ++k)
             sm = std::max(sm, persistent_smem(h->reps[h->order[g.first + k]], h->opts.precision, c));
@@ -1668,10 +1712,14 @@ int cg_autotune(cg_handle *h, uint32_t hops_per_trial)
                 const int t = shapes[ti];
                 // the single-CTA update needs L/2 base columns (L on the cubic
                 // lattice); the cluster kernel maps a thread to a column and
-                // is built for 512 and 1024 threads
-                if (t < g.L / 2 || (g.dim == 3 && t < g.L)) continue;
-                if (c > 1 && (t < 512 || t < g.L)) continue;
-                if (g.random && c > 1) continue;
+                // is built for 512 and 1024 threads; the random-site kernels
+                // take any L, the cluster form 256, 512 or 1024 threads
+                if (g.random) {
+                    if (c > 1 && t == 384) continue;
+                } else {
+                    if (t < g.L / 2 || (g.dim == 3 && t < g.L)) continue;
+                    if (c > 1 && (t < 512 || t < g.L)) continue;
+                }
                 for (int mi = 0; mi < 4 && ce == cudaSuccess; ++mi) {
                     Group trial = g;
                     trial.threads = t;

@@ -49,13 +49,15 @@ struct Slot {
 
 // Square lattice: the CTA that owns row y and the row's local index there
 // (base rows of B = L/(2C) per CTA, partner rows y + L/2 after them);
-// magicB = floor(2^32 / B) + 1 divides by B for y < L <= 1024.
+// magicB = floor(2^32 / B) + 1 divides by B for y < L <= 1024 when B >= 2;
+// B = 1 (L = 2C), where that multiplier would need 33 bits, has magicB = 0
+// and owner = y mod L/2.
 __device__ __forceinline__ void cluster_row_owner(int y, int Lh, int B, unsigned magicB,
                                                   unsigned &owner, int &yl)
 {
     const bool upper = y >= Lh;
     const int yb = upper ? y - Lh : y;
-    owner = __umulhi((unsigned)yb, magicB);
+    owner = magicB ? __umulhi((unsigned)yb, magicB) : (unsigned)yb;
     yl = yb - (int)owner * B + (upper ? B : 0);
 }
 
@@ -127,7 +129,8 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int log2L = __ffs(L) - 1;
     // square lattice: base rows per CTA and the multiplier that divides by it
     const int Bq = rows_local >> 1;
-    const unsigned magicB = kDim == 3 ? 0u : (unsigned)(4294967296ull / (unsigned)Bq + 1ull);
+    const unsigned magicB =
+        (kDim == 3 || Bq < 2) ? 0u : (unsigned)(4294967296ull / (unsigned)Bq + 1ull);
     const int ntab = kDim == 3 ? H1 * H1 * H1 : H1 * H1;
 
     const SmemLayout lay = smem_layout(N_local, ntab, V, words, (int)sizeof(Real));

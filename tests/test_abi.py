@@ -169,8 +169,7 @@ def test_product_package_has_no_cpu_path():
 
 @pytest.mark.parametrize("bad,msg", [(dict(precision=1), "random sites"),
                                      (dict(pair_frac=0.1, pair_rmax=2), "random sites"),
-                                     (dict(time_mode=1), "random sites"),
-                                     (dict(cluster_size=2), "random sites")])
+                                     (dict(time_mode=1), "random sites")])
 def test_random_sites_refuse_unsupported_options_on_host(libcg, bad, msg):
     from paper_1407_5026_gb300 import binding as B
     assert B.CG_FP32 == 1 and B.CG_TIME_GAUSSIAN == 1
@@ -188,36 +187,39 @@ def test_random_site_descriptor_checks_on_host(libcg, kw, msg):
     assert msg in str(ei.value)
 
 
-def test_random_sites_too_large_for_a_cta_are_refused_at_once(libcg):
-    # eps of a random-site replica lives in one CTA's shared memory; L = 1024
-    # (N = 2^20) is refused by the descriptor check, before the O(N^2) site
-    # geometry would be built
+def test_random_sites_too_large_for_a_cluster_are_refused_at_once(libcg):
+    # eps of a random-site replica lives in the shared memory of one CTA or
+    # of a cluster of up to 8; L = 1024 (N = 2^20) is refused by the
+    # descriptor check, before the site geometry would be built
     import time
     from paper_1407_5026_gb300 import binding as B
     big = [B.desc(L=1024, r_max=6, sites=B.CG_SITES_RANDOM)]
     t0 = time.perf_counter()
     with pytest.raises(B.CgError) as ei:
         B.cg_create_batch(big, B.opts())
-    assert "L <= 168" in str(ei.value)
+    assert "L <= 362" in str(ei.value)
     assert B.cg_workspace_bytes(big, B.opts()) == 0
-    assert "L <= 168" in B.cg_last_error()
+    assert "L <= 362" in B.cg_last_error()
     assert time.perf_counter() - t0 < 5.0
 
 
-def test_workspace_plan_counts_the_random_site_geometry(libcg):
+@pytest.mark.parametrize("L,r_max", [(16, 3), (10, 4), (30, 2), (36, 5)])
+def test_workspace_plan_counts_the_random_site_geometry(libcg, L, r_max):
     # a random-site replica adds its positions (2 N doubles), the N x N
     # coupling matrix, a 64-byte guide record per site and per pair an
     # 8-byte record (running weight + partner) and a 16-byte one (1/r + E dx);
-    # the pair count
-    # is the oracle's, so the host geometry finds the same partners
+    # the pair count is the oracle's, whose full scan over every pair checks
+    # the library's cell-list search (L / (r_max + 1) cells per axis; fewer
+    # than 3 at L = 10, r_max = 4, where the library scans every pair too)
     import oracle
     from paper_1407_5026_gb300 import binding as B
     up = lambda b: (b + 255) // 256 * 256
-    p = dict(L=16, r_max=3, xi=1.0, seed=5, replica=2)
+    p = dict(L=L, r_max=r_max, xi=1.0, seed=5, replica=2)
     rnd = B.cg_workspace_bytes([B.desc(sites=B.CG_SITES_RANDOM, **p)], B.opts())
     lat = B.cg_workspace_bytes([B.desc(**p)], B.opts())
-    cnt = len(oracle.Chain(16, r_max=3, xi=1.0, seed=5, replica=2, random_sites=True).pairs()[1])
-    N = 256
+    cnt = len(oracle.Chain(L, r_max=r_max, xi=1.0, seed=5, replica=2,
+                           random_sites=True).pairs()[1])
+    N = L * L
     assert cnt > 0
     assert rnd - lat == 2 * up(N * 8) + up(N * N * 8) + up(N * 64) + up(cnt * 8) + up(cnt * 16)
 

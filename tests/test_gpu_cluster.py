@@ -36,8 +36,10 @@ def _oracle_for(p):
                         T=p["T"], E=p["E"], seed=p["seed"], replica=p.get("replica", 0))
 
 
+# (16, 8): one base row per CTA (L = 2C), where the row-owner division has
+# no 32-bit multiplier and takes the row index itself
 @pytest.mark.parametrize("L,cluster,T", [(32, 2, 0.05), (64, 4, 0.02), (48, 2, 0.1),
-                                         (64, 8, 0.05)])
+                                         (64, 8, 0.05), (16, 8, 0.1)])
 def test_cluster_binary64_trajectory_is_bit_exact(B, L, cluster, T):
     reps = [dict(L=L, nu=0.5, W=1.0, xi=1.0, r_max=6, T=T, E=0.01, seed=s, replica=s)
             for s in range(3)]
