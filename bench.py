@@ -734,7 +734,9 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
     tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
     4-CTA clusters (eps split by z-planes), 304 replicas of L=64 with and
-    without two-electron hops (a fifth of the labels proposing a pair), and
+    without two-electron hops (a fifth of the labels proposing a pair), 19
+    replicas of the 64^3 lattice on 8-CTA clusters (1/r of the update indexed
+    by r^2), and
     152 binary64 replicas of L=64 (and of L=32) with sites at random
     positions against the L=64 replicas on the lattice, one random-site
     replica of L=128 on one CTA and on an 8-CTA cluster, and 16 random-site
@@ -752,6 +754,10 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
             ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False, 4, False),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False, 0, True),
             ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False, 0, True),
+            # 19 replicas of 64^3 on 8-CTA clusters (152 SMs), the update
+            # reading 1/r by r^2 (the folded table fits beside no eps share)
+            ("cubic_L64_T0.05_R19_cluster8", W.cubic(R=19, L=64), 2048, 4096, 0, False, 0,
+             True),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False, 0, True),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False, 0, True),
             ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False, 0, True),

@@ -32,6 +32,10 @@ __device__ __forceinline__ int tab_entries(const DevReplica &R)
     return R.dim == 3 ? R.H1 * R.H1 * R.H1 : R.H1 * R.H1;
 }
 
+// kTabGlobal: the binary64 table stays in global memory (read through the
+// read-only cache) when it does not fit shared memory beside the bitmask
+// (the 64^3 lattice: 288 KB); the sums are the same.
+template <bool kTabGlobal>
 __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restrict__ rp,
                                                        int precision)
 {
@@ -39,9 +43,11 @@ __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restr
     const DevReplica &R = *rp;
     const int L = R.L, N = R.N, H1 = R.H1, words = R.words, ntab = tab_entries(R);
     const int Lz = R.dim == 3 ? L : 1;
-    double *tab = reinterpret_cast<double *>(sm);
-    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(ntab * 8));
-    for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab[l] = R.tinv64[l];
+    double *tab_s = reinterpret_cast<double *>(sm);
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + (kTabGlobal ? 0 : cg_align16(ntab * 8)));
+    const double *tab = kTabGlobal ? R.tinv64 : tab_s;
+    if (!kTabGlobal)
+        for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab_s[l] = R.tinv64[l];
     for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,7 +66,9 @@ __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restr
                 const int t = base + xt;
                 if (t == s) continue;
                 const double c = ((occ[t >> 5] >> (t & 31)) & 1u) ? c_occ : c_emp;
-                acc = d_add(acc, d_mul(c, row[fold_axis(xs - xt, L)]));
+                const double g = kTabGlobal ? __ldg(row + fold_axis(xs - xt, L))
+                                            : row[fold_axis(xs - xt, L)];
+                acc = d_add(acc, d_mul(c, g));
             }
         }
     }
@@ -71,17 +79,31 @@ __global__ void __launch_bounds__(128) eps_init_kernel(const DevReplica *__restr
         reinterpret_cast<float *>(R.eps)[s] = __double2float_rn(e);
 }
 
+// Shared memory of the set-up and refresh kernels above which the table is
+// read from global memory instead.
+constexpr int kAuxSmemLimit = 200 * 1024;
+
 cudaError_t launch_eps_init(const DevReplica *d_rep, int N, int ntab, int words, int precision,
                             cudaStream_t st)
 {
     const int smem = cg_align16(ntab * 8) + words * 4;
-    cudaError_t e = cudaFuncSetAttribute(eps_init_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e) return e;
-    eps_init_kernel<<<(N + 127) / 128, 128, smem, st>>>(d_rep, precision);
+    cudaError_t e;
+    if (smem > kAuxSmemLimit) {
+        const int sm2 = words * 4;
+        if ((e = cudaFuncSetAttribute(eps_init_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm2)))
+            return e;
+        eps_init_kernel<true><<<(N + 127) / 128, 128, sm2, st>>>(d_rep, precision);
+        return cudaGetLastError();
+    }
+    if ((e = cudaFuncSetAttribute(eps_init_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    eps_init_kernel<false><<<(N + 127) / 128, 128, smem, st>>>(d_rep, precision);
     return cudaGetLastError();
 }
 
+template <bool kTabGlobal>
 __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__restrict__ rp)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -89,9 +111,11 @@ __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__r
     const DevReplica &R = *rp;
     const int L = R.L, N = R.N, H1 = R.H1, words = R.words, ntab = tab_entries(R);
     const int Lz = R.dim == 3 ? L : 1;
-    double *tab = reinterpret_cast<double *>(sm);
-    unsigned *occ = reinterpret_cast<unsigned *>(sm + cg_align16(ntab * 8));
-    for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab[l] = R.tinv64[l];
+    double *tab_s = reinterpret_cast<double *>(sm);
+    unsigned *occ = reinterpret_cast<unsigned *>(sm + (kTabGlobal ? 0 : cg_align16(ntab * 8)));
+    const double *tab = kTabGlobal ? R.tinv64 : tab_s;
+    if (!kTabGlobal)
+        for (int l = threadIdx.x; l < ntab; l += blockDim.x) tab_s[l] = R.tinv64[l];
     for (int l = threadIdx.x; l < words; l += blockDim.x) occ[l] = R.occ[l];
     if (threadIdx.x == 0) s_max = 0ull;
     __syncthreads();
@@ -109,8 +133,9 @@ __global__ void __launch_bounds__(256) refresh_fp64_kernel(const DevReplica *__r
                 const int t = w * 32 + b;
                 int xt, yt, zt;
                 site_xyz((unsigned)t, R, xt, yt, zt);
-                acc += tab[(fold_axis(zs - zt, Lz) * H1 + fold_axis(ys - yt, L)) * H1 +
-                           fold_axis(xs - xt, L)];
+                const int o = (fold_axis(zs - zt, Lz) * H1 + fold_axis(ys - yt, L)) * H1 +
+                              fold_axis(xs - xt, L);
+                acc += kTabGlobal ? __ldg(tab + o) : tab[o];
             }
         }
         const double e = R.phi[s] + (acc + R.negC0nu);
@@ -137,10 +162,19 @@ cudaError_t launch_refresh_fp64(const DevReplica *d_rep, int N, int ntab, int wo
                                 cudaStream_t st)
 {
     const int smem = cg_align16(ntab * 8) + words * 4;
-    cudaError_t e = cudaFuncSetAttribute(refresh_fp64_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e) return e;
-    refresh_fp64_kernel<<<(N + 255) / 256, 256, smem, st>>>(d_rep);
+    cudaError_t e;
+    if (smem > kAuxSmemLimit) {
+        const int sm2 = words * 4;
+        if ((e = cudaFuncSetAttribute(refresh_fp64_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm2)))
+            return e;
+        refresh_fp64_kernel<true><<<(N + 255) / 256, 256, sm2, st>>>(d_rep);
+        return cudaGetLastError();
+    }
+    if ((e = cudaFuncSetAttribute(refresh_fp64_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    refresh_fp64_kernel<false><<<(N + 255) / 256, 256, smem, st>>>(d_rep);
     return cudaGetLastError();
 }
 

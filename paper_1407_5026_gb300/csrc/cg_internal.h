@@ -61,6 +61,8 @@ struct alignas(16) DevReplica {
     const unsigned int *thr;  // V tower thresholds C_k - 1
     const int *disp;          // V packed hop vectors: (dx & 0xffff) | (dy << 16)
     const double *tinvd;      // V: 1/r of each hop vector (binary64)
+    const double *tinv_r2_64; // cubic lattice: 1/r by r^2 = fx^2+fy^2+fz^2, 3 (L/2)^2 + 1
+    const float *tinv_r2_32;  // entries (the folded table's values); null on the square one
     const unsigned short *guide; // kGuide entries
     // state (device)
     void *eps;                // N binary64 (CG_FP64) or binary32 (CG_FP32)

@@ -117,6 +117,12 @@ struct Tables {
     std::vector<unsigned short> guide;
     std::vector<uint32_t> split;      // hi | lo << 16 of each 1/r entry: BF16 of 1/r on the
                                       // square lattice, binary16 of 2^10 / r on the cubic one
+    // cubic lattice: the folded table's values indexed by r^2 = fx^2 + fy^2 +
+    // fz^2 (3 (L/2)^2 + 1 entries; 0 where r^2 is no sum of three squares)
+    std::vector<double> r2_64;
+    std::vector<float> r2_32;
+    double *d_r2_64 = nullptr;
+    float *d_r2_32 = nullptr;
     unsigned short *d_guide = nullptr;
     uint32_t *d_split = nullptr;
     double *d_t64 = nullptr;
@@ -140,6 +146,21 @@ int build_tables(Tables &t, int L, double xi, int r_max, int dim)
                         ? 0.0 : 1.0 / std::sqrt((double)(fx * fx + fy * fy + fz * fz));
     t.t32.resize(t.t64.size());
     for (size_t k = 0; k < t.t64.size(); ++k) t.t32[k] = (float)t.t64[k];
+    if (dim == 3) {
+        // 1/r depends on r^2 alone, so each r^2 takes the folded entry's
+        // bits (every offset with that r^2 holds the same value)
+        const int h = L / 2;
+        t.r2_64.assign((size_t)3 * h * h + 1, 0.0);
+        t.r2_32.assign(t.r2_64.size(), 0.0f);
+        for (int fz = 0; fz < H1; ++fz)
+            for (int fy = 0; fy < H1; ++fy)
+                for (int fx = 0; fx < H1; ++fx) {
+                    const size_t k = ((size_t)fz * H1 + fy) * H1 + fx;
+                    const int q = fx * fx + fy * fy + fz * fz;
+                    t.r2_64[q] = t.t64[k];
+                    t.r2_32[q] = t.t32[k];
+                }
+    }
     // two-term split of 1/r for the tensor-core refresh.  Square lattice:
     // hi = bf16(T), lo = bf16(T - hi), so T - hi - lo is below 2^-16 of T.
     // Cubic lattice, where sum_t G_st^2 is about eight times larger and that
@@ -240,6 +261,7 @@ struct Rep {
     int *d_guide = nullptr;           // kRandomGuide ints per site
     uint2 *d_rec = nullptr;           // running weight and partner of each pair
     double2 *d_rgx = nullptr;         // 1/r and E dx of each pair
+    bool pair = false;                // the handle proposes two-electron hops
 };
 
 struct Group {
@@ -401,11 +423,15 @@ double gamma_of(const Rep &r, const cg_opts &o)
     return Tp ? g / (1.0 - (double)Tp * 0x1p-32) : g;
 }
 
+// The single-hop cluster kernel on the cubic lattice keeps 1/r indexed by
+// r^2 (3 (L/2)^2 + 1 entries) instead of the (L/2+1)^3 folded table.
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
     if (r.random) return random_smem_bytes(r.N, cluster);
     const int rb = precision == CG_FP64 ? 8 : 4;
-    return smem_layout(r.N / cluster, (int)r.tab->t64.size(), r.tab->V, r.words, rb).total;
+    const bool r2 = dim_of(r.d) == 3 && cluster > 1 && !r.pair;
+    const int ntab = r2 ? (int)r.tab->r2_64.size() : (int)r.tab->t64.size();
+    return smem_layout(r.N / cluster, ntab, r.tab->V, r.words, rb).total;
 }
 
 // L must be a multiple of this for a cluster of c CTAs: c on the cubic
@@ -469,6 +495,7 @@ void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
     dr.pair_T = pair_threshold(o);
     dr.pair_R = dr.pair_T ? o.pair_rmax : 0;
     dr.tinv64 = t.d_t64; dr.tinv32 = t.d_t32; dr.thr = t.d_thr; dr.disp = t.d_disp;
+    dr.tinv_r2_64 = t.d_r2_64; dr.tinv_r2_32 = t.d_r2_32;
     dr.tinvd = t.d_tinvd;
     dr.guide = t.d_guide;
     dr.C0 = t.C0;
@@ -792,6 +819,10 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
                     }
             total += up(tab * 8) + up(tab * 4) + up(V * 4) + up(V * 4) + up(V * 8) +
                      up((size_t)kGuide * 2) + up(tab * 4);
+            if (dim_of(d) == 3) {
+                const size_t n2 = 3 * (size_t)(d.L / 2) * (d.L / 2) + 1;
+                total += up(n2 * 8) + up(n2 * 4);
+            }
         }
     }
     return total + tc_total;
@@ -877,6 +908,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         r.N = sites_of(r.d);
         r.words = (r.N + 31) / 32;
         r.random = r.d.sites == CG_SITES_RANDOM;
+        r.pair = o.pair_frac > 0.0;
         if (r.random && build_random(r) != CG_OK) {
             destroy_partial();
             return nullptr;
@@ -912,6 +944,12 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             dalloc(h.get(), (void **)&t->d_tinvd, t->tinvd.size() * 8) ||
             dalloc(h.get(), (void **)&t->d_guide, t->guide.size() * 2) ||
             dalloc(h.get(), (void **)&t->d_split, t->split.size() * 4)) { destroy_partial(); return nullptr; }
+        if (t->dim == 3) {
+            if (dalloc(h.get(), (void **)&t->d_r2_64, t->r2_64.size() * 8) ||
+                dalloc(h.get(), (void **)&t->d_r2_32, t->r2_32.size() * 4)) { destroy_partial(); return nullptr; }
+            cudaMemcpyAsync(t->d_r2_64, t->r2_64.data(), t->r2_64.size() * 8, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(t->d_r2_32, t->r2_32.data(), t->r2_32.size() * 4, cudaMemcpyHostToDevice, h->st);
+        }
         cudaMemcpyAsync(t->d_split, t->split.data(), t->split.size() * 4, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_t64, t->t64.data(), t->t64.size() * 8, cudaMemcpyHostToDevice, h->st);
         cudaMemcpyAsync(t->d_t32, t->t32.data(), t->t32.size() * 4, cudaMemcpyHostToDevice, h->st);

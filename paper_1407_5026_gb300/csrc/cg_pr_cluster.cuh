@@ -31,6 +31,12 @@
 // in turn.
 // The wall-clock limit of a hop is decided by rank 0 and published in its
 // exchange slot, so every exit decision is uniform over the cluster.
+// On the cubic lattice with single hops the update reads 1/r indexed by
+// r^2 = fx^2 + fy^2 + fz^2 of the folded offsets (3 (L/2)^2 + 1 entries, the
+// folded table's own values: 1/r depends on r^2 alone) instead of the
+// (L/2+1)^3 folded table: 12 KiB instead of 144 KiB at L = 64 in binary32,
+// where the folded table fits beside no share of eps.  The labels never read
+// either table (their 1/r comes from the per-vector tables).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -95,6 +101,8 @@ template <typename Real, int kThreads, bool kPow2, int kDim, bool kPair = false>
 __global__ void __launch_bounds__(kThreads, 1)
 pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
+    // the update's 1/r indexed by r^2 (cubic lattice, single hops)
+    constexpr bool kR2 = kDim == 3 && !kPair;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
@@ -131,7 +139,7 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
     const int Bq = rows_local >> 1;
     const unsigned magicB =
         (kDim == 3 || Bq < 2) ? 0u : (unsigned)(4294967296ull / (unsigned)Bq + 1ull);
-    const int ntab = kDim == 3 ? H1 * H1 * H1 : H1 * H1;
+    const int ntab = kR2 ? 3 * (L >> 1) * (L >> 1) + 1 : kDim == 3 ? H1 * H1 * H1 : H1 * H1;
 
     const SmemLayout lay = smem_layout(N_local, ntab, V, words, (int)sizeof(Real));
     Shared S;
@@ -160,9 +168,10 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 eps[l] = eps_g[(size_t)cluster_global_row(yl, rank, L >> 1, Bq) * L + x];
             }
         }
-        const Real *tab_g = (sizeof(Real) == 8)
-                                ? reinterpret_cast<const Real *>(Rg.tinv64)
-                                : reinterpret_cast<const Real *>(Rg.tinv32);
+        const Real *tab_g =
+            (sizeof(Real) == 8)
+                ? reinterpret_cast<const Real *>(kR2 ? Rg.tinv_r2_64 : Rg.tinv64)
+                : reinterpret_cast<const Real *>(kR2 ? Rg.tinv_r2_32 : Rg.tinv32);
         Real *tab_s = reinterpret_cast<Real *>(S.tinv);
         for (int l = tid; l < ntab; l += kThreads) tab_s[l] = tab_g[l];
         for (int l = tid; l < words; l += kThreads) S.occ[l] = Rg.occ[l];
@@ -465,13 +474,26 @@ pr_cluster(const DevReplica *__restrict__ reps, const int *__restrict__ index, R
                 yj = (int)qj - zj * L;
             }
             const int fxj = fold_axis(ux - xj, L), fxi = fold_axis(ux - xi, L);
-            for (int r = uy0; r < rows_local * L; r += rows_per_pass) {
-                const int zl = kPow2 ? (r >> log2L) : (int)__umulhi((unsigned)r, magic);
-                const int y = r - zl * L, z = row0 + zl;
-                const int oj = (fold_axis(z - zj, L) * H1 + fold_axis(y - yj, L)) * H1 + fxj;
-                const int oi = (fold_axis(z - zi, L) * H1 + fold_axis(y - yi, L)) * H1 + fxi;
-                Real *e = eps + r * L + ux;
-                *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[oj], tinv[oi]));
+            if constexpr (kR2) {
+                const int qj = fxj * fxj, qi = fxi * fxi;
+                for (int r = uy0; r < rows_local * L; r += rows_per_pass) {
+                    const int zl = kPow2 ? (r >> log2L) : (int)__umulhi((unsigned)r, magic);
+                    const int y = r - zl * L, z = row0 + zl;
+                    const int fzj = fold_axis(z - zj, L), fyj = fold_axis(y - yj, L);
+                    const int fzi = fold_axis(z - zi, L), fyi = fold_axis(y - yi, L);
+                    Real *e = eps + r * L + ux;
+                    *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[qj + fyj * fyj + fzj * fzj],
+                                                             tinv[qi + fyi * fyi + fzi * fzi]));
+                }
+            } else {
+                for (int r = uy0; r < rows_local * L; r += rows_per_pass) {
+                    const int zl = kPow2 ? (r >> log2L) : (int)__umulhi((unsigned)r, magic);
+                    const int y = r - zl * L, z = row0 + zl;
+                    const int oj = (fold_axis(z - zj, L) * H1 + fold_axis(y - yj, L)) * H1 + fxj;
+                    const int oi = (fold_axis(z - zi, L) * H1 + fold_axis(y - yi, L)) * H1 + fxi;
+                    Real *e = eps + r * L + ux;
+                    *e = Prec<Real>::add(*e, Prec<Real>::sub(tinv[oj], tinv[oi]));
+                }
             }
             }
         } else if (kDim == 2 && !a.toy && tid < qactive) {

@@ -10,8 +10,10 @@ stochastic clock of step 3c is exact in 3D too; in binary32 (refreshed in
 binary64) eps stays within 1e-4 of its definition; the split-BF16 tensor-core
 refresh on cubic tables (N = L^3 a multiple of 128) gives eps within 5e-5 of
 its definition, alone and inside runs; on thread-block clusters (eps split
-by z-planes) binary64 stays bit-exact and binary32 lattices beyond one CTA
-(L = 40, 48) refresh within 1e-4.
+by z-planes, 1/r of the update indexed by r^2) binary64 stays bit-exact and
+binary32 lattices beyond one CTA (L = 40, 48) refresh within 1e-4; the 64^3
+lattice runs in binary32 on 8-CTA clusters, its eps within 1e-4 of the
+definition, its hops valid.
 """
 import numpy as np
 import pytest
@@ -233,3 +235,55 @@ def test_cubic_binary32_beyond_one_cta(B, L, R, cluster):
             assert o["refreshes"] == 3 and o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("R", [2, 8])
+def test_cubic_l64_binary32_without_the_table(B, R):
+    # L = 64 (N = 262144): the (L/2+1)^3 folded table (144 KiB) fits beside
+    # no share of eps, and the cluster kernel's update reads 1/r indexed by
+    # r^2 (12 KiB), so the replicas run on 8-CTA clusters (128 KiB of eps
+    # each).  The set-up eps (binary64 sums, the table read from global
+    # memory) equals the definition; every logged hop moves an electron from
+    # an occupied site to an empty one within r_max; eps stays within 1e-4
+    # of its definition, refreshed in binary64 (2 replicas) or on the tensor
+    # cores (8 replicas).  (The r^2 table is the cubic cluster kernel's for
+    # every L: the binary64 cluster trajectories above check it hop for hop.)
+    L, r_max = 64, 3
+    reps = [_cubic(L=L, r_max=r_max, T=0.05, seed=s, replica=s) for s in range(R)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=2048, torch_memory=False)
+    try:
+        assert B.cg_group_shape(s.h, 0)["cluster"] == 8
+        n0, eps0, phi0, _ = s.state(R - 1)
+        assert np.abs(eps0 - ref.site_energies_fft3(n0, phi0, 0.5, L)).max() <= 1e-5
+        rc, log = s.run_logged(2 * 2048 + 100, 1024)
+        assert rc == B.CG_OK
+        for k in (0, R - 1):
+            n, eps, phi, _ = s.state(k)
+            assert np.abs(eps - ref.site_energies_fft3(n, phi, 0.5, L)).max() <= 1e-4
+            o = s.observables(k)
+            assert o["refreshes"] == 2 and o["max_eps_err_last_refresh"] <= 1e-4
+        # replay replica 0's hops on its initial occupation (a fresh handle
+        # rebuilds the same initial state)
+        t = B.System(reps[:1], precision=B.CG_FP32, torch_memory=False)
+        try:
+            occ = t.state(0)[0].astype(np.int8).copy()
+        finally:
+            t.close()
+        for e in log[0]:
+            i, j = int(e["i"]), int(e["j"])
+            assert occ[i] == 1 and occ[j] == 0
+            d = [((j // L**a) % L - (i // L**a) % L + L // 2) % L - L // 2 for a in range(3)]
+            assert 0 < d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= r_max * r_max
+            occ[i], occ[j] = 0, 1
+        np.testing.assert_array_equal(occ, s.state(0)[0])
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("kw", [dict(precision=0), dict(precision=1, pair_frac=0.2,
+                                                                pair_rmax=2)])
+def test_cubic_l64_refuses_what_does_not_fit(B, kw):
+    # binary64 eps of the 64^3 lattice (2 MiB) outgrows 8 CTAs, and the
+    # table-free kernel takes single hops only
+    with pytest.raises(B.CgError, match="does not fit"):
+        B.System([_cubic(L=64, r_max=3)], torch_memory=False, **kw)
