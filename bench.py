@@ -701,8 +701,9 @@ def shape_of(B, h, g, tuned):
 def cluster_roofline(reps, hops_per_s, cluster, smem_peak, sms, precision):
     """The eps update's algorithmic shared-memory bytes per second (16 N B
     per hop in binary32, 32 N in binary64) against the measured
-    shared-memory peak of the SMs the launch occupies (one CTA per SM)."""
-    N = reps[0]["L"] ** 2
+    shared-memory peak of the SMs the launch occupies (one CTA per SM); N =
+    L^2 on the square lattice, L^3 on the cubic one."""
+    N = reps[0]["L"] ** (3 if reps[0].get("dim") == 3 else 2)
     per_hop = (16 if precision == "fp32" else 32) * N
     used = min(sms, len(reps) * cluster)
     peak = smem_peak * used / sms
@@ -733,7 +734,8 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     L=256 whose eps is split over a thread-block cluster (refresh every 4096
     hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
     tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
-    4-CTA clusters (eps split by z-planes), 304 replicas of L=64 with and
+    4-CTA clusters (eps split by z-planes; refresh every 8192 hops, as for
+    64^3), 304 replicas of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair), 19
     replicas of the 64^3 lattice on 8-CTA clusters (1/r of the update indexed
     by r^2), and
@@ -753,11 +755,16 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
             # autotuner's trial launches (profiling with --config only)
             ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False, 4, False),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False, 0, True),
-            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False, 0, True),
+            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48, refresh_every=8192), 2048, 8192,
+             0, False, 0, True),
+            # 8 replicas of 32^3 on one CTA each and on forced 4-CTA clusters
+            # (small cases for profiling the cubic cluster kernel; --config only)
+            ("cubic_L32_T0.05_R8", W.cubic(R=8), 4096, 2048, 0, False, 0, False),
+            ("cubic_L32_T0.05_R8_cluster4", W.cubic(R=8), 4096, 2048, 0, False, 4, False),
             # 19 replicas of 64^3 on 8-CTA clusters (152 SMs), the update
             # reading 1/r by r^2 (the folded table fits beside no eps share)
-            ("cubic_L64_T0.05_R19_cluster8", W.cubic(R=19, L=64), 2048, 4096, 0, False, 0,
-             True),
+            ("cubic_L64_T0.05_R19_cluster8", W.cubic(R=19, L=64, refresh_every=8192), 2048, 8192,
+             0, False, 0, True),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False, 0, True),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False, 0, True),
             ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False, 0, True),

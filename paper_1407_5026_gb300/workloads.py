@@ -124,15 +124,17 @@ def pairs(R: int = 304, pair_frac: float = 0.2, hops: int = 1_000_000) -> Worklo
                     extra={"pair_frac": pair_frac, "pair_rmax": 4})
 
 
-def cubic(R: int = 152, L: int = 32, hops: int = 1_000_000) -> Workload:
+def cubic(R: int = 152, L: int = 32, hops: int = 1_000_000,
+          refresh_every: int = 1024) -> Workload:
     """The cubic lattice the paper's conclusions name as the next extension:
     L x L x L sites (N = 32768 for L=32), nu=1/2, phi ~ U[-0.5, 0.5], xi=1,
     hops inside the ball |d| <= 3 (122 vectors), T=0.05, E=0.01, one replica
-    per SM, FP32 eps with a binary64 refresh every 1024 hops."""
+    per SM, FP32 eps with a refresh from scratch every `refresh_every` hops
+    (a refresh costs N^2 pair terms: larger lattices refresh less often)."""
     reps = tuple(Replica(L=L, nu=0.5, W=1.0, xi=1.0, r_max=3, T=0.05, E=0.01,
                          seed=s, replica=s, dim=3) for s in range(R))
     return Workload(f"cubic_L{L}_T0.05_R{R}", reps, M=4096, hops=hops,
-                    precision="fp32", refresh_every=1024)
+                    precision="fp32", refresh_every=refresh_every)
 
 
 def random_sites(R: int = 152, L: int = 64, hops: int = 1_000_000,
