@@ -147,8 +147,9 @@ def workload_config(args, R):
             "M": (args.M if args.no_tune
                   else "autotuned from {1024, 4096, 16384, 65536} (relaxing with "
                        f"{args.M})"),
-            "refresh": "every 1024 hops: split-BF16 tcgen05 contraction over the "
-                       "replicas, binary64 reduction",
+            "refresh": "every 1024 hops: eps from its definition by the convolution "
+                       "theorem (binary32 radix-2 FFTs, two replicas per complex "
+                       "transform, times DFT(1/r); phi added in binary64)",
             "l2": "256 MB buffer zeroed between steps (outside the timed events)",
             "state": f"chains relaxed {args.relax_steps * HOPS_PER_STEP} hops from "
                      f"their random start, then {args.warmup} warm-up steps"}
@@ -478,16 +479,15 @@ def run_ours(args):
         # over the share of the CTAs' cycles spent in label rounds
         "rejection_roofline": rejection_roofline(evaluated, sum(run_ms) * 1e-3, cyc_rej,
                                                  cyc_upd, philox_peak),
-        # the refresh as a whole (error reset, S image, contraction,
-        # reduction) against the measured sustained BF16 tensor peak: the
-        # contraction is 2 (hi, lo) x 2 N^2 flop per replica
+        # the refresh as a whole (error reset and the three FFT passes)
+        # against the measured HBM copy rate
         "refresh_roofline": refresh_roofline(N, R, statistics.mean(ref_ms)),
         "phase_split": {"refresh_ms_per_step": statistics.mean(ref_ms),
                         "run_ms_per_step": statistics.mean(run_ms),
                         "update_cycles_frac": cyc_upd / max(1, cyc_upd + cyc_rej),
                         "max_eps_err_last_refresh": max_err},
-        # per step: one persistent launch per L, then the refresh: error reset,
-        # S image, contraction and reduction (tensor-core batch)
+        # per step: one persistent launch per L, then the refresh: error reset
+        # and three FFT passes
         "gpu_launches": args.steps * (1 + 4),
         "clocks": clk,
         "peaks_measured": {"smem_rmw32_GBps": smem_peak / 1e9, "dadd_per_s": dadd_peak,
@@ -675,20 +675,27 @@ def rejection_roofline(evaluated, run_s, cyc_rej, cyc_upd, philox_peak):
 
 
 def refresh_roofline(N, R, ms):
+    """The FFT refresh's bytes per replica and refresh: the occupation bits
+    (N/8), four sweeps of its half of the complex transform buffer (4 x 4 N:
+    written by the first pass, read and written by the second, read by the
+    third), half of DFT(g)/N (2 N, one read per replica pair), phi (8 N) and
+    eps read and written (8 N), against the measured HBM copy rate."""
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
     except (OSError, ValueError):
         pass
-    if "bf16_tflops_sustained" in peaks:
-        peak, src = float(peaks["bf16_tflops_sustained"]), "of measured (MEASURED_PEAKS.json, sustained BF16)"
+    if "hbm_gbs" in peaks:
+        peak, src = float(peaks["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
     else:
-        peak, src = 1700.0, "of fallback (1.7 PFLOP/s sustained BF16)"
-    achieved = 4.0 * N * N * R / (ms * 1e-3) / 1e12
-    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_source": src, "kernel": "refresh_tc_kernel (+ pack, reduce)",
-            "flop_per_refresh": 4.0 * N * N * R}
+        peak, src = 6800.0, "of fallback (6.8 TB/s)"
+    per_replica = N / 8.0 + 16.0 * N + 2.0 * N + 8.0 * N + 8.0 * N
+    achieved = per_replica * R / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": src,
+            "kernel": "fft_pass_kernel x 3 (+ error reset)",
+            "bytes_per_refresh": per_replica * R}
 
 
 def shape_of(B, h, g, tuned):
@@ -729,13 +736,13 @@ def random_roofline(reps, hops_per_s):
 def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
-    replayed as a CUDA graph, CTA size and M from the autotuner, split-BF16
-    tensor-core refresh per same-L group every 1024 hops), 16 replicas of
-    L=256 whose eps is split over a thread-block cluster (refresh every 4096
-    hops), 152 replicas of the 32 x 32 x 32 cubic lattice (binary16-split
-    tensor-core refresh every 1024 hops), 38 replicas of the 48^3 lattice on
-    4-CTA clusters (eps split by z-planes; refresh every 8192 hops, as for
-    64^3), 304 replicas of L=64 with and
+    replayed as a CUDA graph, CTA size and M from the autotuner, a refresh
+    per same-L group every 1024 hops: FFT for L = 32, 64, split-BF16 tensor
+    cores for L = 48, 96), 16 replicas of L=256 whose eps is split over a
+    thread-block cluster (refresh every 4096 hops), 152 replicas of the
+    32 x 32 x 32 cubic lattice (FFT refresh every 1024 hops), 38 replicas of
+    the 48^3 lattice on 4-CTA clusters (eps split by z-planes; binary16-split
+    tensor-core refresh), 304 replicas of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair), 19
     replicas of the 64^3 lattice on 8-CTA clusters (1/r of the update indexed
     by r^2), and
@@ -755,16 +762,15 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
             # autotuner's trial launches (profiling with --config only)
             ("L256_T0.02_R16_cluster4", W.l256(), 65536, 4096, 0, False, 4, False),
             ("cubic_L32_T0.05_R152", W.cubic(), 4096, 4096, 0, False, 0, True),
-            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48, refresh_every=8192), 2048, 8192,
-             0, False, 0, True),
+            ("cubic_L48_T0.05_R38_cluster4", W.cubic(R=38, L=48), 2048, 2048, 0, False, 0, True),
             # 8 replicas of 32^3 on one CTA each and on forced 4-CTA clusters
             # (small cases for profiling the cubic cluster kernel; --config only)
             ("cubic_L32_T0.05_R8", W.cubic(R=8), 4096, 2048, 0, False, 0, False),
             ("cubic_L32_T0.05_R8_cluster4", W.cubic(R=8), 4096, 2048, 0, False, 4, False),
             # 19 replicas of 64^3 on 8-CTA clusters (152 SMs), the update
             # reading 1/r by r^2 (the folded table fits beside no eps share)
-            ("cubic_L64_T0.05_R19_cluster8", W.cubic(R=19, L=64, refresh_every=8192), 2048, 8192,
-             0, False, 0, True),
+            ("cubic_L64_T0.05_R19_cluster8", W.cubic(R=19, L=64), 2048, 4096, 0, False, 0,
+             True),
             ("pairs_L64_T0.05_R304_p0.2", W.pairs(), 4096, 4096, 0, False, 0, True),
             ("single_L64_T0.05_R304", W.pairs(pair_frac=0.0), 4096, 4096, 0, False, 0, True),
             ("random_L64_T0.05_R152_fp64", W.random_sites(), 2048, 2048, 0, False, 0, True),

@@ -56,6 +56,9 @@ extern "C" {
 #define CG_REFRESH_FP64 1  /* direct G (n - nu) in binary64                   */
 #define CG_REFRESH_BF16X2 2 /* split-BF16 hi+lo tensor-core contraction over
                                the replicas of one L                          */
+#define CG_REFRESH_FFT 3   /* the convolution theorem: binary32 FFTs of
+                               n - nu, two replicas per complex transform,
+                               times DFT(1/r); power-of-two L              */
 
 typedef struct cg_handle cg_handle;
 
@@ -301,9 +304,17 @@ int cg_observables(cg_handle *h, int replica, cg_obs *out);
  * recompute it in the serial summation order (bit-identical to a fresh
  * start).  CG_FP32 handles record the largest |eps_fp32 - eps_new|
  * (cg_obs.max_eps_err_last_refresh) and store eps_new rounded to binary32,
- * where eps_new comes from one of two paths:
- *   - a group of replicas of one L whose N is a multiple of 128 (and
- *     CG_REFRESH_AUTO or CG_REFRESH_BF16X2): the tensor-core contraction, the
+ * where eps_new comes from one of three paths:
+ *   - a group of replicas of one power-of-two L (CG_REFRESH_AUTO or
+ *     CG_REFRESH_FFT): the convolution theorem, eps - phi = IDFT(DFT(n - nu)
+ *     DFT(1/r)) on the periodic lattice, radix-2 transforms in binary32 with
+ *     two replicas per complex transform (DFT(1/r) is real), DFT(1/r) and the
+ *     twiddles from binary64 on the host, phi added in binary64 (error below
+ *     2e-5 up to L = 256 square and L = 64 cubic, measured against the
+ *     definition);
+ *   - otherwise, a group of replicas of one L whose N is a multiple of 128
+ *     (CG_REFRESH_AUTO with at least 8 replicas, or CG_REFRESH_BF16X2): the
+ *     tensor-core contraction, the
  *     1/r table split into two BF16 terms (binary16 terms of 2^10/r on the
  *     cubic lattice), the +-1 occupations exact in that format, products
  *     accumulated in binary32 by the tensor cores over K ranges of at most

@@ -24,7 +24,7 @@ CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_ESTUCK, CG_ESTATE = 0, -1
 CG_FP64, CG_FP32 = 0, 1
 CG_TIME_DETERMINISTIC, CG_TIME_GAUSSIAN = 0, 1
 CG_SITES_LATTICE, CG_SITES_RANDOM = 0, 1
-CG_REFRESH_AUTO, CG_REFRESH_FP64, CG_REFRESH_BF16X2 = 0, 1, 2
+CG_REFRESH_AUTO, CG_REFRESH_FP64, CG_REFRESH_BF16X2, CG_REFRESH_FFT = 0, 1, 2, 3
 
 EXPORTED = [
     "cg_create", "cg_create_batch", "cg_workspace_bytes", "cg_create_batch_ws",

@@ -24,7 +24,8 @@ SOURCES = ["cg_lib.cu", "cg_pr_kernel.cu", "cg_pr_kernel3d.cu", "cg_pr_kernel_pa
            "cg_pr_kernel_pair_time.cu", "cg_pr_cluster_pair.cu", "cg_pr_kernel3d_pair.cu",
            "cg_pr_random.cu", "cg_pr_random_cluster.cu",
            "cg_aux_kernels.cu",
-           "cg_microbench.cu", "cg_refresh_tc.cu", "cg_refresh_static.cu", "cg_pr_cluster.cu"]
+           "cg_microbench.cu", "cg_refresh_tc.cu", "cg_refresh_static.cu", "cg_pr_cluster.cu",
+           "cg_refresh_fft.cu"]
 HEADERS = ["cg_internal.h", "cg_device.cuh", "cg_pr_common.cuh", "cg_pr_persistent.cuh",
            "cg_pr_cluster.cuh", "cg_pr_random.cuh"]
 

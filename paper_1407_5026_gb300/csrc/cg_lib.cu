@@ -16,6 +16,7 @@
 //     (s, 2, 0xFFFFFFFF, replica), s), the first nu N occupied.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -123,6 +124,12 @@ struct Tables {
     std::vector<float> r2_32;
     double *d_r2_64 = nullptr;
     float *d_r2_32 = nullptr;
+    // the FFT refresh (binary32 handles, power-of-two L): DFT(g) / N of the
+    // minimum-image 1/r (real: g is even) and the twiddles exp(-2 pi i k/L)
+    std::vector<float> ghat;
+    std::vector<float2> tw;
+    float *d_ghat = nullptr;
+    float2 *d_tw = nullptr;
     unsigned short *d_guide = nullptr;
     uint32_t *d_split = nullptr;
     double *d_t64 = nullptr;
@@ -276,6 +283,9 @@ struct Group {
     bool tc = false;                 // refresh on the tensor cores
     unsigned char *d_img = nullptr;  // S image scratch of the tensor-core refresh
     int *d_err = nullptr;            // its error word
+    bool fft = false;                // refresh by the convolution theorem
+    float2 *d_fft = nullptr;         // its transform buffer (a complex value per
+                                     // site per replica pair)
 };
 
 // dynamic shared memory the contraction may take: the 227 KiB per-CTA opt-in
@@ -286,6 +296,69 @@ constexpr int kTcSmemLimit = 227 * 1024 - 1024;
 // refreshes on the tensor cores: the site count must be a multiple of 128 and
 // the contraction's stages plus the folded table must fit one CTA's shared
 // memory.
+// In-place radix-2 DFT (exponent -2 pi i j k / n) of n = 2^m complex values
+// at stride `stride`, binary64, for the refresh's host-side table.
+void host_fft(std::complex<double> *x, int n, size_t stride)
+{
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[(size_t)i * stride], x[(size_t)j * stride]);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * M_PI / (double)len;
+        for (int i = 0; i < n; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+                std::complex<double> &a = x[(size_t)(i + k) * stride];
+                std::complex<double> &b = x[(size_t)(i + k + len / 2) * stride];
+                const std::complex<double> u = a, v = b * w;
+                a = u + v;
+                b = u - v;
+            }
+    }
+}
+
+// DFT(g) / N of the minimum-image 1/r on the L^dim torus (g(0) = 0), rounded
+// to binary32, and the twiddles of the device transforms.
+void build_fft_tables(Tables &t)
+{
+    const int L = t.L, H1 = t.H1;
+    const size_t N = t.dim == 3 ? (size_t)L * L * L : (size_t)L * L;
+    std::vector<std::complex<double>> g(N);
+    const int Lz = t.dim == 3 ? L : 1;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                const int fz = t.dim == 3 ? std::min(z, L - z) : 0;
+                const int fy = std::min(y, L - y), fx = std::min(x, L - x);
+                g[((size_t)z * L + y) * L + x] = t.t64[((size_t)fz * H1 + fy) * H1 + fx];
+            }
+    const size_t lines = N / L;
+    for (size_t r = 0; r < lines; ++r) host_fft(g.data() + r * L, L, 1);          // x
+    for (int z = 0; z < Lz; ++z)
+        for (int x = 0; x < L; ++x) host_fft(g.data() + (size_t)z * L * L + x, L, L);   // y
+    if (t.dim == 3)
+        for (size_t c = 0; c < (size_t)L * L; ++c) host_fft(g.data() + c, L, (size_t)L * L);
+    t.ghat.resize(N);
+    for (size_t k = 0; k < N; ++k) t.ghat[k] = (float)(g[k].real() / (double)N);
+    t.tw.resize(L / 2);
+    for (int k = 0; k < L / 2; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)L;
+        t.tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+}
+
+// Whether a group of binary32 replicas of side L refreshes by the FFT:
+// power-of-two L (CG_REFRESH_AUTO or CG_REFRESH_FFT).
+bool group_uses_fft(const cg_opts &o, int L, int dim)
+{
+    if (o.precision != CG_FP32 || L < 4 || L > 1024 || (L & (L - 1)) != 0) return false;
+    if (dim != 2 && dim != 3) return false;
+    return o.refresh_kind == CG_REFRESH_AUTO || o.refresh_kind == CG_REFRESH_FFT;
+}
+
 bool group_uses_tc(const cg_opts &o, int L, int count, int dim)
 {
     const long long N = dim == 3 ? (long long)L * L * L : (long long)L * L;
@@ -293,6 +366,7 @@ bool group_uses_tc(const cg_opts &o, int L, int count, int dim)
     const int R_pad = (std::min(count, refresh_tc_max_replicas(dim)) + 15) / 16 * 16;
     if (o.precision != CG_FP32 || N % 128 != 0) return false;
     if (refresh_tc_smem_bytes(R_pad, tab) > kTcSmemLimit) return false;
+    if (group_uses_fft(o, L, dim)) return false;
     if (o.refresh_kind == CG_REFRESH_BF16X2) return true;
     if (o.refresh_kind == CG_REFRESH_AUTO) return count >= 8;
     return false;
@@ -784,6 +858,13 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
     }
     size_t tc_total = 0;
     for (auto &g : groups)
+        if (group_uses_fft(o, std::get<0>(g), std::get<1>(g))) {
+            const size_t L = (size_t)std::get<0>(g);
+            const size_t N = std::get<1>(g) == 3 ? L * L * L : L * L;
+            tc_total += up(refresh_fft_buffer_bytes((int)N, std::get<2>(g))) + up(N * 4) +
+                        up(L / 2 * 8);
+        }
+    for (auto &g : groups)
         if (group_uses_tc(o, std::get<0>(g), std::get<2>(g), std::get<1>(g)))
             tc_total += up(tc_img_bytes(std::get<0>(g), std::get<1>(g), std::get<2>(g))) +
                         up(sizeof(int));
@@ -841,6 +922,10 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
     if (o.block_threads && (o.block_threads != 256 && o.block_threads != 384 &&
                             o.block_threads != 512 && o.block_threads != 1024)) {
         fail(CG_EINVAL, "block_threads must be 0, 256, 384, 512 or 1024");
+        return nullptr;
+    }
+    if (o.refresh_kind < CG_REFRESH_AUTO || o.refresh_kind > CG_REFRESH_FFT) {
+        fail(CG_EINVAL, "refresh_kind must be CG_REFRESH_AUTO, _FP64, _BF16X2 or _FFT");
         return nullptr;
     }
     if (o.time_mode != CG_TIME_DETERMINISTIC && o.time_mode != CG_TIME_GAUSSIAN) {
@@ -922,6 +1007,7 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
                 destroy_partial();
                 return nullptr;
             }
+            if (!r.random && group_uses_fft(o, r.d.L, dim_of(r.d))) build_fft_tables(*t);
             r.tab = t.get();
             h->tables.push_back(std::move(t));
         }
@@ -944,6 +1030,12 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             dalloc(h.get(), (void **)&t->d_tinvd, t->tinvd.size() * 8) ||
             dalloc(h.get(), (void **)&t->d_guide, t->guide.size() * 2) ||
             dalloc(h.get(), (void **)&t->d_split, t->split.size() * 4)) { destroy_partial(); return nullptr; }
+        if (!t->ghat.empty()) {
+            if (dalloc(h.get(), (void **)&t->d_ghat, t->ghat.size() * 4) ||
+                dalloc(h.get(), (void **)&t->d_tw, t->tw.size() * 8)) { destroy_partial(); return nullptr; }
+            cudaMemcpyAsync(t->d_ghat, t->ghat.data(), t->ghat.size() * 4, cudaMemcpyHostToDevice, h->st);
+            cudaMemcpyAsync(t->d_tw, t->tw.data(), t->tw.size() * 8, cudaMemcpyHostToDevice, h->st);
+        }
         if (t->dim == 3) {
             if (dalloc(h.get(), (void **)&t->d_r2_64, t->r2_64.size() * 8) ||
                 dalloc(h.get(), (void **)&t->d_r2_32, t->r2_32.size() * 4)) { destroy_partial(); return nullptr; }
@@ -1051,6 +1143,14 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             if (g.threads < 512) g.threads = 512;
             while (g.threads < g.L && g.threads < 1024) g.threads *= 2;
         }
+        g.fft = !g.random && group_uses_fft(o, g.L, g.dim);
+        if (g.fft && dalloc(h.get(), (void **)&g.d_fft,
+                            refresh_fft_buffer_bytes(dim_of(h->reps[order[g.first]].d) == 3
+                                                         ? g.L * g.L * g.L : g.L * g.L,
+                                                     g.count))) {
+            destroy_partial();
+            return nullptr;
+        }
         g.tc = group_uses_tc(o, g.L, g.count, g.dim);
         if (g.tc && (dalloc(h.get(), (void **)&g.d_img, tc_img_bytes(g.L, g.dim, g.count)) ||
                      dalloc(h.get(), (void **)&g.d_err, sizeof(int)))) {
@@ -1134,7 +1234,11 @@ int refresh_group(cg_handle *h, const Group &g, cudaStream_t st)
         return CG_OK;
     }
     CG_CUDA(launch_reset_refresh_err(h->d_reps, h->d_index + g.first, g.count, st));
-    if (g.tc) {
+    if (g.fft) {
+        const Tables &t = *h->reps[h->order[g.first]].tab;
+        CG_CUDA(launch_refresh_fft(h->d_reps, h->d_index + g.first, g.count, g.L, g.dim, t.d_ghat,
+                                   t.d_tw, g.d_fft, st));
+    } else if (g.tc) {
         const uint32_t *split = h->reps[h->order[g.first]].tab->d_split;
         const int per = refresh_tc_max_replicas(g.dim);
         for (int c0 = 0; c0 < g.count; c0 += per) {

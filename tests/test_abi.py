@@ -85,6 +85,8 @@ def test_create_rejects_bad_parameters_on_host(libcg, bad, msg):
 @pytest.mark.parametrize("bad,msg", [(dict(time_mode=2), "time_mode"),
                                      (dict(block_threads=300), "block_threads"),
                                      (dict(precision=7), "precision"),
+                                     (dict(refresh_kind=7), "refresh_kind"),
+                                     (dict(refresh_kind=-1), "refresh_kind"),
                                      (dict(pair_frac=1.0, pair_rmax=2), "pair_frac"),
                                      (dict(pair_frac=-0.1, pair_rmax=2), "pair_frac"),
                                      (dict(pair_frac=0.1, pair_rmax=0), "pair_rmax"),
@@ -109,10 +111,19 @@ def test_workspace_plan_counts_every_buffer(libcg):
     from paper_1407_5026_gb300 import binding as B
     reps = [B.desc(L=16), B.desc(L=16, seed=1), B.desc(L=32, r_max=6)]
     b64 = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP64))
-    b32 = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32))
+    b32 = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32,
+                                            refresh_kind=B.CG_REFRESH_FP64))
     # eps shrinks by 4 bytes per site in binary32 (each buffer 256-aligned)
     assert b64 - b32 == 2 * 256 * 4 + 1024 * 4
     assert b64 % 256 == 0
+    # the FFT refresh (power-of-two L, the automatic choice) adds per group a
+    # complex binary32 value per site and replica pair, DFT(g)/N (a binary32
+    # per site) and the L/2 twiddles (8 bytes each), each 256-aligned
+    fft = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32))
+    up = lambda b: (b + 255) // 256 * 256
+    extra = sum(up(((R + 1) // 2) * N * 8) + up(N * 4) + up(L // 2 * 8)
+                for L, N, R in ((16, 256, 2), (32, 1024, 1)))
+    assert fft - b32 == extra
 
 
 def test_workspace_plan_counts_the_cubic_tensor_core_scratch(libcg):

@@ -142,7 +142,7 @@ def test_cubic_stochastic_clock_bit_exact(B):
 
 def test_cubic_binary32_with_binary64_refresh(B):
     reps = [_cubic(L=16, r_max=3, T=0.05, seed=s, replica=s) for s in range(6)]
-    s = B.System(reps, precision=B.CG_FP32, refresh_every=256)
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=256, refresh_kind=B.CG_REFRESH_FP64)
     try:
         s.run(2000, 512)
         for k in range(6):
@@ -177,9 +177,10 @@ def test_cubic_tensor_core_refresh_matches_definition(B, L, R):
 
 
 def test_cubic_tensor_core_refresh_in_runs(B):
-    # the automatic choice takes the tensor cores for 16 cubic replicas
+    # 16 cubic replicas refreshed on the tensor cores inside runs
     reps = [_cubic(L=16, r_max=3, T=0.03, seed=s, replica=s) for s in range(16)]
-    s = B.System(reps, precision=B.CG_FP32, refresh_every=256)
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=256,
+                 refresh_kind=B.CG_REFRESH_BF16X2)
     try:
         s.run(4 * 256 + 50, 1024)
         for k in (0, 7, 15):
@@ -237,20 +238,22 @@ def test_cubic_binary32_beyond_one_cta(B, L, R, cluster):
         s.close()
 
 
-@pytest.mark.parametrize("R", [2, 8])
-def test_cubic_l64_binary32_without_the_table(B, R):
+@pytest.mark.parametrize("R,kind", [(2, 0), (8, 2), (3, 1)], ids=["fft", "bf16x2", "fp64"])
+def test_cubic_l64_binary32_without_the_table(B, R, kind):
     # L = 64 (N = 262144): the (L/2+1)^3 folded table (144 KiB) fits beside
     # no share of eps, and the cluster kernel's update reads 1/r indexed by
     # r^2 (12 KiB), so the replicas run on 8-CTA clusters (128 KiB of eps
     # each).  The set-up eps (binary64 sums, the table read from global
     # memory) equals the definition; every logged hop moves an electron from
     # an occupied site to an empty one within r_max; eps stays within 1e-4
-    # of its definition, refreshed in binary64 (2 replicas) or on the tensor
-    # cores (8 replicas).  (The r^2 table is the cubic cluster kernel's for
-    # every L: the binary64 cluster trajectories above check it hop for hop.)
+    # of its definition, refreshed by the FFT, on the tensor cores or in
+    # binary64 (refresh_kind 0, 2, 1).  (The r^2 table is the cubic cluster
+    # kernel's for every L: the binary64 cluster trajectories above check it
+    # hop for hop.)
     L, r_max = 64, 3
     reps = [_cubic(L=L, r_max=r_max, T=0.05, seed=s, replica=s) for s in range(R)]
-    s = B.System(reps, precision=B.CG_FP32, refresh_every=2048, torch_memory=False)
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=2048, torch_memory=False,
+                 refresh_kind=kind)
     try:
         assert B.cg_group_shape(s.h, 0)["cluster"] == 8
         n0, eps0, phi0, _ = s.state(R - 1)

@@ -77,7 +77,7 @@ def test_eps_error_stays_below_1em4(B, L, T, hops, every):
 
 def test_refresh_restores_exact_eps(B):
     p = dict(L=32, nu=0.5, W=1.0, xi=1.0, r_max=6, T=0.05, E=0.01, seed=4)
-    s = B.System([p], precision=B.CG_FP32)
+    s = B.System([p], precision=B.CG_FP32, refresh_kind=B.CG_REFRESH_FP64)
     try:
         s.run(5000, 1024)
         B.cg_refresh(s.h)
