@@ -36,9 +36,12 @@ HOPS_PER_STEP = 1024          # one refresh period
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 
 # DRAM bytes (read + write) of one launch of the persistent kernel in this
-# workload (304 replicas x 1024 hops), from the ncu capture of the relaxed
-# L=128 batch kept under profiles/; valid only while the kernel sources hash
-# to the captured version.
+# workload (304 replicas x 1024 hops), from an ncu capture of the relaxed
+# L=128 batch; valid only while the kernel sources hash to the captured
+# version and the launch takes the captured kernel instance (CTA size and
+# CTAs per replica).  M changes which labels are drawn, not the bytes (the
+# state is loaded and stored once per launch): captures at M = 4096 and
+# 16384 gave 20.748 and 20.742 MB.
 TRAFFIC_CAPTURE = {"sources_sha256_16": "f5dffe00b6b3fc12", "bytes_per_launch": 20.742e6,
                    "replicas": 304, "hops_per_replica": 1024, "M": 16384, "threads": 512,
                    "cluster": 1}
@@ -455,7 +458,7 @@ def run_ours(args):
                                  if (kernel_sources_hash() == TRAFFIC_CAPTURE["sources_sha256_16"]
                                      and R == TRAFFIC_CAPTURE["replicas"]
                                      and all(shape[k] == TRAFFIC_CAPTURE[k]
-                                             for k in ("M", "threads", "cluster")))
+                                             for k in ("threads", "cluster")))
                                  else None),
                      "traffic_unit": "DRAM bytes per launch (ncu capture)",
                      "kernel": "pr_persistent<float>",

@@ -153,23 +153,33 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
     if (kMode >= 2) dif(s, Ls, a, true);
     // ---- store ----
     double err_a = 0.0, err_b = 0.0;
-    for (int e = threadIdx.x; e < n; e += kFftThreads) {
-        int w, k;
-        if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
-        const unsigned site = site_of(axis, g, w, k, L, W);
-        const float2 v = s[w * Ls + (kMode >= 2 ? (int)bitrev((unsigned)k, a.log2L) : k)];
-        if (kMode != 4) {
-            buf[site] = v;
-        } else {
-            float *ea = reinterpret_cast<float *>(Ra.eps);
-            const double na = d_add(Ra.phi[site], (double)v.x);
-            err_a = fmax(err_a, fabs((double)ea[site] - na));
-            ea[site] = __double2float_rn(na);
+    if (kMode != 4) {
+        for (int e = threadIdx.x; e < n; e += kFftThreads) {
+            int w, k;
+            if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
+            const unsigned site = site_of(axis, g, w, k, L, W);
+            buf[site] = s[w * Ls + (kMode >= 2 ? (int)bitrev((unsigned)k, a.log2L) : k)];
+        }
+    } else {
+        // axis x: element e of the CTA is site g W L + e.  phi and eps of
+        // different sites are independent, so four elements' loads are in
+        // flight at once (restrict: eps is not phi)
+        const unsigned site0 = (unsigned)(g * W) * (unsigned)L;
+        const double *__restrict__ pa = Ra.phi + site0;
+        const double *__restrict__ pb = Rb.phi + site0;
+        float *__restrict__ ea = reinterpret_cast<float *>(Ra.eps) + site0;
+        float *__restrict__ eb = reinterpret_cast<float *>(Rb.eps) + site0;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < n; e += kFftThreads) {
+            const int w = e / L, k = e - w * L;
+            const float2 v = s[w * Ls + (int)bitrev((unsigned)k, a.log2L)];
+            const double na = d_add(pa[e], (double)v.x);
+            err_a = fmax(err_a, fabs((double)ea[e] - na));
+            ea[e] = __double2float_rn(na);
             if (two) {
-                float *eb = reinterpret_cast<float *>(Rb.eps);
-                const double nb = d_add(Rb.phi[site], (double)v.y);
-                err_b = fmax(err_b, fabs((double)eb[site] - nb));
-                eb[site] = __double2float_rn(nb);
+                const double nb = d_add(pb[e], (double)v.y);
+                err_b = fmax(err_b, fabs((double)eb[e] - nb));
+                eb[e] = __double2float_rn(nb);
             }
         }
     }
