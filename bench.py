@@ -739,13 +739,12 @@ def random_roofline(reps, hops_per_s):
 def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
-    replayed as a CUDA graph, CTA size and M from the autotuner, a refresh
-    per same-L group every 1024 hops: FFT for L = 32, 64, split-BF16 tensor
-    cores for L = 48, 96), 16 replicas of L=256 whose eps is split over a
+    replayed as a CUDA graph, CTA size and M from the autotuner, an FFT
+    refresh per same-L group every 1024 hops), 16 replicas of L=256 whose eps is split over a
     thread-block cluster (refresh every 4096 hops), 152 replicas of the
     32 x 32 x 32 cubic lattice (FFT refresh every 1024 hops), 38 replicas of
-    the 48^3 lattice on 4-CTA clusters (eps split by z-planes; binary16-split
-    tensor-core refresh), 304 replicas of L=64 with and
+    the 48^3 lattice on 4-CTA clusters (eps split by z-planes), 304 replicas
+    of L=64 with and
     without two-electron hops (a fifth of the labels proposing a pair), 19
     replicas of the 64^3 lattice on 8-CTA clusters (1/r of the update indexed
     by r^2), and

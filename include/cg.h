@@ -58,7 +58,7 @@ extern "C" {
                                the replicas of one L                          */
 #define CG_REFRESH_FFT 3   /* the convolution theorem: binary32 FFTs of
                                n - nu, two replicas per complex transform,
-                               times DFT(1/r); power-of-two L              */
+                               times DFT(1/r); L = 2^m or 3 2^m            */
 
 typedef struct cg_handle cg_handle;
 
@@ -305,10 +305,11 @@ int cg_observables(cg_handle *h, int replica, cg_obs *out);
  * start).  CG_FP32 handles record the largest |eps_fp32 - eps_new|
  * (cg_obs.max_eps_err_last_refresh) and store eps_new rounded to binary32,
  * where eps_new comes from one of three paths:
- *   - a group of replicas of one power-of-two L (CG_REFRESH_AUTO or
- *     CG_REFRESH_FFT): the convolution theorem, eps - phi = IDFT(DFT(n - nu)
- *     DFT(1/r)) on the periodic lattice, radix-2 transforms in binary32 with
- *     two replicas per complex transform (DFT(1/r) is real), DFT(1/r) and the
+ *   - a group of replicas of one L = 2^m (4 <= L <= 1024) or 3 2^m (6 <= L
+ *     <= 192) (CG_REFRESH_AUTO or CG_REFRESH_FFT): the convolution theorem,
+ *     eps - phi = IDFT(DFT(n - nu) DFT(1/r)) on the periodic lattice,
+ *     radix-2 (and one radix-3) transforms in binary32 with two replicas per
+ *     complex transform (DFT(1/r) is real), DFT(1/r) and the
  *     twiddles from binary64 on the host, phi added in binary64 (error below
  *     2e-5 up to L = 256 square and L = 64 cubic, measured against the
  *     definition);

@@ -246,13 +246,14 @@ cudaError_t launch_refresh_tc(const DevReplica *d_reps, const int *d_index, int 
                               int dim, const uint32_t *d_tab, unsigned char *d_scratch,
                               int *d_err, cudaStream_t st);
 int refresh_tc_smem_bytes(int R_pad, int tab_entries);
-// The FFT refresh of R binary32 replicas of one power-of-two L (4 <= L <=
-// 1024, dim 2 or 3; cg_refresh_fft.cu): d_ghat holds DFT(g)/N (N floats),
-// d_tw the L/2 twiddles exp(-2 pi i k / L), d_buf refresh_fft_buffer_bytes.
+// The FFT refresh of R binary32 replicas of one L = 2^m or 3 2^m (dim 2 or
+// 3; cg_refresh_fft.cu): d_ghat holds DFT(g)/N (N floats), d_tw the L
+// twiddles exp(-2 pi i k / L), d_buf refresh_fft_buffer_bytes.
 cudaError_t launch_refresh_fft(const DevReplica *d_reps, const int *d_index, int R, int L,
                                int dim, const float *d_ghat, const float2 *d_tw, float2 *d_buf,
                                cudaStream_t st);
 size_t refresh_fft_buffer_bytes(int N, int R);
+bool refresh_fft_size_ok(int L);      // L = 2^m (4..1024) or 3 2^m (6..192)
 int refresh_tc_ksplit(int N, int dim);
 int refresh_tc_max_replicas(int dim);   // replicas per launch
 size_t refresh_tc_scratch_bytes(int N, int dim, int R);

@@ -296,10 +296,25 @@ constexpr int kTcSmemLimit = 227 * 1024 - 1024;
 // refreshes on the tensor cores: the site count must be a multiple of 128 and
 // the contraction's stages plus the folded table must fit one CTA's shared
 // memory.
-// In-place radix-2 DFT (exponent -2 pi i j k / n) of n = 2^m complex values
-// at stride `stride`, binary64, for the refresh's host-side table.
+// In-place DFT (exponent -2 pi i j k / n) of n complex values at stride
+// `stride`, binary64, for the refresh's host-side table: radix 2 for n = 2^m,
+// the plain sum otherwise (n <= 192 there).
 void host_fft(std::complex<double> *x, int n, size_t stride)
 {
+    if (n & (n - 1)) {
+        std::vector<std::complex<double>> in(n), w(n);
+        for (int j = 0; j < n; ++j) {
+            in[j] = x[(size_t)j * stride];
+            const double a = -2.0 * M_PI * (double)j / (double)n;
+            w[j] = std::complex<double>(std::cos(a), std::sin(a));
+        }
+        for (int k = 0; k < n; ++k) {
+            std::complex<double> acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += in[j] * w[(size_t)j * k % n];
+            x[(size_t)k * stride] = acc;
+        }
+        return;
+    }
     for (int i = 1, j = 0; i < n; ++i) {
         int bit = n >> 1;
         for (; j & bit; bit >>= 1) j ^= bit;
@@ -343,18 +358,18 @@ void build_fft_tables(Tables &t)
         for (size_t c = 0; c < (size_t)L * L; ++c) host_fft(g.data() + c, L, (size_t)L * L);
     t.ghat.resize(N);
     for (size_t k = 0; k < N; ++k) t.ghat[k] = (float)(g[k].real() / (double)N);
-    t.tw.resize(L / 2);
-    for (int k = 0; k < L / 2; ++k) {
+    t.tw.resize(L);
+    for (int k = 0; k < L; ++k) {
         const double a = -2.0 * M_PI * (double)k / (double)L;
         t.tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
 }
 
 // Whether a group of binary32 replicas of side L refreshes by the FFT:
-// power-of-two L (CG_REFRESH_AUTO or CG_REFRESH_FFT).
+// L = 2^m or 3 2^m (CG_REFRESH_AUTO or CG_REFRESH_FFT).
 bool group_uses_fft(const cg_opts &o, int L, int dim)
 {
-    if (o.precision != CG_FP32 || L < 4 || L > 1024 || (L & (L - 1)) != 0) return false;
+    if (o.precision != CG_FP32 || !refresh_fft_size_ok(L)) return false;
     if (dim != 2 && dim != 3) return false;
     return o.refresh_kind == CG_REFRESH_AUTO || o.refresh_kind == CG_REFRESH_FFT;
 }
@@ -862,7 +877,7 @@ size_t plan_bytes(int R, const cg_replica_desc *reps, const cg_opts &o)
             const size_t L = (size_t)std::get<0>(g);
             const size_t N = std::get<1>(g) == 3 ? L * L * L : L * L;
             tc_total += up(refresh_fft_buffer_bytes((int)N, std::get<2>(g))) + up(N * 4) +
-                        up(L / 2 * 8);
+                        up(L * 8);
         }
     for (auto &g : groups)
         if (group_uses_tc(o, std::get<0>(g), std::get<2>(g), std::get<1>(g)))

@@ -6,11 +6,16 @@
 // two replicas share one complex transform: z = a + i b (a, b = n - nu of the
 // two) gives IDFT(DFT(z) . DFT(g)) = (a * g) + i (b * g).
 //
-// Power-of-two L.  Radix-2 transforms in binary32 along one axis per pass,
-// W lines per CTA in shared memory: a forward pass loads in bit-reversed
-// order and runs decimation-in-time butterflies (natural-order output); an
-// inverse pass runs decimation-in-frequency butterflies on natural-order
-// input and stores from the bit-reversed positions.  Passes:
+// L = 2^m or 3 2^m.  Transforms in binary32 along one axis per pass, W lines
+// per CTA in shared memory.  L = 2^m: a forward pass loads in bit-reversed
+// order and runs radix-2 decimation-in-time butterflies (natural-order
+// output); an inverse pass runs decimation-in-frequency butterflies on
+// natural-order input and stores from the bit-reversed positions.  L = 3M
+// (M = 2^m), both directions: with n = M n1 + n2 and k = k1 + 3 k2,
+//     X[k1 + 3 k2] = sum_n2 W_M^(n2 k2) W_L^(n2 k1) sum_n1 W_3^(n1 k1) x[M n1 + n2],
+// a radix-3 step over the thirds of the line with the twiddles W_L^(n2 k1),
+// then an M-point decimation-in-frequency transform of each third; X[k]
+// sits at (k mod 3) M + bitrev(k / 3).  Passes:
 //   square lattice: forward x (from the bitmasks) | forward y, times
 //                   DFT(g)/N, inverse y | inverse x (into eps);
 //   cubic lattice:  forward x | forward y | forward z, times DFT(g)/N,
@@ -31,10 +36,11 @@ constexpr int kFftThreads = 256;
 struct FftArgs {
     const DevReplica *reps;
     const int *index;     // the group's replicas, in group order
-    int R, L, log2L, W;   // replicas; side; lines per CTA
+    int R, L, log2L, W;   // replicas; side (log2L: of a power-of-two L); lines per CTA
+    int M3, log2M;        // L = 3 M3 (0 for a power-of-two L), log2 M3
     float2 *buf;          // ceil(R/2) x N complex values
     const float *ghat;    // N: DFT(g) / N
-    const float2 *tw;     // L/2: exp(-2 pi i k / L)
+    const float2 *tw;     // L: exp(-2 pi i k / L)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -101,6 +107,62 @@ __device__ __forceinline__ void dif(float2 *s, int Ls, const FftArgs &a, bool co
     }
 }
 
+// L = 3 M: the radix-3 step with its twiddles, then an M-point
+// decimation-in-frequency transform of each third (natural-order input;
+// X[k] at (k mod 3) M + bitrev(k / 3)).  conj: the inverse transform.
+__device__ __forceinline__ void mixed3(float2 *s, int Ls, const FftArgs &a, bool conj)
+{
+    const int M = a.M3, lm = a.log2M, nb3 = a.W * M;
+    const float c = 0.8660254037844386f;                  // sqrt(3) / 2
+    for (int b = threadIdx.x; b < nb3; b += kFftThreads) {
+        const int w = b >> lm, n2 = b & (M - 1);
+        float2 *l = s + w * Ls;
+        const float2 x0 = l[n2], x1 = l[M + n2], x2 = l[2 * M + n2];
+        const float2 s1 = make_float2(x1.x + x2.x, x1.y + x2.y);
+        const float2 d1 = make_float2(x1.x - x2.x, x1.y - x2.y);
+        const float2 t = make_float2(fmaf(-0.5f, s1.x, x0.x), fmaf(-0.5f, s1.y, x0.y));
+        const float sg = conj ? -1.0f : 1.0f;
+        float2 y1 = make_float2(fmaf(sg * c, d1.y, t.x), fmaf(-sg * c, d1.x, t.y));
+        float2 y2 = make_float2(fmaf(-sg * c, d1.y, t.x), fmaf(sg * c, d1.x, t.y));
+        float2 w1 = a.tw[n2], w2 = a.tw[2 * n2];
+        if (conj) {
+            w1.y = -w1.y;
+            w2.y = -w2.y;
+        }
+        l[n2] = make_float2(x0.x + s1.x, x0.y + s1.y);
+        l[M + n2] = cmul(y1, w1);
+        l[2 * M + n2] = cmul(y2, w2);
+    }
+    __syncthreads();
+    const int half = M >> 1, nb = a.W * 3 * half;
+    for (int st = lm - 1; st >= 0; --st) {
+        const int h = 1 << st;
+        for (int b = threadIdx.x; b < nb; b += kFftThreads) {
+            const int sub = b >> (lm - 1), j = b & (half - 1);
+            const int w = sub / 3, k1 = sub - 3 * w;
+            const int pos = j & (h - 1), i0 = ((j >> st) << (st + 1)) + pos, i1 = i0 + h;
+            float2 t = a.tw[3 * (pos << (lm - 1 - st))];        // W_M^(pos M / 2h)
+            if (conj) t.y = -t.y;
+            float2 *l = s + w * Ls + k1 * M;
+            const float2 x0 = l[i0], x1 = l[i1];
+            l[i0] = make_float2(x0.x + x1.x, x0.y + x1.y);
+            l[i1] = cmul(make_float2(x0.x - x1.x, x0.y - x1.y), t);
+        }
+        __syncthreads();
+    }
+}
+
+// Position in the line of output element k after a transform: L = 3 M
+// (either direction), or L = 2^m after the inverse (decimation in frequency).
+__device__ __forceinline__ int out_pos(int k, const FftArgs &a, bool dif_out)
+{
+    if (a.M3) {
+        const int k2 = k / 3;
+        return (k - 3 * k2) * a.M3 + (int)bitrev((unsigned)k2, a.log2M);
+    }
+    return dif_out ? (int)bitrev((unsigned)k, a.log2L) : k;
+}
+
 // One pass over W lines of one pair.  kMode: 0 forward x from the bitmasks;
 // 1 forward (buffer to buffer); 2 forward, product with DFT(g)/N, inverse
 // (the last axis); 3 inverse (buffer to buffer); 4 inverse x into eps.
@@ -119,7 +181,9 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
     const unsigned Nr = (unsigned)Ra.N;                    // L^2 or L^3
     float2 *buf = a.buf + (size_t)p * Nr;
     const int n = W * L;
-    const bool inverse_in = kMode >= 3;                    // natural-order load
+    const bool mixed = a.M3 != 0;
+    // natural-order load for the inverse and for every L = 3 M transform
+    const bool natural_in = kMode >= 3 || mixed;
     // ---- load ----
     for (int e = threadIdx.x; e < n; e += kFftThreads) {
         int w, k;
@@ -134,23 +198,43 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
         } else {
             v = buf[site];
         }
-        s[w * Ls + (inverse_in ? k : (int)bitrev((unsigned)k, a.log2L))] = v;
+        s[w * Ls + (natural_in ? k : (int)bitrev((unsigned)k, a.log2L))] = v;
     }
     if (kMode == 4 && threadIdx.x < 2) s_err[threadIdx.x] = 0ull;
     __syncthreads();
     // ---- transform ----
-    if (kMode <= 2) dit(s, Ls, a, false);
-    if (kMode == 2) {
-        for (int e = threadIdx.x; e < n; e += kFftThreads) {
-            int w, k;
-            if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
-            const float gh = a.ghat[site_of(axis, g, w, k, L, W)];
-            float2 &v = s[w * Ls + k];
-            v = make_float2(v.x * gh, v.y * gh);
+    float2 *out = s;                                       // where the result lies
+    if (!mixed) {
+        if (kMode <= 2) dit(s, Ls, a, false);
+        if (kMode == 2) {
+            for (int e = threadIdx.x; e < n; e += kFftThreads) {
+                int w, k;
+                if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
+                const float gh = a.ghat[site_of(axis, g, w, k, L, W)];
+                float2 &v = s[w * Ls + k];
+                v = make_float2(v.x * gh, v.y * gh);
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (kMode >= 2) dif(s, Ls, a, true);
+    } else {
+        mixed3(s, Ls, a, kMode >= 3);
+        if (kMode == 2) {
+            // the product in natural order into the second buffer, then the
+            // inverse transform there
+            float2 *s2 = s + W * Ls;
+            for (int e = threadIdx.x; e < n; e += kFftThreads) {
+                int w, k;
+                if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
+                const float gh = a.ghat[site_of(axis, g, w, k, L, W)];
+                const float2 v = s[w * Ls + out_pos(k, a, false)];
+                s2[w * Ls + k] = make_float2(v.x * gh, v.y * gh);
+            }
+            __syncthreads();
+            mixed3(s2, Ls, a, true);
+            out = s2;
+        }
     }
-    if (kMode >= 2) dif(s, Ls, a, true);
     // ---- store ----
     double err_a = 0.0, err_b = 0.0;
     if (kMode != 4) {
@@ -158,7 +242,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
             int w, k;
             if (axis == 0) { w = e / L; k = e - w * L; } else { k = e / W; w = e - k * W; }
             const unsigned site = site_of(axis, g, w, k, L, W);
-            buf[site] = s[w * Ls + (kMode >= 2 ? (int)bitrev((unsigned)k, a.log2L) : k)];
+            buf[site] = out[w * Ls + out_pos(k, a, kMode >= 2)];
         }
     } else {
         // axis x: element e of the CTA is site g W L + e.  phi and eps of
@@ -172,7 +256,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
 #pragma unroll 4
         for (int e = threadIdx.x; e < n; e += kFftThreads) {
             const int w = e / L, k = e - w * L;
-            const float2 v = s[w * Ls + (int)bitrev((unsigned)k, a.log2L)];
+            const float2 v = out[w * Ls + out_pos(k, a, true)];
             const double na = d_add(pa[e], (double)v.x);
             err_a = fmax(err_a, fabs((double)ea[e] - na));
             ea[e] = __double2float_rn(na);
@@ -213,7 +297,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
 template <int kMode>
 cudaError_t launch_pass(const FftArgs &a, int axis, int pairs, int groups, cudaStream_t st)
 {
-    const int smem = a.W * (a.L + 1) * (int)sizeof(float2);
+    // L = 3 M: the middle pass keeps a second buffer for the product
+    const int smem = (a.M3 && kMode == 2 ? 2 : 1) * a.W * (a.L + 1) * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<kMode>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e) return e;
@@ -223,22 +308,37 @@ cudaError_t launch_pass(const FftArgs &a, int axis, int pairs, int groups, cudaS
 
 }  // namespace
 
-// lines per CTA: 16, fewer where L is large (at most 8192 values of shared
-// memory) or small (the y and z passes take W adjacent columns)
-static int refresh_fft_lines(int L) { return L >= 16 ? (8192 / L < 16 ? 8192 / L : 16) : L; }
+// lines per CTA: the largest power of two up to 16 that divides L (the y and
+// z passes take W adjacent columns) with W L <= 8192 values of shared memory
+static int refresh_fft_lines(int L)
+{
+    int W = 16;
+    while (W > 1 && (L % W != 0 || W * L > 8192)) W >>= 1;
+    return W;
+}
+
+// The sides the FFT refresh takes: 2^m (4 <= L <= 1024) or 3 2^m (6 <= L <= 192).
+bool refresh_fft_size_ok(int L)
+{
+    if (L >= 4 && L <= 1024 && (L & (L - 1)) == 0) return true;
+    const int M = L / 3;
+    return L % 3 == 0 && L >= 6 && L <= 192 && (M & (M - 1)) == 0;
+}
 
 cudaError_t launch_refresh_fft(const DevReplica *d_reps, const int *d_index, int R, int L,
                                int dim, const float *d_ghat, const float2 *d_tw, float2 *d_buf,
                                cudaStream_t st)
 {
-    if (R < 1 || L < 4 || (L & (L - 1)) != 0 || L > 1024 || (dim != 2 && dim != 3))
-        return cudaErrorInvalidValue;
+    if (R < 1 || !refresh_fft_size_ok(L) || (dim != 2 && dim != 3)) return cudaErrorInvalidValue;
     FftArgs a;
     a.reps = d_reps;
     a.index = d_index;
     a.R = R;
     a.L = L;
-    a.log2L = __builtin_ctz((unsigned)L);
+    const bool pow2 = (L & (L - 1)) == 0;
+    a.log2L = pow2 ? __builtin_ctz((unsigned)L) : 0;
+    a.M3 = pow2 ? 0 : L / 3;
+    a.log2M = pow2 ? 0 : __builtin_ctz((unsigned)(L / 3));
     a.W = refresh_fft_lines(L);
     a.buf = d_buf;
     a.ghat = d_ghat;

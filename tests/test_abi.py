@@ -116,12 +116,12 @@ def test_workspace_plan_counts_every_buffer(libcg):
     # eps shrinks by 4 bytes per site in binary32 (each buffer 256-aligned)
     assert b64 - b32 == 2 * 256 * 4 + 1024 * 4
     assert b64 % 256 == 0
-    # the FFT refresh (power-of-two L, the automatic choice) adds per group a
-    # complex binary32 value per site and replica pair, DFT(g)/N (a binary32
-    # per site) and the L/2 twiddles (8 bytes each), each 256-aligned
+    # the FFT refresh (L = 2^m or 3 2^m, the automatic choice) adds per group
+    # a complex binary32 value per site and replica pair, DFT(g)/N (a
+    # binary32 per site) and the L twiddles (8 bytes each), each 256-aligned
     fft = B.cg_workspace_bytes(reps, B.opts(precision=B.CG_FP32))
     up = lambda b: (b + 255) // 256 * 256
-    extra = sum(up(((R + 1) // 2) * N * 8) + up(N * 4) + up(L // 2 * 8)
+    extra = sum(up(((R + 1) // 2) * N * 8) + up(N * 4) + up(L * 8)
                 for L, N, R in ((16, 256, 2), (32, 1024, 1)))
     assert fft - b32 == extra
 

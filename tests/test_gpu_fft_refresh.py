@@ -4,11 +4,11 @@ per complex binary32 transform).
 
 After hops from the random start, a refresh rebuilds eps within 2e-5 of the
 definition (evaluated in binary64 by numpy's FFT) on square and cubic
-lattices of every power-of-two side the handles take, with an even and an
+lattices of sides 2^m and 3 2^m, with an even and an
 odd number of replicas (the last one alone in its transform), reports the
 largest change and counts the refresh; it agrees with the binary64 direct
 refresh on the same states; inside runs it keeps eps within 1e-4; the
-automatic choice takes it for power-of-two L, and the other kinds stay
+automatic choice takes it for those sides, and the other kinds stay
 reachable.
 """
 import numpy as np
@@ -42,9 +42,13 @@ def _exact(n, phi, L, dim):
 
 @pytest.mark.parametrize("L,dim,R", [(4, 2, 1), (8, 2, 2), (16, 2, 3), (64, 2, 5),
                                      (128, 2, 20), (256, 2, 3), (8, 3, 3), (16, 3, 2),
-                                     (32, 3, 7), (64, 3, 2)])
+                                     (32, 3, 7), (64, 3, 2),
+                                     # L = 3 2^m: the radix-3 step, then 2^m-point
+                                     (6, 2, 1), (12, 2, 3), (48, 2, 4), (96, 2, 5),
+                                     (192, 2, 2), (6, 3, 3), (12, 3, 2), (24, 3, 3),
+                                     (48, 3, 2)])
 def test_fft_refresh_matches_definition(B, L, dim, R):
-    r_max = 1 if L == 4 else 3
+    r_max = 1 if L == 4 else 2 if L == 6 else 3
     reps = _reps(L, R, dim, r_max)
     s = B.System(reps, precision=B.CG_FP32, refresh_kind=B.CG_REFRESH_FFT, torch_memory=False)
     try:
