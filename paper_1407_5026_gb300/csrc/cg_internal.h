@@ -76,6 +76,7 @@ struct alignas(16) DevReplica {
     const int *rguide;        // 16 ints per site: kRandomGuide layout
     const uint2 *rrec;        // per pair: C mod 2^32, partner j | (C >> 32) << 31 (C <= 2^32)
     const double2 *rgx;       // per pair: 1/r, E dx (minimum-image dx, binary64)
+    int rguide_small;         // 1: every partner list holds at most 255 pairs
 };
 
 // Thread 0 at commit: record trace points whose attempt threshold the
@@ -108,6 +109,7 @@ struct RunArgs {
     int toy;                       // constant-acceptance test mode
     int time_mode;                 // CG_TIME_DETERMINISTIC or CG_TIME_GAUSSIAN
     int pair;                      // 1: two-electron hops (the kPair instances)
+    int smem_guide;                // random sites, one CTA: guide records in shared memory
     double toy_A0;
 };
 
@@ -163,10 +165,15 @@ __host__ __device__ inline int random_cluster_sites(int N, int C)
     return C <= 1 ? N : (((N + C - 1) / C + 31) / 32) * 32;
 }
 // Dynamic shared memory of a random-site CTA: its eps (binary64) and the
-// whole occupation bitmask.
-inline int random_smem_bytes(int N, int C = 1)
+// whole occupation bitmask; with guide = true (one CTA per replica, every
+// list below 256 pairs) also each site's guide record compacted to 32 bytes
+// (kRandomGuideSmem): first pair, the last running weight (33 bits), the
+// list's length (16 bits) and the 16 bucket starts as 8-bit offsets.
+constexpr int kRandomGuideSmem = 32;
+inline int random_smem_bytes(int N, int C = 1, bool guide = false)
 {
-    return cg_align16(random_cluster_sites(N, C) * 8) + cg_align16(((N + 31) / 32) * 4);
+    return cg_align16(random_cluster_sites(N, C) * 8) + cg_align16(((N + 31) / 32) * 4) +
+           (guide ? N * kRandomGuideSmem : 0);
 }
 // The random-site chain on clusters of `cluster` (2, 4 or 8) CTAs per replica
 // (cg_pr_random_cluster.cu); grid = n_reps * cluster CTAs of 256, 512 or 1024

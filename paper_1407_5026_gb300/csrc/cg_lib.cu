@@ -269,12 +269,16 @@ struct Rep {
     uint2 *d_rec = nullptr;           // running weight and partner of each pair
     double2 *d_rgx = nullptr;         // 1/r and E dx of each pair
     bool pair = false;                // the handle proposes two-electron hops
+    // random sites: every partner list holds at most 255 pairs, and on one
+    // CTA the compacted guide records fit shared memory beside eps
+    bool guide_small = false, sguide = false;
 };
 
 struct Group {
     int L = 0, first = 0, count = 0, threads = 0, smem = 0;
     int dim = 2;                     // 2: square lattice, 3: cubic lattice
     bool random = false;             // random-site replicas (pr_random)
+    bool sguide = false;             // their guide records in shared memory
     int cluster = 1;                 // CTAs per replica
     unsigned M = 4096;               // labels per round when cg_run is given M = 0
     bool tuned = false;
@@ -516,7 +520,7 @@ double gamma_of(const Rep &r, const cg_opts &o)
 // r^2 (3 (L/2)^2 + 1 entries) instead of the (L/2+1)^3 folded table.
 int persistent_smem(const Rep &r, int precision, int cluster = 1)
 {
-    if (r.random) return random_smem_bytes(r.N, cluster);
+    if (r.random) return random_smem_bytes(r.N, cluster, cluster == 1 && r.sguide);
     const int rb = precision == CG_FP64 ? 8 : 4;
     const bool r2 = dim_of(r.d) == 3 && cluster > 1 && !r.pair;
     const int ntab = r2 ? (int)r.tab->r2_64.size() : (int)r.tab->t64.size();
@@ -591,6 +595,7 @@ void fill_dev(const Rep &r, const cg_opts &o, DevReplica &dr, cg_hop *log)
     dr.eps = r.d_eps; dr.occ = r.d_occ; dr.phi = r.d_phi; dr.ctr = r.d_ctr;
     dr.log = log;
     dr.G = r.d_G; dr.rguide = r.d_guide; dr.rrec = r.d_rec; dr.rgx = r.d_rgx;
+    dr.rguide_small = r.guide_small ? 1 : 0;
 }
 
 // The device form of a random-site replica's partner lists: per site the
@@ -1013,6 +1018,12 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
             destroy_partial();
             return nullptr;
         }
+        if (r.random) {
+            int longest = 0;
+            for (int k = 0; k < r.N; ++k) longest = std::max(longest, r.roff[k + 1] - r.roff[k]);
+            r.guide_small = longest <= 255;
+            r.sguide = r.guide_small && random_smem_bytes(r.N, 1, true) <= optin - 2048;
+        }
         for (auto &t : h->tables)
             if (t->L == r.d.L && t->r_max == r.d.r_max && t->xi == r.d.xi && t->dim == dim_of(r.d))
                 r.tab = t.get();
@@ -1137,6 +1148,9 @@ cg_handle *create_impl(int R, const cg_replica_desc *reps, const cg_opts *opts, 
         g.L = h->reps[order[k]].d.L;
         g.dim = dim_of(h->reps[order[k]].d);
         g.random = h->reps[order[k]].random;
+        g.sguide = g.random;
+        for (int m = k; m < R && gkey(order[m]) == gkey(order[k]); ++m)
+            g.sguide = g.sguide && h->reps[order[m]].sguide;
         g.first = k;
         const int key = gkey(order[k]);
         int smem = 0, cluster = 1;
@@ -1297,6 +1311,7 @@ int launch_group(cg_handle *h, const Group &g, unsigned long long hops, unsigned
     a.toy_A0 = h->toy_A0;
     a.time_mode = h->opts.time_mode;
     a.pair = h->opts.pair_frac > 0.0 ? 1 : 0;
+    a.smem_guide = (g.random && g.cluster == 1 && g.sguide) ? 1 : 0;
     if (g.random && g.cluster > 1)
         CG_CUDA(launch_pr_random_cluster(h->d_reps, h->d_index + g.first, g.count, g.cluster,
                                          g.threads, g.smem, a, st));

@@ -99,11 +99,17 @@ pr_random(const DevReplica *__restrict__ reps, const int *__restrict__ index, Ru
     const float invTf = (float)(1.0 / T);
     double *eps = reinterpret_cast<double *>(smem);
     unsigned *occ = reinterpret_cast<unsigned *>(smem + cg_align16(N * 8));
+    // the compacted guide records after eps and the bitmask (every list of
+    // the group below 256 pairs and room for them), else the global records
+    uint4 *gsm = a.smem_guide
+                     ? reinterpret_cast<uint4 *>(smem + cg_align16(N * 8) + cg_align16(words * 4))
+                     : nullptr;
 
     {
         const double *eps_g = reinterpret_cast<const double *>(Rg.eps);
         for (int l = tid; l < N; l += kThreads) eps[l] = eps_g[l];
         for (int l = tid; l < words; l += kThreads) occ[l] = Rg.occ[l];
+        if (gsm) stage_guide<kThreads>(gsm, Rg, N, tid);
     }
     unsigned long long rounds = Rg.ctr->rounds;
     if (tid == 0) {
@@ -139,7 +145,8 @@ pr_random(const DevReplica *__restrict__ reps, const int *__restrict__ index, Ru
                 philox_prefix((uint32_t)rounds, (uint32_t)(rounds >> 32), rep, key0, key1);
             for (unsigned kb = 0; kb < M; kb += C) {
                 const unsigned k0 = kb + (unsigned)tid;
-                const RLabel p0 = propose_random(Rg, occ, k0, PP, key0, key1, (unsigned)N, k0 < M);
+                const RLabel p0 = propose_random(Rg, occ, k0, PP, key0, key1, (unsigned)N, k0 < M,
+                                                 gsm);
                 double dE0 = 0.0;
                 bool acc0 = false;
                 if (p0.theta) {
