@@ -101,3 +101,21 @@ def test_fft_refresh_in_runs_is_the_automatic_choice(B):
             assert o["refreshes"] == 4 and 0 < o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()
+
+
+def test_fft_refresh_at_the_bench_batch_size(B):
+    # the bench's batch: 304 replicas of L = 128 (152 complex transforms per
+    # pass); after 1024 hops and a refresh, sampled replicas' eps is within
+    # 2e-5 of the definition and every replica counted one refresh
+    reps = [dict(L=128, nu=0.5, W=2.0, xi=1.0, r_max=8, T=0.01, E=0.005, seed=s, replica=s)
+            for s in range(304)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_every=1024, block_threads=512)
+    try:
+        assert s.run(1024, 4096) == B.CG_OK
+        for k in (0, 151, 152, 303):
+            n, eps, phi, _ = s.state(k)
+            assert np.abs(eps - _exact(n, phi, 128, 2)).max() <= 2e-5
+            o = s.observables(k)
+            assert o["refreshes"] == 1 and 0 < o["max_eps_err_last_refresh"] <= 1e-4
+    finally:
+        s.close()
