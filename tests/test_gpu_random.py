@@ -3,7 +3,9 @@ serial oracle.
 
 Binary64, so every logged hop (sites, label, round, dH bit for bit), the
 final occupation, eps bit for bit and the counters equal the oracle's:
-for powers of two and other even L, with and without a field, one replica
+for powers of two and other even L, with and without a field, with the
+guide records in shared memory and (lists of 256 pairs or more) in global
+memory, one replica
 and a batch that mixes random-site and lattice replicas (graph replay
 included).  A refresh rebuilds eps from its definition bit for bit; every
 CTA size and the autotuner keep the chain; the lattice-only calls refuse.
@@ -60,6 +62,9 @@ def _check_same(s, idx, ch, log=None, olog=None):
     (16, 3, 1.0, 0.1, 0.0, 1024),
     (18, 4, 0.7, 0.2, 0.05, 333),
     (32, 6, 1.0, 0.05, 0.01, 4096),
+    # lists of about 314 pairs: the guide records stay in global memory (the
+    # shared-memory copy takes lists below 256 pairs)
+    (32, 10, 1.5, 0.05, 0.01, 4096),
 ], ids=lambda v: str(v))
 def test_binary64_random_site_trajectory_bit_exact(B, L, r_max, xi, T, E, M):
     p = dict(L=L, nu=0.5, W=1.0, xi=xi, r_max=r_max, T=T, E=E, seed=13, replica=2,
