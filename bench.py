@@ -359,6 +359,8 @@ def run_ours(args):
     smem_peak = B.cg_microbench(0, local)          # bytes/s, 32-bit RMW
     dadd_peak = B.cg_microbench(1, local)          # adds/s
     philox_peak = B.cg_microbench(3, local)        # Philox blocks/s: one per evaluated label
+    # seconds per barrier: one CTA of 1024 threads, clusters of 2, 4 and 8
+    barrier_us = {c: B.cg_microbench(k, local) * 1e6 for c, k in ((1, 7), (2, 4), (4, 5), (8, 6))}
 
     sysm = B.System(reps, precision=B.CG_FP32, refresh_every=0, block_threads=args.threads,
                     device=local)
@@ -493,7 +495,8 @@ def run_ours(args):
         # and three FFT passes
         "gpu_launches": args.steps * (1 + 4),
         "clocks": clk,
-        "peaks_measured": {"smem_rmw32_GBps": smem_peak / 1e9, "dadd_per_s": dadd_peak,
+        "peaks_measured": {"barrier_us_by_ctas": {str(c): v for c, v in barrier_us.items()},
+                           "smem_rmw32_GBps": smem_peak / 1e9, "dadd_per_s": dadd_peak,
                            "philox_blocks_per_s": philox_peak},
         "wall_s_timed": t_wall,
     }
@@ -606,7 +609,8 @@ def run_ours(args):
     # the mixed-L batch and the cluster-sized lattice (not the headline
     # workload): throughput of their own launch paths
     if not args.no_other_configs and rank == 0:
-        result["other_configs"] = other_configs(args, B, local, smem_peak=smem_peak, sms=sms)
+        result["other_configs"] = other_configs(args, B, local, smem_peak=smem_peak, sms=sms,
+                                                barrier_us=barrier_us)
 
     # sigma(t) relaxation at L=256: binary32 form against the binary64 form
     if args.sigma_hops > 0 and not args.no_other_configs and rank == 0:
@@ -736,7 +740,7 @@ def random_roofline(reps, hops_per_s):
                     "latency-bound gathers"}
 
 
-def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
+def other_configs(args, B, local, only=None, smem_peak=None, sms=None, barrier_us=None):
     """Throughput of the other batch configurations: 256 replicas with L
     drawn from {32, 48, 64, 96} (one launch per L on concurrent streams,
     replayed as a CUDA graph, CTA size and M from the autotuner, an FFT
@@ -830,6 +834,11 @@ def other_configs(args, B, local, only=None, smem_peak=None, sms=None):
         elif cl > 1 and smem_peak and sms:
             out[name]["roofline"] = cluster_roofline(reps, out[name]["hops_per_s"], cl,
                                                      smem_peak, sms, wl.precision)
+            if barrier_us:
+                # a hop of one replica against the measured cluster barrier
+                # (each chunk and each hop ends in one)
+                out[name]["roofline"]["hop_us"] = len(reps) / out[name]["hops_per_s"] * 1e6
+                out[name]["roofline"]["cluster_barrier_us"] = barrier_us.get(cl)
         if pair:
             out[name].update(pair)
             out[name]["pair_hops_share"] = pair_share(B, s, reps, wl.M)

@@ -377,8 +377,13 @@ int cg_refresh_tc_noalloc(int L, int R, double nu, const unsigned int *occ,
  *           ceiling of the rejection phase: one block per evaluated label;
  *           section "Parallel rejection algorithm", 3M random numbers per
  *           round on the GPU)
- * summed over all SMs; result written to *result.  CG_EINVAL for another
- * kind, CG_ECUDA on a CUDA error. */
+ * summed over all SMs;
+ *   kind 4, 5, 6: seconds per cluster barrier of 2, 4 or 8 CTAs of 1024
+ *           threads (one CTA per SM, all SMs busy), the fixed cost of the
+ *           cluster kernels' chunks and hops;
+ *   kind 7: seconds per CTA barrier of 1024 threads (one CTA per SM);
+ * result written to *result.  CG_EINVAL for another kind, CG_ECUDA on a
+ * CUDA error. */
 int cg_microbench(int kind, int device, double *result);
 
 /* Log-spaced trace of the dipole moment P and the energy, from which the

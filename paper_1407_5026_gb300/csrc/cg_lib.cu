@@ -2049,7 +2049,7 @@ int cg_refresh_async(cg_handle *h)
 
 int cg_microbench(int kind, int device, double *result)
 {
-    if (!result || kind < 0 || kind > 3) return fail(CG_EINVAL, "bad microbenchmark kind");
+    if (!result || kind < 0 || kind > 7) return fail(CG_EINVAL, "bad microbenchmark kind");
     int rc = microbench(kind, device, result);
     if (rc) return fail(rc, "microbenchmark failed");
     return CG_OK;

@@ -10,7 +10,15 @@
 //   kind 3  aggregate Philox-4x32-10 rate (blocks/s) of the PR kernels' own
 //           label generator (per-round prefix + per-label finish, two labels
 //           per thread, 2 x 512 threads per SM), the ceiling of the rejection
-//           phase: every evaluated label costs one block.
+//           phase: every evaluated label costs one block;
+//   kind 4, 5, 6  seconds per cluster barrier (cluster.sync) of 2, 4 or 8
+//           CTAs of 1024 threads, one CTA per SM, every SM's clusters busy:
+//           the fixed cost the cluster kernels pay per chunk and per hop;
+//   kind 7  seconds per CTA barrier (__syncthreads) of 1024 threads, one CTA
+//           per SM: the single-CTA kernels' per-chunk cost.
+// Barrier times are the difference of two launch lengths (4096 and 1024
+// barriers) over 3072 barriers, so the launch overhead cancels.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "cg_device.cuh"
@@ -69,6 +77,27 @@ __global__ void __launch_bounds__(512, 2) philox_rate_kernel(int iters, uint32_t
     }
     acc = __reduce_xor_sync(0xffffffffu, acc);
     if ((threadIdx.x & 31) == 0) atomicXor(&sink[blockIdx.x & 15], acc);
+}
+
+// iters barriers of the whole cluster (kCluster) or of the CTA; the dynamic
+// shared memory only keeps one CTA per SM, as in the persistent kernels
+template <bool kCluster>
+__global__ void __launch_bounds__(1024) barrier_kernel(int iters, unsigned *sink)
+{
+    unsigned acc = threadIdx.x;
+    if (kCluster) {
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        for (int it = 0; it < iters; ++it) {
+            cl.sync();
+            acc += (unsigned)it;
+        }
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            __syncthreads();
+            acc += (unsigned)it;
+        }
+    }
+    if (acc == 0xFFFFFFFFu) sink[0] = acc;            // keeps the loop
 }
 
 static double time_ms(cudaEvent_t a, cudaEvent_t b)
@@ -136,6 +165,41 @@ int microbench(int kind, int device, double *result)
             const double labels = 2.0 * iters * 512.0 * blocks;
             const double rate = labels / (time_ms(e0, e1) * 1e-3);
             if (rep > 0 && rate > best) best = rate;
+        }
+    } else if (kind >= 4 && kind <= 7) {
+        const int C = kind == 4 ? 2 : kind == 5 ? 4 : kind == 6 ? 8 : 1;
+        const int smem = 120 * 1024;                      // one CTA per SM
+        const int blocks = (sms / C) * C;
+        auto kern = C > 1 ? barrier_kernel<true> : barrier_kernel<false>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        double ms_short = 0.0;
+        best = 1e30;
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            for (int len = 0; len < 2 && err == cudaSuccess; ++len) {
+                const int iters = len ? 4096 : 1024;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+                cfg.blockDim = dim3(1024, 1, 1);
+                cfg.dynamicSmemBytes = (size_t)smem;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)C;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = C > 1 ? 1 : 0;
+                cudaEventRecord(e0);
+                err = cudaLaunchKernelEx(&cfg, kern, iters, (unsigned *)sink);
+                cudaEventRecord(e1);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                const double ms = time_ms(e0, e1);
+                if (!len) {
+                    ms_short = ms;
+                } else if (rep > 0) {
+                    const double t = (ms - ms_short) * 1e-3 / 3072.0;
+                    if (t < best) best = t;
+                }
+            }
         }
     } else {
         err = cudaErrorInvalidValue;

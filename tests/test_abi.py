@@ -144,6 +144,13 @@ def test_workspace_plan_counts_the_cubic_tensor_core_scratch(libcg):
     assert tc - plain == ((scratch + 255) // 256) * 256 + 256
 
 
+def test_microbench_refuses_unknown_kinds_on_host(libcg):
+    from paper_1407_5026_gb300 import binding as B
+    for kind in (-1, 8):
+        with pytest.raises(B.CgError, match="microbenchmark kind"):
+            B.cg_microbench(kind, 0)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     # a fresh process whose library path points nowhere: every entry point
     # goes through load(), which raises instead of falling back to anything
