@@ -253,15 +253,19 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(FftArgs a, int ax
         const double *__restrict__ pb = Rb.phi + site0;
         float *__restrict__ ea = reinterpret_cast<float *>(Ra.eps) + site0;
         float *__restrict__ eb = reinterpret_cast<float *>(Rb.eps) + site0;
+        // the transforms took n - nu with nu rounded to binary32; sum_t g(s-t)
+        // = C0 for every s, so (nu_f - nu) C0 restores the exact nu
+        const double ca = d_mul(d_sub((double)(float)Ra.nu, Ra.nu), Ra.C0);
+        const double cb = d_mul(d_sub((double)(float)Rb.nu, Rb.nu), Rb.C0);
 #pragma unroll 4
         for (int e = threadIdx.x; e < n; e += kFftThreads) {
             const int w = e / L, k = e - w * L;
             const float2 v = out[w * Ls + out_pos(k, a, true)];
-            const double na = d_add(pa[e], (double)v.x);
+            const double na = d_add(pa[e], d_add((double)v.x, ca));
             err_a = fmax(err_a, fabs((double)ea[e] - na));
             ea[e] = __double2float_rn(na);
             if (two) {
-                const double nb = d_add(pb[e], (double)v.y);
+                const double nb = d_add(pb[e], d_add((double)v.y, cb));
                 err_b = fmax(err_b, fabs((double)eb[e] - nb));
                 eb[e] = __double2float_rn(nb);
             }

@@ -119,3 +119,23 @@ def test_fft_refresh_at_the_bench_batch_size(B):
             assert o["refreshes"] == 1 and 0 < o["max_eps_err_last_refresh"] <= 1e-4
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("L,dim,n_occ", [(12, 2, 48), (48, 2, 768), (24, 3, 4608)])
+def test_fft_refresh_with_a_filling_binary32_does_not_hold(B, L, dim, n_occ):
+    # nu = 1/3 is not a binary32 number; the transforms take n - nu_f and the
+    # last pass adds (nu_f - nu) C0 back in binary64
+    N = L ** dim
+    nu = n_occ / N
+    reps = [dict(r, nu=nu) for r in _reps(L, 3, dim, 2)]
+    s = B.System(reps, precision=B.CG_FP32, refresh_kind=B.CG_REFRESH_FFT)
+    try:
+        assert s.run(200, 512) == B.CG_OK
+        B.cg_refresh(s.h)
+        for k in range(3):
+            n, eps, phi, _ = s.state(k)
+            exact = (ref.site_energies_fft3(n, phi, nu, L) if dim == 3
+                     else ref.site_energies_fft(n, phi, nu, L))
+            assert np.abs(eps - exact).max() <= 2e-5
+    finally:
+        s.close()
