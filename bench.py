@@ -916,7 +916,7 @@ def e2e(args, B, reps, local, snapshot, with_eps=False):
     B.cg_run(sysm.h, HOPS_PER_STEP, M_run)             # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hops = 0
+    hops = attempts = 0
     for _ in range(steps):
         for g in groups:
             sysm.write_group(g, occ=bufs[g][0], eps=bufs[g][1] if with_eps else None,
@@ -929,6 +929,7 @@ def e2e(args, B, reps, local, snapshot, with_eps=False):
         for g in groups:
             _, _, c = sysm.read_group(g, occ=bufs[g][0], eps=bufs[g][1] if with_eps else False)
             hops += int((c["hops"] - bufs[g][2]["hops"]).sum())
+            attempts += int((c["attempts"] - bufs[g][2]["attempts"]).sum())
             bufs[g][2] = c
     dt = time.perf_counter() - t0
     sysm.close()
@@ -944,8 +945,11 @@ def e2e(args, B, reps, local, snapshot, with_eps=False):
             if not with_eps else
             "per step: cg_write_group_state (occupations, binary32 eps, counters) + cg_run + "
             "cg_refresh + cg_read_group_state (the same) from/to pinned host buffers")
+    # attempts/s beside hops/s: these steps come later in the chains'
+    # relaxation than the device-timed ones (acceptance slowly falling)
     return {"value": hops / dt, "unit": "hops/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": steps, "note": note}
+            "d2h_bytes_per_step": d2h, "steps": steps, "attempts_per_s": attempts / dt,
+            "acceptance": hops / max(1, attempts), "note": note}
 
 
 def main():
