@@ -915,6 +915,10 @@ def e2e(args, B, reps, local, snapshot, with_eps=False):
         M_run = 0
     B.cg_run(sysm.h, HOPS_PER_STEP, M_run)             # warm
     torch.cuda.synchronize()
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_initialized() else 1
+    if ws > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     hops = attempts = 0
     for _ in range(steps):
@@ -933,12 +937,14 @@ def e2e(args, B, reps, local, snapshot, with_eps=False):
             bufs[g][2] = c
     dt = time.perf_counter() - t0
     sysm.close()
+    # the whole job: every rank's hops over the slowest rank's time
+    dt, hops, attempts = combine_ranks(dt, hops, attempts, device=f"cuda:{local}")
     # per replica and step: bitmask words (and binary32 eps) each way; the
     # 112-byte device counter block read once and written once by the group
     # write (which keeps the library's own fields) and read once by the read
     e = 4 * N if with_eps else 0
-    h2d = R * (4 * words + e + 112)
-    d2h = R * (4 * words + e + 2 * 112)
+    h2d = ws * R * (4 * words + e + 112)                # the whole job's bytes
+    d2h = ws * R * (4 * words + e + 2 * 112)
     note = ("per step: cg_write_group_state (occupations, counters) + cg_refresh (eps rebuilt "
             "from the uploaded occupations) + cg_run + cg_refresh + cg_read_group_state "
             "(occupations, counters) for the whole batch from/to pinned host buffers"
