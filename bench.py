@@ -465,6 +465,10 @@ def run_ours(args):
                      "traffic_unit": "DRAM bytes per launch (ncu capture)",
                      "kernel": "pr_persistent<float>",
                      "bytes_per_hop": bytes_per_hop,
+                     # the strict lower bound: the eps read-modify-write alone
+                     # (2 s N bytes per hop, the two table reads counted as free)
+                     "bytes_per_hop_strict": N * 2 * 4,
+                     "frac_strict": achieved / 2 / smem_peak,
                      "peak_source": "measured: shared-memory 32-bit read-modify-write "
                                     "microbenchmark over all SMs (cg_microbench kind 0)",
                      # the eps-update phase alone (the bandwidth-bound step):

@@ -1,6 +1,8 @@
 // cg_pr_kernel3d.cu -- launches of the persistent parallel-rejection kernel
 // (cg_pr_persistent.cuh) on the L x L x L cubic lattice, with L known at run
-// time (a power of two or any even L).
+// time (a power of two or any even L), and binary32 L = 32 fixed at compile
+// time (the largest power of two whose eps fits one CTA: the octant update's
+// offsets and loop counts become constants).
 #include "cg_pr_persistent.cuh"
 
 namespace cg {
@@ -9,6 +11,13 @@ template <typename Real, int kThreads, bool kTime>
 static void launch3_tt(const DevReplica *d_reps, const int *d_index, int n_ctas, int smem_bytes,
                        const RunArgs &args, cudaStream_t st, int L)
 {
+    if constexpr (sizeof(Real) == 4) {
+        if (L == 32) {
+            pr_persistent<Real, kThreads, 5, kTime, 3>
+                <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+            return;
+        }
+    }
     if ((L & (L - 1)) == 0)
         pr_persistent<Real, kThreads, 0, kTime, 3>
             <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
@@ -31,11 +40,17 @@ static cudaError_t launch3_t(const DevReplica *d_reps, const int *d_index, int n
 template <typename Real, int kThreads>
 static cudaError_t set3_one(int bytes)
 {
-    const void *k[4] = {(const void *)pr_persistent<Real, kThreads, 0, false, 3>,
+    const void *k[6] = {(const void *)pr_persistent<Real, kThreads, 0, false, 3>,
                         (const void *)pr_persistent<Real, kThreads, -1, false, 3>,
                         (const void *)pr_persistent<Real, kThreads, 0, true, 3>,
-                        (const void *)pr_persistent<Real, kThreads, -1, true, 3>};
+                        (const void *)pr_persistent<Real, kThreads, -1, true, 3>,
+                        nullptr, nullptr};
+    if constexpr (sizeof(Real) == 4) {
+        k[4] = (const void *)pr_persistent<Real, kThreads, 5, false, 3>;
+        k[5] = (const void *)pr_persistent<Real, kThreads, 5, true, 3>;
+    }
     for (const void *f : k) {
+        if (!f) continue;
         const cudaError_t e =
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e) return e;

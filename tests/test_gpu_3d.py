@@ -7,7 +7,10 @@ bit-identical to the oracle's for powers of two and other even L, with and
 without a field; the tower sampler on cubic tables equals the oracle's; a
 batch that mixes square and cubic replicas keeps each chain exact; the
 stochastic clock of step 3c is exact in 3D too; in binary32 (refreshed in
-binary64) eps stays within 1e-4 of its definition; the split-BF16 tensor-core
+binary64) eps stays within 1e-4 of its definition, and at L = 32 on one CTA
+(L fixed at compile time) eps tracks its definition without a refresh, the
+logged hops replay on the occupations and the first hops equal the binary64
+serial chain's; the split-BF16 tensor-core
 refresh on cubic tables (N = L^3 a multiple of 128) gives eps within 5e-5 of
 its definition, alone and inside runs; on thread-block clusters (eps split
 by z-planes, 1/r of the update indexed by r^2) binary64 stays bit-exact and
@@ -152,6 +155,43 @@ def test_cubic_binary32_with_binary64_refresh(B):
             ch = _oracle_for(reps[k])
             ch.set_state(n, phi)
             assert np.max(np.abs(eps - ch.state()[1])) <= 1e-4
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("threads", [1024, 512, 256])
+def test_cubic_binary32_l32_one_cta(B, threads):
+    # binary32 at L = 32 on one CTA (the instance with L fixed at compile
+    # time): with no refresh, eps after 1500 hops stays within 1e-4 of its
+    # definition (every site of the octant update gets its 1/r terms); the
+    # logged hops move an electron from an occupied site to an empty one
+    # within r_max and reproduce the final occupation; the first hops equal
+    # the binary64 serial chain's (no near tie among them on these seeds)
+    L, r_max = 32, 3
+    reps = [_cubic(L=L, r_max=r_max, T=0.05, seed=s, replica=s) for s in range(3)]
+    s = B.System(reps, precision=B.CG_FP32, cluster_size=1, block_threads=threads)
+    try:
+        sh = B.cg_group_shape(s.h, 0)
+        assert sh["cluster"] == 1 and sh["threads"] == threads
+        occ0 = [s.state(k)[0].astype(np.int8).copy() for k in range(3)]
+        rc, log = s.run_logged(1500, 1024)
+        assert rc == B.CG_OK
+        for k in range(3):
+            n, eps, phi, _ = s.state(k)
+            assert np.abs(eps - ref.site_energies_fft3(n, phi, 0.5, L)).max() <= 1e-4
+            occ = occ0[k]
+            for e in log[k]:
+                i, j = int(e["i"]), int(e["j"])
+                assert occ[i] == 1 and occ[j] == 0
+                d = [((j // L**a) % L - (i // L**a) % L + L // 2) % L - L // 2
+                     for a in range(3)]
+                assert 0 < d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= r_max * r_max
+                occ[i], occ[j] = 0, 1
+            np.testing.assert_array_equal(occ, n)
+        ch = _oracle_for(reps[0])
+        _, olog = ch.run(30, 1024, log=True)
+        for f in ("i", "j", "q", "p", "round"):
+            np.testing.assert_array_equal(log[0][f][:30], olog[f], err_msg=f)
     finally:
         s.close()
 
