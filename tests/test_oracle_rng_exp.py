@@ -5,6 +5,7 @@
   b & 0xFFFF, 0) under key (seed lo 32, seed hi 32); reaching offsets past
   2^48 blocks exercises counter words 0, 1, 2 and both key words.
 * exp: Python's ``math.exp`` (the platform libm) within 2 ulp.
+* Uniformity and independence of the outputs by chi-square tests.
 """
 import ctypes
 import math
@@ -87,6 +88,35 @@ def test_philox_uniformity_chi2():
         exp = len(top) / 16
         chi2 = float(((cnt - exp) ** 2 / exp).sum())
         assert chi2 < 45.0  # 15 dof, p ~ 1e-4
+
+
+def test_philox_independence_chi2():
+    # joint 8 x 8 histograms of the top three bits of two outputs, against
+    # independence: two words of one block, word 0 of consecutive labels k,
+    # k + 1 (counter word 0) and of consecutive rounds r, r + 1 (counter word
+    # 1), and words 2 and 3 of one block under the replica word set (counter
+    # word 3).  A counter word the generator ignored or a word it repeated
+    # would put every pair on the diagonal.
+    key = [0x0BADF00D, 0x5EED1234]
+    n = 8192
+
+    def chi2(a, b):
+        cnt = np.bincount((a >> 29).astype(np.int64) * 8 + (b >> 29).astype(np.int64),
+                          minlength=64)
+        exp = len(a) / 64
+        return float(((cnt - exp) ** 2 / exp).sum())
+
+    blk = np.array([oracle.philox([k, 9, 0, 0], key) for k in range(n + 1)], dtype=np.uint32)
+    nxt = np.array([oracle.philox([77, r + 1, 0, 0], key) for r in range(n)], dtype=np.uint32)
+    cur = np.array([oracle.philox([77, r, 0, 0], key) for r in range(n)], dtype=np.uint32)
+    rep = np.array([oracle.philox([k, 9, 0, 3], key) for k in range(n)], dtype=np.uint32)
+    # 63 degrees of freedom: the 1e-4 upper quantile is 113.5
+    assert chi2(blk[:n, 0], blk[:n, 1]) < 113.5
+    assert chi2(blk[:n, 0], blk[1:, 0]) < 113.5
+    assert chi2(cur[:, 0], nxt[:, 0]) < 113.5
+    assert chi2(rep[:, 2], rep[:, 3]) < 113.5
+    # the statistic does see dependence: a word against itself
+    assert chi2(blk[:n, 0], blk[:n, 0]) > 1000.0
 
 
 def _ulp(x):
