@@ -1,7 +1,7 @@
 // cg_pr_kernel.cu -- launches of the persistent parallel-rejection kernel
-// (cg_pr_persistent.cuh) on the square lattice, with L = 64 and L = 128
-// fixed at compile time and any other L at run time; cubic lattices go to
-// cg_pr_kernel3d.cu.
+// (cg_pr_persistent.cuh) on the square lattice, with L = 32, 48, 64, 96 and
+// 128 fixed at compile time and any other L at run time; cubic lattices go
+// to cg_pr_kernel3d.cu.
 #include "cg_pr_persistent.cuh"
 
 namespace cg {
@@ -11,6 +11,18 @@ static void launch_tt(const DevReplica *d_reps, const int *d_index, int n_ctas, 
                       const RunArgs &args, cudaStream_t st, int L)
 {
     switch (L) {
+    case 32:
+        pr_persistent<Real, kThreads, 5, kTime>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    case 48:
+        pr_persistent<Real, kThreads, -48, kTime>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
+    case 96:
+        pr_persistent<Real, kThreads, -96, kTime>
+            <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
+        break;
     case 64:
         pr_persistent<Real, kThreads, 6, kTime>
             <<<n_ctas, kThreads, smem_bytes, st>>>(d_reps, d_index, args);
@@ -44,6 +56,13 @@ template <typename Real, int kThreads, bool kTime>
 static cudaError_t set_smem_tt(int bytes)
 {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 5, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
+        (e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, -48, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) ||
+        (e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, -96, kTime>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+        return e;
     if ((e = cudaFuncSetAttribute(pr_persistent<Real, kThreads, 6, kTime>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
         return e;

@@ -44,6 +44,8 @@
 
 namespace cg {
 
+// kLog2L: L = 2^kLog2L fixed at compile time (> 0), any power of two (0),
+// any even L (-1), or the even L = -kLog2L fixed at compile time (< -1).
 // kTime: CG_TIME_GAUSSIAN runs (the step-3c deviates are drawn in the
 // kernel); the default deterministic clock compiles without that code.
 // kDim: 2 for the L x L square lattice, 3 for the L x L x L cubic lattice
@@ -59,6 +61,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThre
 pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index, RunArgs a)
 {
     constexpr bool kPow2 = kLog2L >= 0;
+    // L fixed at compile time: 2^kLog2L (kLog2L > 0), or -kLog2L, an even L
+    // that is not a power of two (kLog2L < -1); 0 when L is read at run time
+    constexpr int kFixL = kLog2L > 0 ? (1 << kLog2L) : (kLog2L < -1 ? -kLog2L : 0);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int s_wlabel[32];
     __shared__ Cand s_cand[32];
@@ -81,11 +86,15 @@ pr_persistent(const DevReplica *__restrict__ reps, const int *__restrict__ index
 
     const DevReplica &Rg = reps[index[blockIdx.x]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int L = kLog2L > 0 ? (1 << kLog2L) : Rg.L;
+    const int L = kFixL ? kFixL : Rg.L;
     const int N = kDim == 3 ? L * L * L : L * L, H1 = L / 2 + 1, words = (N + 31) / 32;
     const int ntab = kDim == 3 ? H1 * H1 * H1 : H1 * H1;
     const int V = Rg.V;
-    const unsigned magic = kPow2 ? 0u : Rg.magicL;
+    // floor(s / L) = umulhi(s, floor(2^32 / L) + 1) for the site indices used;
+    // the host computes the same multiplier for run-time L
+    const unsigned magic = kPow2  ? 0u
+                           : kFixL ? (unsigned)(4294967296ull / (unsigned long long)kFixL + 1ull)
+                                   : Rg.magicL;
     const int log2L = kLog2L > 0 ? kLog2L : __ffs(L) - 1;   // used when L is a power of two
     const uint32_t key0 = Rg.key0, key1 = Rg.key1, rep = Rg.replica;
     const double T = Rg.T;
