@@ -144,6 +144,27 @@ def test_workspace_plan_counts_the_cubic_tensor_core_scratch(libcg):
     assert tc - plain == ((scratch + 255) // 256) * 256 + 256
 
 
+@pytest.mark.parametrize("L,R,nu,msg", [
+    (15, 4, 0.5, "L must be even"), (1026, 4, 0.5, "L must be even"),
+    (20, 4, 0.5, "multiple of 128"), (64, 0, 0.5, "R must be"), (64, 513, 0.5, "R must be"),
+    (64, 4, 1.0, "nu must be"), (128, 49, 0.5, "static maximum"),
+    (1024, 1, 0.5, "static maximum"),
+])
+def test_noalloc_refresh_refuses_bad_sizes_on_host(libcg, L, R, nu, msg):
+    # every argument and size check comes before the first CUDA call, so the
+    # refusals hold without a GPU; the buffers are host memory the refused
+    # call never touches
+    import numpy as np
+    from paper_1407_5026_gb300 import binding as B
+    buf = np.zeros(4, np.float64)
+    with pytest.raises(B.CgError) as ei:
+        B.cg_refresh_tc_noalloc(L, R, nu, buf.ctypes.data, buf.ctypes.data, buf.ctypes.data)
+    assert ei.value.code == B.CG_EINVAL
+    assert msg in str(ei.value)
+    with pytest.raises(B.CgError, match="required"):
+        B.cg_refresh_tc_noalloc(64, 4, 0.5, 0, buf.ctypes.data, buf.ctypes.data)
+
+
 def test_microbench_refuses_unknown_kinds_on_host(libcg):
     from paper_1407_5026_gb300 import binding as B
     for kind in (-1, 8):
